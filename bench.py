@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of the spectral-element Ax operator on one GB300 per rank.
+
+A step is one application of Ax (gradient, geometric factor, transposed
+gradient, store: the whole hot path) to the FP64 workload N=7, E=32768
+(16.8M nodes, 1.07 GB moved per call; larger than the 129 MB L2, so no flush
+is needed between steps).  The JSON line reports GDOF/s (10^9 element-local
+nodes per second) for that workload, plus
+
+  e2e           the same metric with pinned-host inputs/outputs copied each step;
+  roofline      the FP64 kernel against the FP64 pipe peak (the path is bound by
+                FP64 arithmetic on GB300, not by HBM);
+  variants      FP32 / BF16-split (N=15, E=8192), the uneven-order batched plan,
+                and N=7, E=262144 in FP64 and FP32, each with GDOF/s, GB/s and its
+                error against the FP64 GPU path (itself held to 1e-12 of the CPU
+                oracle by the parity tests), measured with the FP64 GPU reducer;
+  cpu_baseline  the FP64 CPU oracle on the host cores.
+
+`--impl reference` times the CPU oracle alone (the reference arm).
+Under torchrun each rank runs its own E=32768 shard (weak scaling, no
+collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sem_inputs as si  # noqa: E402
+
+METRIC = "Ax GDOF/s and HBM GB/s (FP64 vs mixed/batched) on 1 GB300 at stated error"
+WORKLOAD = dict(N=7, E=32768)
+FP64_PEAK_TFLOPS = 1.2586   # 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (GB300 FP64 pipe)
+KERNEL_SOURCES = ["ax_tile.cuh", "ax_plain.cuh", "ax_f64.cu", "common.cuh"]
+
+
+def flops_per_element(n: int) -> int:
+    """Sum-factorised Ax: 6 contractions of n FMAs per node plus 15 flop of
+    geometric factor per node (FMA = 2 flop)."""
+    return 12 * n ** 4 + 15 * n ** 3
+
+
+def bytes_per_node(elem_bytes: int) -> int:
+    return 8 * elem_bytes          # u + 6 G + w
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard_seed_workload(rank: int, device, E: int | None = None):
+    """Rank r's shard: the N=7, E=32768 recipe with seed [1503, 7659, 1] for
+    rank 0 and [1503, 7659, 1, r] for r > 0 (independent elements; Ax is
+    element-local, so no rank needs another rank's data)."""
+    rng = si.rng_for(1) if rank == 0 else si.rng_for(1, extra=rank)
+    return si.make_mesh(rng, WORKLOAD["E"] if E is None else E, WORKLOAD["N"], device=device)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        load = [s for s, p in zip(sm, pw) if p > 200.0] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------- timing helpers
+
+def time_region(fn, steps: int, warmup: int, world: int = 1) -> float:
+    """Seconds for `steps` calls of fn (after `warmup`), CUDA events on the
+    current stream, barrier + synchronize on both sides, max over ranks."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(world)
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(steps):
+        fn()
+    b.record(s)
+    torch.cuda.synchronize()
+    barrier(world)
+    return max_over_ranks(a.elapsed_time(b) / 1e3, world)
+
+
+def rel_err_gpu(semax, w, ref) -> float:
+    r = semax.reduce(w.reshape(-1), ref.reshape(-1)).cpu().numpy()
+    return float(r[0] / r[1]) if r[1] > 0 else float(r[0])
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1503_07659_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic() -> float | None:
+    """DRAM bytes per launch of the FP64 kernel from the committed ncu summary,
+    only if the kernel sources still hash to what was profiled."""
+    path = os.path.join(ROOT, "profiles", "ax_f64_n8_e32768.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (m_sha and m_tr) or m_sha.group(1) != kernel_source_sha():
+        return None
+    return float(m_tr.group(1))
+
+
+def load_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+
+def cpu_baseline(mesh_host, target_s: float = 10.0) -> dict:
+    import oracle
+    oracle.build()
+    u, G, D = mesh_host
+    E = u.shape[0]
+    n = D.shape[0]
+    reps, t0 = 0, time.perf_counter()
+    used = 0
+    while True:
+        _, used = oracle.sem_ax(u, G, D, return_threads=True)
+        reps += 1
+        if time.perf_counter() - t0 >= target_s or reps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": reps * E * n ** 3 / dt / 1e9, "unit": "GDOF/s", "cores": int(used), "kind": "oracle",
+            "sample": f"full N=7 E={E} workload x {reps} pass(es), {dt:.1f} s, FP64 plain C loop nest "
+                      f"(-O2 -ffp-contract=off, OpenMP over elements)"}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    m = si.make_workload(1, device="cpu")[0]
+    u, G, D = m.u.numpy(), m.G.numpy(), m.D.numpy()
+    n = m.n
+    chunk = 1024                       # elements per timed step (a bounded sample)
+    sl = [(c, min(m.E, c + chunk)) for c in range(0, m.E, chunk)]
+    for q in range(args.warmup):
+        a, b = sl[q % len(sl)]
+        oracle.sem_ax(u[a:b], G[a:b], D)
+    t0 = time.perf_counter()
+    used = 0
+    for q in range(args.steps):
+        a, b = sl[q % len(sl)]
+        _, used = oracle.sem_ax(u[a:b], G[a:b], D, return_threads=True)
+    dt = time.perf_counter() - t0
+    value = args.steps * chunk * n ** 3 / dt / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "sem_ax FP64 N=7 E=32768 (16.8M nodes)", "N": 7, "E": m.E,
+                       "step_sample": f"{chunk} elements per step, cycling through the workload"},
+            "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": int(used), "kind": "oracle",
+                             "sample": f"{chunk}-element slices of the N=7 E=32768 workload, {args.steps} steps"},
+            "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def variants(semax, reps: int) -> dict:
+    """Secondary forms, each on its own workload (timed with CUDA events)."""
+    out = {}
+
+    def rate(fn, dofs, nbytes, r=reps):
+        t = time_region(fn, r, 3) / r
+        return {"gdofs": dofs / t / 1e9, "hbm_gbs": nbytes / t / 1e9, "us_per_call": t * 1e6}
+
+    # N=15, E=8192: FP32 storage, FP32 and BF16-split compute
+    m = si.make_workload(2, device="cuda")[0]
+    dofs = m.dofs
+    ref = semax.sem_ax(m.u, m.G, m.D)
+    u, G, D = m.u.float(), m.G.float(), m.D.float()
+    del m
+    w = torch.empty_like(u)
+    for name, fn in [("f32", lambda: semax.sem_ax_f32(u, G, D, w)),
+                     ("bf16x3", lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=3)),
+                     ("bf16x6", lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=6))]:
+        r = rate(fn, dofs, dofs * bytes_per_node(4))
+        r["rel_err_vs_f64"] = rel_err_gpu(semax, w, ref)
+        out[f"{name}_N15_E8192"] = r
+    del u, G, D, w, ref
+    torch.cuda.empty_cache()
+
+    # uneven orders, one persistent graph-captured launch vs per-order launches
+    mix = si.make_workload(3, device="cuda")
+    dofs = sum(x.dofs for x in mix)
+    ws = [torch.empty_like(x.u) for x in mix]
+    plan = semax.Plan([(x.N, x.u, x.G, x.D, w) for x, w in zip(mix, ws)], tune=True)
+    r = rate(plan, dofs, dofs * bytes_per_node(8))
+    r["tuned"] = {x.N: plan.config(x.N) for x in mix}
+    out["batched_plan_mix"] = r
+    out["per_order_launches_mix"] = rate(lambda: [semax.sem_ax(x.u, x.G, x.D, w) for x, w in zip(mix, ws)],
+                                         dofs, dofs * bytes_per_node(8))
+    out["mix_orders"] = {x.N: x.E for x in mix}
+    plan.close()
+    del mix, ws
+    torch.cuda.empty_cache()
+
+    # N=7, E=262144: FP64 vs FP32 storage and compute
+    m = si.make_workload(4, device="cuda")[0]
+    dofs = m.dofs
+    w64 = torch.empty_like(m.u)
+    out["f64_N7_E262144"] = rate(lambda: semax.sem_ax(m.u, m.G, m.D, w64), dofs, dofs * bytes_per_node(8), 10)
+    u, G, D = m.u.float(), m.G.float(), m.D.float()
+    del m
+    w32 = torch.empty_like(u)
+    r = rate(lambda: semax.sem_ax_f32(u, G, D, w32), dofs, dofs * bytes_per_node(4), 10)
+    r["rel_err_vs_f64"] = rel_err_gpu(semax, w32, w64)
+    out["f32_N7_E262144"] = r
+    del u, G, D, w32, w64
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args, rank, world):
+    import paper_1503_07659_gb300 as semax
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mesh = shard_seed_workload(rank, dev)
+    n, E = mesh.n, mesh.E
+    dofs = mesh.dofs
+    w = torch.empty_like(mesh.u)
+    step = lambda: semax.sem_ax(mesh.u, mesh.G, mesh.D, w)  # noqa: E731
+
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    t = time_region(step, args.steps, args.warmup, world)
+    clk = clocks.stop()
+    t_step = t / args.steps
+    value = world * dofs / t_step / 1e9
+
+    # end to end: pinned host buffers, copies inside the timed region
+    e2e_steps = min(args.steps, 50)
+    u_h = mesh.u.cpu().pin_memory()
+    G_h = mesh.G.cpu().pin_memory()
+    D_h = mesh.D.cpu().pin_memory()
+    w_h = torch.empty_like(u_h).pin_memory()
+    bufs = semax.sem_ax_from_host(u_h, G_h, D_h, w_h)
+    t_e2e = time_region(lambda: semax.sem_ax_from_host(u_h, G_h, D_h, w_h, bufs), e2e_steps,
+                        max(3, args.warmup // 10), world) / e2e_steps
+    e2e = {"value": world * dofs / t_e2e / 1e9, "unit": "GDOF/s",
+           "h2d_bytes_per_step": u_h.numel() * 8 + G_h.numel() * 8 + D_h.numel() * 8,
+           "d2h_bytes_per_step": w_h.numel() * 8, "steps": e2e_steps,
+           "path": "pinned host -> device copies, sem_ax, device -> pinned host copy"}
+    assert torch.equal(w_h, w.cpu()), "end-to-end result differs from the device-resident result"
+    del bufs, u_h, G_h, w_h
+
+    if rank != 0:
+        return
+    flops = E * flops_per_element(n)
+    nbytes = dofs * bytes_per_node(8)
+    achieved = flops / t_step / 1e12
+    peaks = load_peaks()
+    roofline = {"bound": "alu", "kernel": "ax_plain_kernel<double, 8, column>",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": profiled_traffic(),
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (GB300 nominal 1.25 TF)",
+                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                "hbm_gbs": nbytes / t_step / 1e9,
+                "hbm_frac_of_measured": nbytes / t_step / 1e9 / peaks.get("hbm_gbs", 6786.6)}
+    line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "sem_ax FP64 N=7 E=32768 per GPU (16.8M nodes, 1.07 GB/call)",
+                       "N": 7, "E_per_gpu": E, "nodes_per_gpu": dofs,
+                       "l2": "inputs larger than L2 (1.07 GB per step vs 129 MB L2), no flush"},
+            "hbm_gbs": world * nbytes / t_step / 1e9,
+            "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline}
+    if not args.no_variants:
+        line["variants"] = variants(semax, reps=20)
+    if not args.no_cpu_baseline and world == 1:
+        host = shard_seed_workload(0, "cpu")
+        line["cpu_baseline"] = cpu_baseline((host.u.numpy(), host.G.numpy(), host.D.numpy()))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world = dist_setup()
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            if not torch.cuda.is_available():
+                raise SystemExit("bench.py: no CUDA device (the library has no CPU path)")
+            run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,158 @@
+/*
+ * semax.h -- C ABI of libsemax, the element-local spectral-element Laplacian
+ * operator ("Ax") for one NVIDIA GB300 (sm_103a).
+ *
+ * The operation.  For every hexahedral element e of polynomial order N
+ * (n = N+1 Gauss-Lobatto-Legendre nodes per direction) the library computes
+ *
+ *     w_e = sum_{a,b in {r,s,t}} D_a^T diag(G_e,ab) D_b u_e
+ *
+ * with D_r = I(x)I(x)D, D_s = I(x)D(x)I, D_t = D(x)I(x)I acting on the node
+ * index (k*n + j)*n + i, i.e. the sum-factorised sequence
+ *     ur = sum_l D[i][l] u[k][j][l],  us = sum_l D[j][l] u[k][l][i],
+ *     ut = sum_l D[k][l] u[l][j][i];  [wr ws wt] = G_p [ur us ut];
+ *     w  = sum_l D[l][i] wr[k][j][l] + D[l][j] ws[k][l][i] + D[l][k] wt[l][j][i].
+ * This is the textbook weak-form Laplacian of the spectral-element method
+ * (Deville, Fischer & Mund 2002, Sec. 4.4).  The paper (Kloeckner, "Loo.py:
+ * From Fortran to performance via transformation and substitution rules",
+ * ARRAY'15) does not print this operator: its Section 1 names PDE-solver
+ * kernels and autotuning search spaces as the system's use cases, its
+ * Section 3 ingests Fortran array subroutines of exactly this shape (arrays
+ * u(i,j,k,e) passed by the caller, loop bounds as arguments), and its
+ * Section 5.2 blocks a matrix-matrix product, the form each contraction above
+ * takes ((n x n) times (n x n^2)).
+ *
+ * Layouts (all row-major C order, i fastest = Fortran u(i,j,k,e)):
+ *   u, w   [E][n][n][n]
+ *   G      [E][6][n][n][n], components (rr, rs, rt, ss, st, tt) of the
+ *          symmetric 3x3 factor det(J) w_i w_j w_k J^{-1} J^{-T}
+ *   D      [n][n], D[i][l] = derivative of the l-th Lagrange polynomial at
+ *          node i
+ *
+ * Conventions shared by every entry point:
+ *   - All array pointers are DEVICE pointers owned by the caller.  The library
+ *     never allocates, frees or synchronises inside sem_ax* calls; work is
+ *     queued on `stream` (a cudaStream_t, NULL = legacy default stream) and
+ *     the call returns before it finishes.
+ *   - 1 <= N <= 15 (n <= 16), else SEMAX_EUNSUPPORTED_N.
+ *   - E == 0 is a no-op returning SEMAX_OK (pointers are not inspected).
+ *     E < 0 or a NULL pointer with E > 0 returns SEMAX_EINVAL.
+ *   - u, G and w must be 16-byte aligned (128-bit vector access), else
+ *     SEMAX_EALIGN.  D needs only its natural alignment.
+ *   - w must not overlap u, G or D, else SEMAX_EALIAS.
+ *   - A failed kernel launch returns SEMAX_ECUDA; semax_last_cuda_error()
+ *     then gives the cudaError_t of the failing call on this host thread.
+ *   - On any error nothing has been queued and w is untouched.
+ */
+#ifndef SEMAX_H
+#define SEMAX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SEMAX_OK = 0,
+    SEMAX_EINVAL = -1,          /* bad count, NULL pointer, bad argument        */
+    SEMAX_EUNSUPPORTED_N = -2,  /* N outside 1..15                              */
+    SEMAX_EALIGN = -3,          /* u, G or w not 16-byte aligned                */
+    SEMAX_EALIAS = -4,          /* output overlaps an input                     */
+    SEMAX_ECUDA = -5,           /* a CUDA runtime call failed                   */
+    SEMAX_ETIMEOUT = -6,        /* a bounded device-side wait gave up           */
+    SEMAX_ENOPLAN = -7,         /* NULL or destroyed plan                       */
+    SEMAX_EWORKSPACE = -8,      /* workspace missing or too small               */
+    SEMAX_EIO = -9              /* tuning cache could not be read or written    */
+} semax_status;
+
+typedef enum { SEMAX_F64 = 0, SEMAX_F32 = 1 } semax_prec;
+
+/* ---------------------------------------------------------------- plain forms */
+
+/* FP64 Ax.  Loads u and G once, stores w once; computes in double. */
+int sem_ax(int64_t E, int N, const double *u, const double *G, const double *D,
+           double *w, void *stream);
+
+/* FP32 storage and FP32 compute.  G_scale is NULL or [E] per-element factors
+ * s_e: the kernel then treats the stored G as G_e / s_e and multiplies the
+ * element's result by s_e (use powers of two so that this is exact). */
+int sem_ax_f32(int64_t E, int N, const float *u, const float *G, const float *D,
+               float *w, const float *G_scale, void *stream);
+
+/* FP32 storage; the six derivative contractions run on tensor cores in BF16
+ * with FP32 accumulation, each FP32 operand x split as x0 + x1 (+ x2) with
+ * x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1).  terms = 3 keeps
+ * the products x0 y0 + x0 y1 + x1 y0 ("bf16x3", ~16 significant bits);
+ * terms = 6 also keeps x0 y2 + x1 y1 + x2 y0 (~24 bits).  The geometric
+ * factor multiply is FP32.  G_scale as in sem_ax_f32. */
+int sem_ax_bf16x3(int64_t E, int N, const float *u, const float *G, const float *D,
+                  float *w, const float *G_scale, int terms, void *stream);
+
+/* ---------------------------------------------------------------- batched form */
+
+/* One group of E elements of order N (FP64), with its own arrays. */
+typedef struct {
+    int N;
+    int64_t E;
+    const double *u;
+    const double *G;
+    const double *D;
+    double *w;
+} semax_group;
+
+/* Bytes of device workspace sem_ax_batched needs for these groups. */
+int sem_ax_batched_workspace_size(const semax_group *groups, int ngroups, size_t *bytes);
+
+/* All groups in ONE persistent kernel launch: tiles of elements are handed out
+ * longest-first (cost ~ n^4 per element) through a device work counter held
+ * in `workspace` (device memory, >= the size above, caller-owned).  Queues a
+ * small upload of the work list from host memory and the kernel; the host
+ * buffers are copied before the call returns.  Tile sizes and thread mapping
+ * use built-in defaults (see the plan API for tuned choices). */
+int sem_ax_batched(const semax_group *groups, int ngroups, void *workspace,
+                   size_t ws_bytes, void *stream);
+
+/* A plan owns a device work list and a captured CUDA graph that resets the
+ * work counter and launches the persistent kernel.  Creating a plan
+ * allocates device memory; executing it does not.
+ *   tune = 0: use the tuning cache entry if present, else defaults;
+ *   tune = 1: time the candidate (elements per tile, thread mapping) pairs for
+ *             every order present on the current device and keep the fastest;
+ *             the choice is written to cache_path (JSON) if not NULL.
+ * The group arrays are bound into the plan: they must stay valid while the
+ * plan is used (tuning runs the kernel on them, overwriting their w). */
+typedef struct semax_plan semax_plan;
+int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, int ngroups,
+                       int tune, const char *cache_path);
+int sem_ax_plan_exec(semax_plan *plan, void *stream);
+int sem_ax_plan_destroy(semax_plan *plan);
+/* The configuration the plan uses for order N: elements per tile and thread
+ * mapping (0 = one thread per node, 1 = one thread per (i,j) column).
+ * Returns SEMAX_EINVAL if N is not in the plan. */
+int sem_ax_plan_config(const semax_plan *plan, int N, int *elems_per_tile, int *mapping);
+
+/* ---------------------------------------------------------------- FP64 checks */
+
+/* FP64 reductions over `count` entries, on the GPU:
+ *   out[0] = max_i |a_i - b_i|,  out[1] = max_i |b_i|,  out[2] = sum_i a_i b_i
+ * a and b are FP64 or FP32 (a_prec, b_prec in semax_prec), widened to double
+ * before any arithmetic.  `out` is a device pointer to 3 doubles.  Uses
+ * `workspace` (device, >= semax_reduce_workspace_size bytes) for per-block
+ * partial results; the result does not depend on the launch order. */
+int semax_reduce_workspace_size(int64_t count, size_t *bytes);
+int semax_reduce(int64_t count, const void *a, int a_prec, const void *b, int b_prec,
+                 double *out, void *workspace, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- errors */
+
+const char *semax_strerror(int status);
+/* cudaError_t of the last failing CUDA call made by libsemax on this thread. */
+int semax_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEMAX_H */

@@ -1,0 +1,159 @@
+"""semax: the element-local spectral-element Laplacian operator (Ax) on one
+GB300, behind the C ABI of include/semax.h.
+
+PyTorch supplies device memory and streams; the operator runs in the
+library's own CUDA kernels.  Functions take CUDA tensors in the layouts of the
+header (u, w [E,n,n,n]; G [E,6,n,n,n]; D [n,n]) and queue work on the current
+torch stream unless `stream` is given.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import SemaxError, semax_group, check, SEMAX_F32, SEMAX_F64
+
+__all__ = ["sem_ax", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_batched", "Plan", "reduce",
+           "sem_ax_from_host", "SemaxError", "library_path"]
+
+
+def library_path() -> str:
+    return _lib.LIB_PATH
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dims(u: torch.Tensor, D: torch.Tensor) -> tuple[int, int]:
+    n = D.shape[0]
+    E = u.shape[0]
+    return E, n - 1
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _out(w, u):
+    return torch.empty_like(u) if w is None else w
+
+
+def sem_ax(u: torch.Tensor, G: torch.Tensor, D: torch.Tensor, w: torch.Tensor | None = None,
+           stream=None) -> torch.Tensor:
+    """FP64 Ax: w = sum_ab D_a^T diag(G_ab) D_b u per element."""
+    E, N = _dims(u, D)
+    w = _out(w, u)
+    check(_lib.lib().sem_ax(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _stream(stream)), "sem_ax")
+    return w
+
+
+def sem_ax_f32(u, G, D, w=None, G_scale=None, stream=None) -> torch.Tensor:
+    """FP32 storage and compute; optional per-element G scale [E]."""
+    E, N = _dims(u, D)
+    w = _out(w, u)
+    check(_lib.lib().sem_ax_f32(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _ptr(G_scale),
+                                _stream(stream)), "sem_ax_f32")
+    return w
+
+
+def sem_ax_bf16x3(u, G, D, w=None, G_scale=None, terms: int = 3, stream=None) -> torch.Tensor:
+    """FP32 storage; contractions on tensor cores with BF16 operand splits."""
+    E, N = _dims(u, D)
+    w = _out(w, u)
+    check(_lib.lib().sem_ax_bf16x3(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _ptr(G_scale),
+                                   int(terms), _stream(stream)), "sem_ax_bf16x3")
+    return w
+
+
+def _groups(meshes) -> ctypes.Array:
+    """meshes: iterable of (N, u, G, D, w) with FP64 CUDA tensors."""
+    items = list(meshes)
+    arr = (semax_group * max(1, len(items)))()
+    for q, (N, u, G, D, w) in enumerate(items):
+        arr[q] = semax_group(int(N), int(u.shape[0]), _ptr(u), _ptr(G), _ptr(D), _ptr(w))
+    return arr, len(items)
+
+
+def sem_ax_batched(groups, workspace: torch.Tensor | None = None, stream=None) -> None:
+    """All groups (N, u, G, D, w) in one persistent launch (w written in place)."""
+    arr, ng = _groups(groups)
+    size = ctypes.c_size_t(0)
+    check(_lib.lib().sem_ax_batched_workspace_size(arr, ng, ctypes.byref(size)), "sem_ax_batched_workspace_size")
+    if workspace is None:
+        workspace = torch.empty(size.value, dtype=torch.uint8, device="cuda")
+    check(_lib.lib().sem_ax_batched(arr, ng, _ptr(workspace), workspace.numel(), _stream(stream)),
+          "sem_ax_batched")
+
+
+class Plan:
+    """Graph-captured persistent batched launch (see sem_ax_plan_create)."""
+
+    def __init__(self, groups, tune: bool = False, cache_path: str | None = None):
+        self._arr, ng = _groups(groups)
+        self._handle = ctypes.c_void_p()
+        check(_lib.lib().sem_ax_plan_create(ctypes.byref(self._handle), self._arr, ng, int(bool(tune)),
+                                            cache_path.encode() if cache_path else None),
+              "sem_ax_plan_create")
+
+    def __call__(self, stream=None) -> None:
+        check(_lib.lib().sem_ax_plan_exec(self._handle, _stream(stream)), "sem_ax_plan_exec")
+
+    def config(self, N: int) -> tuple[int, int]:
+        epb, mp = ctypes.c_int(0), ctypes.c_int(0)
+        check(_lib.lib().sem_ax_plan_config(self._handle, int(N), ctypes.byref(epb), ctypes.byref(mp)),
+              "sem_ax_plan_config")
+        return epb.value, mp.value
+
+    def close(self) -> None:
+        if self._handle:
+            check(_lib.lib().sem_ax_plan_destroy(self._handle), "sem_ax_plan_destroy")
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def reduce(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None,
+           workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """[max|a-b|, max|b|, a.b] in FP64 on the GPU (a, b FP64 or FP32)."""
+    if a.numel() != b.numel():
+        raise ValueError("reduce: size mismatch")
+    prec = {torch.float64: SEMAX_F64, torch.float32: SEMAX_F32}
+    count = a.numel()
+    size = ctypes.c_size_t(0)
+    check(_lib.lib().semax_reduce_workspace_size(count, ctypes.byref(size)), "semax_reduce_workspace_size")
+    if workspace is None:
+        workspace = torch.empty(size.value, dtype=torch.uint8, device=a.device)
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=a.device)
+    check(_lib.lib().semax_reduce(count, _ptr(a), prec[a.dtype], _ptr(b), prec[b.dtype], _ptr(out),
+                                  _ptr(workspace), workspace.numel(), _stream(stream)), "semax_reduce")
+    return out
+
+
+def sem_ax_from_host(u_host: torch.Tensor, G_host: torch.Tensor, D_host: torch.Tensor,
+                     w_host: torch.Tensor, bufs: dict | None = None, stream=None) -> dict:
+    """End-to-end FP64 Ax from (pinned) host tensors: copy u, G, D to the
+    device, run sem_ax, copy w back into w_host.  `bufs` caches the device
+    buffers between calls; it is returned.  The caller synchronises."""
+    if bufs is None:
+        bufs = {"u": torch.empty(u_host.shape, dtype=u_host.dtype, device="cuda"),
+                "G": torch.empty(G_host.shape, dtype=G_host.dtype, device="cuda"),
+                "D": torch.empty(D_host.shape, dtype=D_host.dtype, device="cuda"),
+                "w": torch.empty(u_host.shape, dtype=u_host.dtype, device="cuda")}
+    s = torch.cuda.current_stream() if stream is None else stream
+    with torch.cuda.stream(s):
+        bufs["u"].copy_(u_host, non_blocking=True)
+        bufs["G"].copy_(G_host, non_blocking=True)
+        bufs["D"].copy_(D_host, non_blocking=True)
+        sem_ax(bufs["u"], bufs["G"], bufs["D"], bufs["w"], stream=s)
+        w_host.copy_(bufs["w"], non_blocking=True)
+    return bufs

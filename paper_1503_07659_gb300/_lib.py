@@ -1,0 +1,85 @@
+"""ctypes binding of libsemax (include/semax.h).
+
+Argument marshalling only: every step of the operator runs in the library's
+CUDA kernels.  There is no CPU or PyTorch fallback: if the shared library is
+missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsemax.so")
+
+SEMAX_OK = 0
+SEMAX_F64, SEMAX_F32 = 0, 1
+
+STATUS_NAMES = {
+    0: "SEMAX_OK", -1: "SEMAX_EINVAL", -2: "SEMAX_EUNSUPPORTED_N", -3: "SEMAX_EALIGN",
+    -4: "SEMAX_EALIAS", -5: "SEMAX_ECUDA", -6: "SEMAX_ETIMEOUT", -7: "SEMAX_ENOPLAN",
+    -8: "SEMAX_EWORKSPACE", -9: "SEMAX_EIO",
+}
+
+# every symbol include/semax.h declares
+EXPORTS = (
+    "sem_ax", "sem_ax_f32", "sem_ax_bf16x3",
+    "sem_ax_batched_workspace_size", "sem_ax_batched",
+    "sem_ax_plan_create", "sem_ax_plan_exec", "sem_ax_plan_destroy", "sem_ax_plan_config",
+    "semax_reduce_workspace_size", "semax_reduce",
+    "semax_strerror", "semax_last_cuda_error",
+)
+
+
+class SemaxError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.semax_strerror(status).decode() if _lib is not None else ""
+        cuda = f" (cudaError {_lib.semax_last_cuda_error()})" if status == -5 and _lib is not None else ""
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}{cuda}")
+
+
+class semax_group(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("E", ctypes.c_int64), ("u", ctypes.c_void_p),
+                ("G", ctypes.c_void_p), ("D", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsemax is not built ({LIB_PATH} missing); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(LIB_PATH)
+    i64, i32, vp, sz = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+    sig = {
+        "sem_ax": [i64, i32, vp, vp, vp, vp, vp],
+        "sem_ax_f32": [i64, i32, vp, vp, vp, vp, vp, vp],
+        "sem_ax_bf16x3": [i64, i32, vp, vp, vp, vp, vp, i32, vp],
+        "sem_ax_batched_workspace_size": [vp, i32, ctypes.POINTER(sz)],
+        "sem_ax_batched": [vp, i32, vp, sz, vp],
+        "sem_ax_plan_create": [ctypes.POINTER(vp), vp, i32, i32, ctypes.c_char_p],
+        "sem_ax_plan_exec": [vp, vp],
+        "sem_ax_plan_destroy": [vp],
+        "sem_ax_plan_config": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "semax_reduce_workspace_size": [i64, ctypes.POINTER(sz)],
+        "semax_reduce": [i64, vp, i32, vp, i32, vp, vp, sz, vp],
+        "semax_strerror": [i32],
+        "semax_last_cuda_error": [],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)  # raises AttributeError if the library lacks a declared symbol
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "semax_strerror" else ctypes.c_int
+    return lib
+
+
+_lib = None
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def check(status: int, where: str) -> None:
+    if status != SEMAX_OK:
+        raise SemaxError(status, where)

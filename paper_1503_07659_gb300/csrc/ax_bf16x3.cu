@@ -1,0 +1,383 @@
+// Ax with FP32 storage and the six derivative contractions on tensor cores:
+// every FP32 operand x is split into BF16 pieces x0 = bf16(x),
+// x1 = bf16(x - x0) (, x2 = bf16(x - x0 - x1)), and a product x*y is formed
+// from the piece products with index sum <= NP-1 (3 products for NP = 2,
+// 6 for NP = 3), accumulated in FP32 by mma.m16n8k16.  The geometric-factor
+// multiply runs in FP32.  Order n = 16 (N = 15).
+//
+// Each contraction is a dense (16 x 16) x (16 x 16) product per plane of the
+// element (the (n x n) x (n x n^2) form); the paper's Section 5.2 blocks a
+// matrix-matrix product with on-chip prefetch of both operand tiles, which is
+// the prior art for staging u_e and the intermediates here.
+//
+// Per element, one CTA of 8 warps:
+//   load   u (FP32, 128-bit loads) -> BF16 pieces in shared memory (XOR
+//          swizzled so that every ldmatrix and fragment store is free of bank
+//          conflicts along both the j and the k axis);
+//   pass T ut = D (x) I (x) I u: warp w owns rows j = 2w, 2w+1, output
+//          tile (k x i); ut -> FP32 shared buffer W;
+//   pass P warp w owns planes k = 2w, 2w+1, output tile (j x i):
+//          ur = u_k D^T and us = D u_k on tensor cores, ut read from W, G
+//          loaded from global memory, [wr ws wt] = G [ur us ut] in FP32;
+//          wt -> BF16 pieces in shared memory; wr re-enters as an A operand
+//          directly from the accumulator registers; ws as a B operand after a
+//          movmatrix transpose; w_rs = wr D + D^T ws -> W (same plane);
+//   pass T' warp w owns rows j again: w_t = D^T (x) I (x) I wt on tensor cores,
+//          w = (w_rs + w_t) * s_e, stored to global memory.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace semax {
+namespace tc {
+
+constexpr int kN = 16;
+constexpr int kThreads = 256;
+constexpr int kPieceBytes = 4096 * 2;      // one BF16 copy of an element
+constexpr int kWRow = 24, kWPlane = 392;   // padded FP32 plane (words)
+constexpr int kWBytes = kN * kWPlane * 4;
+
+// byte offset of BF16 element (k, j, i) inside one piece buffer
+__device__ __forceinline__ uint32_t swz(int k, int j, int i) {
+    const int c = i >> 3;
+    const int line = (k << 2) | (j >> 2);
+    const int local = ((j & 3) << 1) | c;
+    const int s = (k & 7) ^ ((j >> 2) & 1);
+    return (uint32_t)((((line << 3) | (local ^ s)) << 4) + ((i & 7) << 1));
+}
+
+__device__ __forceinline__ int widx(int k, int j, int i) { return k * kWPlane + j * kWRow + i; }
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t a, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t a, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+__device__ __forceinline__ uint32_t movm_t(uint32_t x) {
+    uint32_t y;
+    asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;\n" : "=r"(y) : "r"(x));
+    return y;
+}
+__device__ __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t *>(&h); }
+
+// Split the pair (x, y) into NP BF16 pieces, packed (x in the low half).
+template <int NP>
+__device__ __forceinline__ void split2(float x, float y, uint32_t (&out)[NP]) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+        out[p] = pack(h);
+        x -= __low2float(h);
+        y -= __high2float(h);
+    }
+}
+
+// piece p of a scalar (for the constant D fragments)
+template <int NP>
+__device__ __forceinline__ uint32_t piece_pair(float x, float y, int p) {
+    uint32_t o[NP];
+    split2<NP>(x, y, o);
+    uint32_t r = o[0];
+#pragma unroll
+    for (int q = 1; q < NP; ++q)
+        if (q == p) r = o[q];
+    return r;
+}
+
+// acc += sum over piece pairs (pa, pb), pa + pb <= NP - 1, smallest first
+template <int NP>
+__device__ __forceinline__ void mma_split(float (&c)[4], const uint32_t (&a)[NP][4],
+                                          const uint32_t (&b)[NP][2]) {
+#pragma unroll
+    for (int s = NP - 1; s >= 0; --s)
+#pragma unroll
+        for (int pa = s; pa >= 0; --pa) {
+            const int pb = s - pa;
+            mma(c, a[pa], b[pb][0], b[pb][1]);
+        }
+}
+
+template <int NP>
+struct DFrag {
+    uint32_t AD[NP][4];      // A(r, c) = D[r][c]
+    uint32_t ADt[NP][4];     // A(r, c) = D[c][r]
+    uint32_t BD[NP][2][2];   // B(l, i) = D[i][l], per n-tile
+    uint32_t BDt[NP][2][2];  // B(l, i) = D[l][i], per n-tile
+};
+
+template <int NP>
+__device__ __forceinline__ void load_dfrag(const float *__restrict__ D, DFrag<NP> &f) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    auto d = [&](int r, int c) { return D[r * kN + c]; };
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        f.AD[p][0] = piece_pair<NP>(d(g, 2 * t), d(g, 2 * t + 1), p);
+        f.AD[p][1] = piece_pair<NP>(d(g + 8, 2 * t), d(g + 8, 2 * t + 1), p);
+        f.AD[p][2] = piece_pair<NP>(d(g, 2 * t + 8), d(g, 2 * t + 9), p);
+        f.AD[p][3] = piece_pair<NP>(d(g + 8, 2 * t + 8), d(g + 8, 2 * t + 9), p);
+        f.ADt[p][0] = piece_pair<NP>(d(2 * t, g), d(2 * t + 1, g), p);
+        f.ADt[p][1] = piece_pair<NP>(d(2 * t, g + 8), d(2 * t + 1, g + 8), p);
+        f.ADt[p][2] = piece_pair<NP>(d(2 * t + 8, g), d(2 * t + 9, g), p);
+        f.ADt[p][3] = piece_pair<NP>(d(2 * t + 8, g + 8), d(2 * t + 9, g + 8), p);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int i = g + 8 * nt;
+            f.BD[p][nt][0] = piece_pair<NP>(d(i, 2 * t), d(i, 2 * t + 1), p);
+            f.BD[p][nt][1] = piece_pair<NP>(d(i, 2 * t + 8), d(i, 2 * t + 9), p);
+            f.BDt[p][nt][0] = piece_pair<NP>(d(2 * t, i), d(2 * t + 1, i), p);
+            f.BDt[p][nt][1] = piece_pair<NP>(d(2 * t + 8, i), d(2 * t + 9, i), p);
+        }
+    }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads, 2)
+ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__ G,
+               const float *__restrict__ D, float *__restrict__ w, const float *__restrict__ scale) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *upc = smem;                                // NP pieces of u
+    unsigned char *wpc = smem + NP * kPieceBytes;             // NP pieces of wt
+    float *W = reinterpret_cast<float *>(smem + 2 * NP * kPieceBytes);
+    const uint32_t upc_s = smem_addr(upc), wpc_s = smem_addr(wpc);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int lm = lane >> 3, lr = lane & 7;  // ldmatrix: matrix id, row id
+
+    DFrag<NP> f;
+    load_dfrag<NP>(D, f);
+
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const float *ue = u + e * 4096;
+        const float *Ge = G + e * 6 * 4096;
+        float *we = w + e * 4096;
+
+        // ---- load u, split into pieces
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            const int q = tid + it * kThreads;  // float4 index, 0..1023
+            const float4 v = ld_stream4(reinterpret_cast<const float4 *>(ue) + q);
+            const int k = q >> 6, j = (q >> 2) & 15, i = (q & 3) << 2;
+            uint32_t lo[NP], hi[NP];
+            split2<NP>(v.x, v.y, lo);
+            split2<NP>(v.z, v.w, hi);
+            const uint32_t off = swz(k, j, i);
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+                *reinterpret_cast<uint2 *>(upc + p * kPieceBytes + off) = make_uint2(lo[p], hi[p]);
+        }
+        __syncthreads();
+
+        // ---- pass T: ut[k][j][i] = sum_l D[k][l] u[l][j][i]
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            const int j = 2 * warp + jj;
+            uint32_t b[NP][4];
+            const uint32_t a_off = swz(lr + 8 * (lm & 1), j, 8 * (lm >> 1));
+#pragma unroll
+            for (int p = 0; p < NP; ++p) ldsm_x4_t(upc_s + p * kPieceBytes + a_off, b[p]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                uint32_t bb[NP][2];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) { bb[p][0] = b[p][2 * nt]; bb[p][1] = b[p][2 * nt + 1]; }
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_split<NP>(c, f.AD, bb);
+                const int i = 8 * nt + 2 * t;
+                *reinterpret_cast<float2 *>(W + widx(g, j, i)) = make_float2(c[0], c[1]);
+                *reinterpret_cast<float2 *>(W + widx(g + 8, j, i)) = make_float2(c[2], c[3]);
+            }
+        }
+        __syncthreads();
+
+        // ---- pass P: planes k = 2*warp, 2*warp+1
+#pragma unroll 1
+        for (int kk = 0; kk < 2; ++kk) {
+            const int k = 2 * warp + kk;
+            // geometric factors of this thread's 8 nodes (2 n-tiles x 2 row halves)
+            float2 gv[6][2][2];
+#pragma unroll
+            for (int comp = 0; comp < 6; ++comp)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float *p = Ge + comp * 4096 + k * 256 + (g + 8 * h) * 16 + 8 * nt + 2 * t;
+                        float2 v;
+                        asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0,%1}, [%2];"
+                                     : "=f"(v.x), "=f"(v.y) : "l"(p));
+                        gv[comp][nt][h] = v;
+                    }
+            uint32_t au[NP][4], bu[NP][4];
+            const uint32_t off = swz(k, lr + 8 * (lm & 1), 8 * (lm >> 1));
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                ldsm_x4(upc_s + p * kPieceBytes + off, au[p]);
+                ldsm_x4_t(upc_s + p * kPieceBytes + off, bu[p]);
+            }
+            float wacc[2][4];
+            uint32_t awr[NP][4];   // wr as A operand (C -> A reuse)
+            uint32_t bws[NP][2][2];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                float ur[4] = {0.f, 0.f, 0.f, 0.f}, us[4] = {0.f, 0.f, 0.f, 0.f};
+                uint32_t bd[NP][2], bb[NP][2];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    bd[p][0] = f.BD[p][nt][0];
+                    bd[p][1] = f.BD[p][nt][1];
+                    bb[p][0] = bu[p][2 * nt];
+                    bb[p][1] = bu[p][2 * nt + 1];
+                }
+                // ur: A = u_k (rows j, cols l), B = D^T; us: A = D, B = u_k (rows l, cols i)
+#pragma unroll
+                for (int s = NP - 1; s >= 0; --s)
+#pragma unroll
+                    for (int pa = s; pa >= 0; --pa) mma(ur, au[s - pa], bd[pa][0], bd[pa][1]);
+                mma_split<NP>(us, f.AD, bb);
+                const int i = 8 * nt + 2 * t;
+                float wr[4], ws[4], wt[4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 ut2 = *reinterpret_cast<const float2 *>(W + widx(k, g + 8 * h, i));
+                    const float utv[2] = {ut2.x, ut2.y};
+#pragma unroll
+                    for (int x = 0; x < 2; ++x) {
+                        const int q = 2 * h + x;
+                        const float grr = x ? gv[0][nt][h].y : gv[0][nt][h].x;
+                        const float grs = x ? gv[1][nt][h].y : gv[1][nt][h].x;
+                        const float grt = x ? gv[2][nt][h].y : gv[2][nt][h].x;
+                        const float gss = x ? gv[3][nt][h].y : gv[3][nt][h].x;
+                        const float gst = x ? gv[4][nt][h].y : gv[4][nt][h].x;
+                        const float gtt = x ? gv[5][nt][h].y : gv[5][nt][h].x;
+                        const float r = ur[q], s = us[q], tt = utv[x];
+                        wr[q] = __fmaf_rn(grt, tt, __fmaf_rn(grs, s, grr * r));
+                        ws[q] = __fmaf_rn(gst, tt, __fmaf_rn(gss, s, grs * r));
+                        wt[q] = __fmaf_rn(gtt, tt, __fmaf_rn(gst, s, grt * r));
+                    }
+                }
+                // wt pieces -> shared (for pass T')
+                uint32_t p0[NP], p1[NP];
+                split2<NP>(wt[0], wt[1], p0);
+                split2<NP>(wt[2], wt[3], p1);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    *reinterpret_cast<uint32_t *>(wpc + p * kPieceBytes + swz(k, g, i)) = p0[p];
+                    *reinterpret_cast<uint32_t *>(wpc + p * kPieceBytes + swz(k, g + 8, i)) = p1[p];
+                }
+                // wr pieces as A fragment columns 8*nt..8*nt+7
+                split2<NP>(wr[0], wr[1], p0);
+                split2<NP>(wr[2], wr[3], p1);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    awr[p][2 * nt] = p0[p];
+                    awr[p][2 * nt + 1] = p1[p];
+                }
+                // ws pieces, transposed 8x8 blocks -> B fragment of n-tile nt
+                split2<NP>(ws[0], ws[1], p0);
+                split2<NP>(ws[2], ws[3], p1);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    bws[p][nt][0] = movm_t(p0[p]);
+                    bws[p][nt][1] = movm_t(p1[p]);
+                }
+            }
+            // w_rs = wr D + D^T ws
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                wacc[nt][0] = wacc[nt][1] = wacc[nt][2] = wacc[nt][3] = 0.f;
+                uint32_t bdt[NP][2], bw[NP][2];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    bdt[p][0] = f.BDt[p][nt][0];
+                    bdt[p][1] = f.BDt[p][nt][1];
+                    bw[p][0] = bws[p][nt][0];
+                    bw[p][1] = bws[p][nt][1];
+                }
+                mma_split<NP>(wacc[nt], awr, bdt);
+                mma_split<NP>(wacc[nt], f.ADt, bw);
+                const int i = 8 * nt + 2 * t;
+                *reinterpret_cast<float2 *>(W + widx(k, g, i)) = make_float2(wacc[nt][0], wacc[nt][1]);
+                *reinterpret_cast<float2 *>(W + widx(k, g + 8, i)) = make_float2(wacc[nt][2], wacc[nt][3]);
+            }
+        }
+        __syncthreads();
+
+        // ---- pass T': w += sum_l D[l][k] wt[l][j][i]; store
+        const float sc = scale ? scale[e] : 1.f;
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            const int j = 2 * warp + jj;
+            uint32_t b[NP][4];
+            const uint32_t a_off = swz(lr + 8 * (lm & 1), j, 8 * (lm >> 1));
+#pragma unroll
+            for (int p = 0; p < NP; ++p) ldsm_x4_t(wpc_s + p * kPieceBytes + a_off, b[p]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                uint32_t bb[NP][2];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) { bb[p][0] = b[p][2 * nt]; bb[p][1] = b[p][2 * nt + 1]; }
+                float c[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_split<NP>(c, f.ADt, bb);
+                const int i = 8 * nt + 2 * t;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = g + 8 * h;
+                    const float2 prev = *reinterpret_cast<const float2 *>(W + widx(k, j, i));
+                    float2 out = make_float2((prev.x + c[2 * h]) * sc, (prev.y + c[2 * h + 1]) * sc);
+                    *reinterpret_cast<float2 *>(we + k * 256 + j * 16 + i) = out;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int NP>
+static int launch(int64_t E, const float *u, const float *G, const float *D, float *w, const float *scale,
+                  cudaStream_t s) {
+    const size_t smem = 2 * NP * kPieceBytes + kWBytes;
+    auto kern = ax_bf16_kernel<NP>;
+    int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (st != SEMAX_OK) return st;
+    int per_sm = 0;
+    st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    if (st != SEMAX_OK) return st;
+    if (per_sm < 1) return SEMAX_EINVAL;
+    int64_t grid = (int64_t)per_sm * device_sm_count();
+    if (grid > E) grid = E;
+    kern<<<(unsigned)grid, kThreads, smem, s>>>(E, u, G, D, w, scale);
+    return launch_status();
+}
+
+}  // namespace tc
+}  // namespace semax
+
+using namespace semax;
+
+extern "C" int sem_ax_bf16x3(int64_t E, int N, const float *u, const float *G, const float *D, float *w,
+                             const float *G_scale, int terms, void *stream) {
+    if (terms != 3 && terms != 6) return SEMAX_EINVAL;
+    int st = check_args(E, N, u, G, D, w);
+    if (st != SEMAX_OK || E == 0) return st;
+    if (N != 15) return SEMAX_EUNSUPPORTED_N;
+    if (G_scale && overlaps(w, (size_t)E * 4096 * sizeof(float), G_scale, (size_t)E * sizeof(float)))
+        return SEMAX_EALIAS;
+    if (terms == 3) return tc::launch<2>(E, u, G, D, w, G_scale, (cudaStream_t)stream);
+    return tc::launch<3>(E, u, G, D, w, G_scale, (cudaStream_t)stream);
+}

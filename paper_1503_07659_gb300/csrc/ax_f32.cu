@@ -1,0 +1,7 @@
+// FP32 instantiation of the plain Ax kernels.
+#include "ax_plain.cuh"
+
+namespace semax {
+template int launch_plain<float>(int64_t, int, const TileConfig &, const float *, const float *,
+                                 const float *, float *, const float *, cudaStream_t);
+}  // namespace semax

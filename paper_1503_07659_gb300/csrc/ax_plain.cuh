@@ -1,0 +1,86 @@
+// Plain (one order per launch) Ax kernels, FP64 and FP32 CUDA-core forms.
+#pragma once
+
+#include "ax_tile.cuh"
+
+namespace semax {
+
+struct TileConfig {
+    int epb;   // elements per CTA tile
+    int map;   // MAP_NODE or MAP_COLUMN
+    int threads;
+};
+
+// Default tile shape: about 256 threads, one (i,j) column per thread.
+inline TileConfig default_tile(int n) {
+    TileConfig c;
+    c.map = MAP_COLUMN;
+    c.epb = 256 / (n * n) > 0 ? 256 / (n * n) : 1;
+    c.threads = round_up(c.epb * n * n, 32);
+    return c;
+}
+
+template <typename T, int n, int MAP>
+__global__ void __launch_bounds__(256)
+ax_plain_kernel(int64_t E, int epb, const T *__restrict__ u, const T *__restrict__ G,
+                const T *__restrict__ D, T *__restrict__ w, const T *__restrict__ scale) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int n3 = n * n * n;
+    T *sD = reinterpret_cast<T *>(smem_raw);
+    T *buf = sD + d_slots<T>(n);
+    const int64_t e0 = (int64_t)blockIdx.x * epb;
+    const int cnt = (int)(E - e0 < epb ? E - e0 : epb);
+    load_D<T, n>(D, sD);
+    ax_tile<T, n, MAP>(cnt, u + e0 * n3, G + e0 * 6 * n3, w + e0 * n3,
+                       scale ? scale + e0 : nullptr, sD, buf);
+}
+
+template <typename T, int n, int MAP>
+int launch_plain_nm(int64_t E, const TileConfig &c, const T *u, const T *G, const T *D, T *w,
+                    const T *scale, cudaStream_t s) {
+    auto kern = ax_plain_kernel<T, n, MAP>;
+    const size_t smem = tile_smem_bytes<T>(n, c.epb, MAP);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    const int64_t tiles = (E + c.epb - 1) / c.epb;
+    if (tiles > 0x7fffffffLL) return SEMAX_EINVAL;
+    kern<<<(unsigned)tiles, c.threads, smem, s>>>(E, c.epb, u, G, D, w, scale);
+    return launch_status();
+}
+
+template <typename T, int n>
+int launch_plain_n(int64_t E, const TileConfig &c, const T *u, const T *G, const T *D, T *w,
+                   const T *scale, cudaStream_t s) {
+    if (c.epb < 1 || c.threads < 32 || c.threads > 256 || (c.threads & 31)) return SEMAX_EINVAL;
+    if (c.map == MAP_COLUMN) {
+        if (c.epb * n * n > c.threads) return SEMAX_EINVAL;
+        return launch_plain_nm<T, n, MAP_COLUMN>(E, c, u, G, D, w, scale, s);
+    }
+    return launch_plain_nm<T, n, MAP_NODE>(E, c, u, G, D, w, scale, s);
+}
+
+template <typename T>
+int launch_plain(int64_t E, int N, const TileConfig &c, const T *u, const T *G, const T *D, T *w,
+                 const T *scale, cudaStream_t s) {
+    switch (N + 1) {
+#define SEMAX_CASE(nn) \
+    case nn: return launch_plain_n<T, nn>(E, c, u, G, D, w, scale, s);
+        SEMAX_CASE(2) SEMAX_CASE(3) SEMAX_CASE(4) SEMAX_CASE(5) SEMAX_CASE(6) SEMAX_CASE(7)
+        SEMAX_CASE(8) SEMAX_CASE(9) SEMAX_CASE(10) SEMAX_CASE(11) SEMAX_CASE(12) SEMAX_CASE(13)
+        SEMAX_CASE(14) SEMAX_CASE(15) SEMAX_CASE(16)
+#undef SEMAX_CASE
+        default: return SEMAX_EUNSUPPORTED_N;
+    }
+}
+
+// Explicit instantiations live in ax_f64.cu / ax_f32.cu.
+extern template int launch_plain<double>(int64_t, int, const TileConfig &, const double *,
+                                         const double *, const double *, double *,
+                                         const double *, cudaStream_t);
+extern template int launch_plain<float>(int64_t, int, const TileConfig &, const float *,
+                                        const float *, const float *, float *, const float *,
+                                        cudaStream_t);
+
+}  // namespace semax

@@ -1,0 +1,92 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads,
+exports every symbol include/semax.h declares, and rejects bad arguments on
+the host before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1503_07659_gb300 import build as b
+    b.build()
+    import paper_1503_07659_gb300._lib as L
+    return L.lib()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "semax.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"^\s*(?:int|const char \*|size_t)\s*\**\s*([a-z_0-9]+)\s*\(", text, flags=re.M))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_1503_07659_gb300._lib as L
+    declared = _declared()
+    assert declared == set(L.EXPORTS), declared ^ set(L.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_strerror_covers_every_status(lib):
+    for st in range(0, -10, -1):
+        assert lib.semax_strerror(st) not in (None, b"unknown status")
+
+
+# fake device addresses: argument checks run before any CUDA call
+A = 1 << 40
+
+
+@pytest.mark.parametrize("fn", ["sem_ax", "sem_ax_f32", "sem_ax_bf16x3"])
+def test_argument_validation(lib, fn):
+    f = getattr(lib, fn)
+
+    def call(E, N, u=A, G=A + (1 << 32), D=A + (2 << 32), w=A + (3 << 32)):
+        extra = {"sem_ax": (), "sem_ax_f32": (None,), "sem_ax_bf16x3": (None, 3)}[fn]
+        return f(E, N, u, G, D, w, *extra, None)
+
+    assert call(0, 7) == 0                      # empty: no-op, nothing inspected
+    assert call(0, 7, None, None, None, None) == 0
+    assert call(-1, 7) == -1                    # EINVAL
+    assert call(4, 0) == -2 and call(4, 16) == -2   # EUNSUPPORTED_N
+    assert call(4, 7, u=None) == -1
+    assert call(4, 7, w=None) == -1
+    assert call(4, 7, u=A + 8) == -3            # EALIGN
+    assert call(4, 7, G=A + (1 << 32) + 4) == -3
+    assert call(4, 7, w=A + 256) == -4          # EALIAS: w overlaps u
+    assert call(4, 7, D=A + (3 << 32) + 64) == -4   # w overlaps D
+
+
+def test_bf16_rejects_bad_terms(lib):
+    assert lib.sem_ax_bf16x3(4, 15, A, A + (1 << 32), A + (2 << 32), A + (3 << 32), None, 4, None) == -1
+
+
+def test_batched_validation_and_workspace_size(lib):
+    import paper_1503_07659_gb300._lib as L
+    g = (L.semax_group * 2)()
+    g[0] = L.semax_group(7, 10, A, A + (1 << 32), A + (2 << 32), A + (3 << 32))
+    g[1] = L.semax_group(3, 10, A + (4 << 32), A + (5 << 32), A + (6 << 32), A + (7 << 32))
+    size = ctypes.c_size_t(0)
+    assert lib.sem_ax_batched_workspace_size(g, 2, ctypes.byref(size)) == 0 and size.value >= 8
+    assert lib.sem_ax_batched(g, 2, None, 0, None) == -8          # EWORKSPACE
+    g[1].w = A + (3 << 32) + 64                                   # two outputs overlap
+    assert lib.sem_ax_batched_workspace_size(g, 2, ctypes.byref(size)) == -4
+    g[1].w = A + (7 << 32)
+    g[1].N = 20
+    assert lib.sem_ax_batched(g, 2, A + (9 << 32), 4096, None) == -2
+    assert lib.sem_ax_batched_workspace_size(g, 40, ctypes.byref(size)) == -1   # too many groups
+    plan = ctypes.c_void_p()
+    assert lib.sem_ax_plan_create(ctypes.byref(plan), g, 2, 0, None) == -2
+    assert lib.sem_ax_plan_exec(None, None) == -7 and lib.sem_ax_plan_destroy(None) == -7
+
+
+def test_reduce_validation(lib):
+    size = ctypes.c_size_t(0)
+    assert lib.semax_reduce_workspace_size(10 ** 9, ctypes.byref(size)) == 0 and size.value >= 24
+    assert lib.semax_reduce_workspace_size(-1, ctypes.byref(size)) == -1
+    assert lib.semax_reduce(100, A, 0, A + 4096, 2, A + 8192, A + 16384, 1 << 20, None) == -1  # bad prec
+    assert lib.semax_reduce(100, A, 0, A + 4096, 0, A + 8192, None, 0, None) == -8

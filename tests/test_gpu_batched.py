@@ -1,0 +1,107 @@
+"""GPU tests of the batched (uneven-order, one persistent launch) form, its
+graph-captured plans and tuner, and the FP64 reducer."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import sem_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def semax():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1503_07659_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def mix():
+    """The uneven-order workload (~4.19M nodes, N in {3,5,7,9,11,15}) on the GPU."""
+    return si.make_workload(3, device="cuda")
+
+
+def _groups(meshes, ws):
+    return [(m.N, m.u, m.G, m.D, w) for m, w in zip(meshes, ws)]
+
+
+def test_batched_equals_per_order_plain_launches(semax, mix):
+    plain = [semax.sem_ax(m.u, m.G, m.D) for m in mix]
+    ws = [torch.full_like(m.u, float("nan")) for m in mix]
+    semax.sem_ax_batched(_groups(mix, ws))
+    torch.cuda.synchronize()
+    for m, a, b in zip(mix, plain, ws):
+        assert torch.equal(a, b), m.N      # same tile arithmetic: bit-identical
+
+
+def test_batched_against_oracle_sampled(semax, mix, oracle_mod):
+    ws = [torch.empty_like(m.u) for m in mix]
+    semax.sem_ax_batched(_groups(mix, ws))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(13)
+    for m, w in zip(mix, ws):
+        idx = np.sort(rng.choice(m.E, size=min(m.E, 40), replace=False))
+        it = torch.from_numpy(idx).cuda()
+        ref = oracle_mod.sem_ax(m.u[it].cpu(), m.G[it].cpu(), m.D.cpu())
+        err = np.max(np.abs(w[it].cpu().numpy() - ref)) / np.max(np.abs(ref))
+        assert err <= 1e-12, (m.N, err)
+
+
+def test_batched_ragged_small_groups(semax, oracle_mod):
+    rng = np.random.default_rng(21)
+    meshes = [si.make_mesh(rng, E, N, device="cuda") for N, E in [(1, 3), (4, 1), (15, 2), (6, 11), (4, 5)]]
+    ws = [torch.empty_like(m.u) for m in meshes]
+    semax.sem_ax_batched(_groups(meshes, ws))
+    torch.cuda.synchronize()
+    for m, w in zip(meshes, ws):
+        ref = oracle_mod.sem_ax(m.u.cpu(), m.G.cpu(), m.D.cpu())
+        assert np.max(np.abs(w.cpu().numpy() - ref)) / np.max(np.abs(ref)) <= 1e-12
+
+
+def test_plan_graph_and_tuner_cache(semax, mix, tmp_path):
+    plain = [semax.sem_ax(m.u, m.G, m.D) for m in mix]
+    cache = tmp_path / "tune.json"
+    ws = [torch.empty_like(m.u) for m in mix]
+    tuned = semax.Plan(_groups(mix, ws), tune=True, cache_path=str(cache))
+    data = json.loads(cache.read_text())
+    assert {e["N"] for e in data["entries"]} == {m.N for m in mix}
+    for w in ws:
+        w.fill_(float("nan"))
+    tuned()
+    tuned()                      # the graph can be replayed
+    torch.cuda.synchronize()
+    for m, a, b in zip(mix, plain, ws):
+        assert torch.equal(a, b), m.N
+    # a second plan reads the cache and makes the same choices
+    again = semax.Plan(_groups(mix, ws), tune=False, cache_path=str(cache))
+    for e in data["entries"]:
+        assert again.config(e["N"]) == (e["epb"], e["map"]) == tuned.config(e["N"])
+    tuned.close()
+    again.close()
+
+
+@pytest.mark.parametrize("count", [1, 1000, 3 * 1024 * 1024 + 7])
+def test_reduce_against_definition(semax, oracle_mod, count):
+    g = torch.Generator(device="cpu").manual_seed(count)
+    a = (torch.rand(count, generator=g, dtype=torch.float64) - 0.5)
+    b = (torch.rand(count, generator=g, dtype=torch.float64) - 0.5)
+    mx, mb, dot = oracle_mod.reduce(a.numpy(), b.numpy())
+    out = semax.reduce(a.cuda(), b.cuda()).cpu().numpy()
+    assert out[0] == mx and out[1] == mb
+    assert abs(out[2] - dot) <= 1e-13 * max(1.0, float(np.sum(np.abs(a.numpy() * b.numpy()))))
+    out32 = semax.reduce(a.float().cuda(), b.cuda()).cpu().numpy()
+    mx32, _, _ = oracle_mod.reduce(a.float().double().numpy(), b.numpy())
+    assert out32[0] == mx32
+    again = semax.reduce(a.cuda(), b.cuda()).cpu().numpy()
+    assert np.array_equal(out, again)                # fixed partition: deterministic
+
+
+def test_reduce_propagates_nan(semax):
+    a = torch.zeros(5000, dtype=torch.float64, device="cuda")
+    a[1234] = float("nan")
+    out = semax.reduce(a, torch.zeros_like(a)).cpu().numpy()
+    assert np.isnan(out[0]) and np.isnan(out[2])
