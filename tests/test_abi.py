@@ -12,8 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_1503_07659_gb300 import build as b
-    b.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1503_07659_gb300._lib as L
     return L.lib()
 
