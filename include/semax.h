@@ -86,7 +86,9 @@ int sem_ax_f32(int64_t E, int N, const float *u, const float *G, const float *D,
  * x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1).  terms = 3 keeps
  * the products x0 y0 + x0 y1 + x1 y0 ("bf16x3", ~16 significant bits);
  * terms = 6 also keeps x0 y2 + x1 y1 + x2 y0 (~24 bits).  The geometric
- * factor multiply is FP32.  G_scale as in sem_ax_f32. */
+ * factor multiply is FP32.  G_scale as in sem_ax_f32.  Order N = 15 only
+ * (n = 16, one 16 x 16 tensor-core tile per plane); other orders return
+ * SEMAX_EUNSUPPORTED_N. */
 int sem_ax_bf16x3(int64_t E, int N, const float *u, const float *G, const float *D,
                   float *w, const float *G_scale, int terms, void *stream);
 
@@ -107,15 +109,17 @@ int sem_ax_batched_workspace_size(const semax_group *groups, int ngroups, size_t
 
 /* All groups in ONE persistent kernel launch: tiles of elements are handed out
  * longest-first (cost ~ n^4 per element) through a device work counter held
- * in `workspace` (device memory, >= the size above, caller-owned).  Queues a
- * small upload of the work list from host memory and the kernel; the host
- * buffers are copied before the call returns.  Tile sizes and thread mapping
- * use built-in defaults (see the plan API for tuned choices). */
+ * in `workspace` (device memory, >= the size above, caller-owned).  At most
+ * 32 groups (else SEMAX_EINVAL); the group table travels in the kernel
+ * parameters, so the call queues only a reset of the counter and the kernel,
+ * and `groups` may be reused as soon as it returns.  Calls sharing one
+ * workspace must not overlap on the GPU.  Tile sizes and thread mapping use
+ * built-in defaults (see the plan API for tuned choices). */
 int sem_ax_batched(const semax_group *groups, int ngroups, void *workspace,
                    size_t ws_bytes, void *stream);
 
-/* A plan owns a device work list and a captured CUDA graph that resets the
- * work counter and launches the persistent kernel.  Creating a plan
+/* A plan owns a device work counter and a captured CUDA graph that resets the
+ * counter and launches the persistent kernel.  Creating a plan
  * allocates device memory; executing it does not.
  *   tune = 0: use the tuning cache entry if present, else defaults;
  *   tune = 1: time the candidate (elements per tile, thread mapping) pairs for
