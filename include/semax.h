@@ -149,6 +149,27 @@ int semax_reduce_workspace_size(int64_t count, size_t *bytes);
 int semax_reduce(int64_t count, const void *a, int a_prec, const void *b, int b_prec,
                  double *out, void *workspace, size_t ws_bytes, void *stream);
 
+/* Same reduction as semax_reduce for callers that cannot allocate device
+ * memory (a legacy solver that owns every allocation and passes the library
+ * only its own arrays, or code where the allocator must not be called), so it
+ * takes no workspace.  The paper has no counterpart: this is a deployment
+ * convenience of this library.  Its per-block partials live in a file-scope
+ * device array of 1024 x 3 doubles (24 KiB) that every GPU which loads the
+ * library holds until the process exits.  The fixed partition of
+ * semax_reduce never needs more than those 1024 blocks, so every count >= 0
+ * fits and the result equals semax_reduce's bit for bit; a partition that
+ * needed more would be rejected with SEMAX_EWORKSPACE.  Nothing in the array
+ * has to start at zero (pass 1 writes every partial that pass 2 reads).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array and
+ * it keeps the last call's partials: calls that can overlap on the GPU (on
+ * different streams, or from several host threads) race on it and must be
+ * ordered by the caller.  No cudaMalloc, cudaFree or allocating library call
+ * is made. */
+int semax_reduce_noalloc(int64_t count, const void *a, int a_prec, const void *b, int b_prec,
+                         double *out, void *stream);
+
 /* ---------------------------------------------------------------- errors */
 
 const char *semax_strerror(int status);

@@ -26,7 +26,7 @@ EXPORTS = (
     "sem_ax", "sem_ax_f32", "sem_ax_bf16x3",
     "sem_ax_batched_workspace_size", "sem_ax_batched",
     "sem_ax_plan_create", "sem_ax_plan_exec", "sem_ax_plan_destroy", "sem_ax_plan_config",
-    "semax_reduce_workspace_size", "semax_reduce",
+    "semax_reduce_workspace_size", "semax_reduce", "semax_reduce_noalloc",
     "semax_strerror", "semax_last_cuda_error",
 )
 
@@ -62,6 +62,7 @@ def _load():
         "sem_ax_plan_config": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "semax_reduce_workspace_size": [i64, ctypes.POINTER(sz)],
         "semax_reduce": [i64, vp, i32, vp, i32, vp, vp, sz, vp],
+        "semax_reduce_noalloc": [i64, vp, i32, vp, i32, vp, vp],
         "semax_strerror": [i32],
         "semax_last_cuda_error": [],
     }

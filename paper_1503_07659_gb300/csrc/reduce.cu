@@ -110,3 +110,65 @@ extern "C" int semax_reduce(int64_t count, const void *a, int a_prec, const void
     if (a_prec == SEMAX_F64 && b_prec == SEMAX_F32) return launch_reduce<double, float>(count, a, b, out, part, blocks, s);
     return launch_reduce<float, float>(count, a, b, out, part, blocks, s);
 }
+
+// ---------------------------------------------------------------- no-allocation form
+//
+// Some callers cannot call cudaMalloc: a legacy Fortran or C solver that hands
+// the library only its own arrays (and owns every device allocation itself),
+// code running where the allocator must not be touched (inside a memory pool
+// owned by another runtime, a real-time loop that forbids allocation), or a
+// caller that has no spare buffer to lend.  semax_reduce_noalloc gives them the
+// same FP64 reduction without a workspace argument: its per-block partials live
+// in the file-scope array below, which every GPU that loads the library holds
+// until the process exits.
+
+namespace semax {
+
+// Partials of the fixed partition: at most kRedMaxBlocks blocks x 3 doubles
+// (24 KiB per device).
+constexpr int kNoAllocBlocks = kRedMaxBlocks;
+static __device__ __align__(256) double g_reduce_scratch[3 * kNoAllocBlocks];
+
+constexpr int kMaxDevices = 64;
+static double *g_scratch_ptr[kMaxDevices];   // device address per device ordinal, set up once
+
+// Device address of g_reduce_scratch on the current device.  In host code the
+// symbol names a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress, once per device with that device current.
+static int noalloc_scratch(double **out) {
+    int dev = 0;
+    int st = cuda_status(cudaGetDevice(&dev));
+    if (st != SEMAX_OK) return st;
+    if (dev < 0 || dev >= kMaxDevices) return SEMAX_EINVAL;
+    double *p = __atomic_load_n(&g_scratch_ptr[dev], __ATOMIC_ACQUIRE);
+    if (!p) {
+        void *addr = nullptr;
+        st = cuda_status(cudaGetSymbolAddress(&addr, g_reduce_scratch));
+        if (st != SEMAX_OK) return st;
+        p = static_cast<double *>(addr);
+        __atomic_store_n(&g_scratch_ptr[dev], p, __ATOMIC_RELEASE);
+    }
+    *out = p;
+    return SEMAX_OK;
+}
+
+}  // namespace semax
+
+extern "C" int semax_reduce_noalloc(int64_t count, const void *a, int a_prec, const void *b, int b_prec,
+                                    double *out, void *stream) {
+    if (count < 0 || !out) return SEMAX_EINVAL;
+    if ((a_prec != SEMAX_F64 && a_prec != SEMAX_F32) || (b_prec != SEMAX_F64 && b_prec != SEMAX_F32))
+        return SEMAX_EINVAL;
+    if (count > 0 && (!a || !b)) return SEMAX_EINVAL;
+    if ((uintptr_t)out & 7u) return SEMAX_EALIGN;
+    const int blocks = reduce_blocks(count);
+    if (blocks > kNoAllocBlocks) return SEMAX_EWORKSPACE;   // partials would not fit the static scratch
+    double *part = nullptr;
+    int st = noalloc_scratch(&part);
+    if (st != SEMAX_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (a_prec == SEMAX_F64 && b_prec == SEMAX_F64) return launch_reduce<double, double>(count, a, b, out, part, blocks, s);
+    if (a_prec == SEMAX_F32 && b_prec == SEMAX_F64) return launch_reduce<float, double>(count, a, b, out, part, blocks, s);
+    if (a_prec == SEMAX_F64 && b_prec == SEMAX_F32) return launch_reduce<double, float>(count, a, b, out, part, blocks, s);
+    return launch_reduce<float, float>(count, a, b, out, part, blocks, s);
+}
