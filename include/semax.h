@@ -133,7 +133,8 @@ int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, int ngroups
 int sem_ax_plan_exec(semax_plan *plan, void *stream);
 int sem_ax_plan_destroy(semax_plan *plan);
 /* The configuration the plan uses for order N: elements per tile and thread
- * mapping (0 = one thread per node, 1 = one thread per (i,j) column).
+ * mapping (0 = one thread per node, 1 = one thread per (i,j) column,
+ * 2 = one thread per line with the even/odd split of D, even n only).
  * Returns SEMAX_EINVAL if N is not in the plan. */
 int sem_ax_plan_config(const semax_plan *plan, int N, int *elems_per_tile, int *mapping);
 

@@ -11,12 +11,14 @@ struct TileConfig {
     int threads;
 };
 
-// Default tile shape: about 256 threads, one (i,j) column per thread.
+// Default tile shape: about 256 threads; even/odd lines for even n (the
+// GLL derivative is centro-antisymmetric), one (i,j) column per thread
+// otherwise.
 inline TileConfig default_tile(int n) {
     TileConfig c;
-    c.map = MAP_COLUMN;
+    c.map = (n % 2 == 0) ? MAP_EO : MAP_COLUMN;
     c.epb = 256 / (n * n) > 0 ? 256 / (n * n) : 1;
-    c.threads = round_up(c.epb * n * n, 32);
+    c.threads = c.map == MAP_EO ? 256 : round_up(c.epb * n * n, 32);
     return c;
 }
 
@@ -58,6 +60,7 @@ int launch_plain_n(int64_t E, const TileConfig &c, const T *u, const T *G, const
         if (c.epb * n * n > c.threads) return SEMAX_EINVAL;
         return launch_plain_nm<T, n, MAP_COLUMN>(E, c, u, G, D, w, scale, s);
     }
+    if (c.map == MAP_EO && n % 2 == 0) return launch_plain_nm<T, n, MAP_EO>(E, c, u, G, D, w, scale, s);
     return launch_plain_nm<T, n, MAP_NODE>(E, c, u, G, D, w, scale, s);
 }
 
