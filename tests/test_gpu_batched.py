@@ -113,16 +113,17 @@ def test_every_mapping_through_cached_plan(semax, oracle_mod, tmp_path, mapping)
     hand-written tuning cache and check the plan against the oracle."""
     rng = np.random.default_rng(31 + mapping)
     meshes = [si.make_mesh(rng, E, N, device="cuda") for N, E in [(3, 40), (4, 9), (7, 13), (15, 3)]]
-    dev = torch.cuda.get_device_name()
+    ws = [torch.empty_like(m.u) for m in meshes]
+    cache = tmp_path / "forced.json"
+    semax.Plan(_groups(meshes, ws), tune=True, cache_path=str(cache)).close()  # device name as the library reads it
+    dev = json.loads(cache.read_text())["device"]
     entries = []
     for m in meshes:
         n = m.N + 1
         mp = mapping if (mapping != 2 or n % 2 == 0) else 1
         epb = 1 if mp == 1 and n * n > 128 else 2
         entries.append(f'{{"N": {m.N}, "prec": "f64", "epb": {epb}, "map": {mp}, "us": 0.0}}')
-    cache = tmp_path / "forced.json"
     cache.write_text('{"device": "%s", "entries": [\n  %s\n]}\n' % (dev, ",\n  ".join(entries)))
-    ws = [torch.empty_like(m.u) for m in meshes]
     plan = semax.Plan(_groups(meshes, ws), tune=False, cache_path=str(cache))
     plan()
     torch.cuda.synchronize()
