@@ -22,8 +22,10 @@ inline TileConfig default_tile(int n) {
     return c;
 }
 
+// Up to n = 8 a tile fits three times in shared memory, so registers are
+// capped for three resident CTAs per SM.
 template <typename T, int n, int MAP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (n <= 8 ? 3 : 1))
 ax_plain_kernel(int64_t E, int epb, const T *__restrict__ u, const T *__restrict__ G,
                 const T *__restrict__ D, T *__restrict__ w, const T *__restrict__ scale) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -44,6 +46,9 @@ int launch_plain_nm(int64_t E, const TileConfig &c, const T *u, const T *G, cons
     const size_t smem = tile_smem_bytes<T>(n, c.epb, MAP);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return cuda_status(e);
     }
     const int64_t tiles = (E + c.epb - 1) / c.epb;

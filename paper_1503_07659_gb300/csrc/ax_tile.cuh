@@ -85,9 +85,9 @@ __device__ __forceinline__ void eo_line(const T *x, T *y, int stride, const T *_
         e[l] = a + b;
         o[l] = a - b;
     }
-    // full unroll keeps P and Q in registers across lines for h <= 4; larger
-    // blocks would not fit, so they are re-read from shared memory
-#pragma unroll(h <= 4 ? h : 1)
+    // P and Q are re-read from shared memory (broadcast) for every line: kept
+    // in registers they would cost 4 h^2 registers and halve the occupancy
+#pragma unroll 1
     for (int i = 0; i < h; ++i) {
         T pe = T(0), qo = T(0);
 #pragma unroll
@@ -150,17 +150,23 @@ __device__ __forceinline__ void tile_node_phases(int cnt, const T *__restrict__ 
     }
 }
 
-// Phases 2-5 of MAP_EO.  sPQ holds P, Q of D then P, Q of D^T.
+// Phases of MAP_EO after staging u.  sPQ holds P, Q of D then P, Q of D^T.
+//   1  r- and s-lines of the gradient -> sr, ss
+//   2  one thread per (i,j) column: the t-line of u -> st, then for each
+//      node of the column the geometric factor (G from global memory) in
+//      place, then the transposed t-line of wt in place.  Fusing the G loads
+//      into this pass spreads them among other warps' arithmetic.
+//   3  transposed r- and s-lines, in place
+//   4  w = r + s + t, one store
 template <typename T, int n>
 __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G, T *__restrict__ w,
                                                const T *__restrict__ scale, const T *__restrict__ sPQ,
                                                const T *su, T *sr, T *ss, T *st) {
     constexpr int n2 = n * n, n3 = n * n * n, h = n / 2;
     const int nodes = cnt * n3, lines = cnt * n2;
-    // gradient: one thread per line, all three directions
 #pragma unroll 1
-    for (int dir = 0; dir < 3; ++dir) {
-        T *out = dir == 0 ? sr : (dir == 1 ? ss : st);
+    for (int dir = 0; dir < 2; ++dir) {
+        T *out = dir == 0 ? sr : ss;
         for (int t = threadIdx.x; t < lines; t += blockDim.x) {
             const int e = t / n2;
             int base, stride;
@@ -169,20 +175,26 @@ __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G,
         }
     }
     __syncthreads();
-    // geometric factor, in place
-    for (int p = threadIdx.x; p < nodes; p += blockDim.x) {
-        const int e = p / n3, q = p - e * n3;
-        T wr, ws, wt;
-        geo_multiply(G + (size_t)e * 6 * n3 + q, n3, sr[p], ss[p], st[p], wr, ws, wt);
-        sr[p] = wr;
-        ss[p] = ws;
-        st[p] = wt;
+    for (int t = threadIdx.x; t < lines; t += blockDim.x) {
+        const int e = t / n2, ji = t - e * n2;
+        const int off = e * n3 + ji;
+        eo_line<T, n>(su + off, st + off, n2, sPQ, sPQ + h * h);          // ut
+        const T *Ge = G + (size_t)e * 6 * n3 + ji;
+#pragma unroll 2
+        for (int k = 0; k < n; ++k) {
+            const int q = off + k * n2;
+            T wr, ws, wt;
+            geo_multiply(Ge + k * n2, n3, sr[q], ss[q], st[q], wr, ws, wt);
+            sr[q] = wr;
+            ss[q] = ws;
+            st[q] = wt;
+        }
+        eo_line<T, n>(st + off, st + off, n2, sPQ + 2 * h * h, sPQ + 3 * h * h);   // transposed t
     }
     __syncthreads();
-    // transposed contractions, each line in place
 #pragma unroll 1
-    for (int dir = 0; dir < 3; ++dir) {
-        T *io = dir == 0 ? sr : (dir == 1 ? ss : st);
+    for (int dir = 0; dir < 2; ++dir) {
+        T *io = dir == 0 ? sr : ss;
         for (int t = threadIdx.x; t < lines; t += blockDim.x) {
             const int e = t / n2;
             int base, stride;
@@ -192,7 +204,6 @@ __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G,
         }
     }
     __syncthreads();
-    // sum of the three directions, one store
     for (int p = threadIdx.x; p < nodes; p += blockDim.x) {
         T acc = (sr[p] + ss[p]) + st[p];
         if (scale) acc *= scale[p / n3];

@@ -121,7 +121,7 @@ def test_every_mapping_through_cached_plan(semax, oracle_mod, tmp_path, mapping)
     for m in meshes:
         n = m.N + 1
         mp = mapping if (mapping != 2 or n % 2 == 0) else 1
-        epb = 1 if mp == 1 and n * n > 128 else 2
+        epb = 1 if n >= 12 else 2        # n = 16 tiles of 2 elements exceed shared memory
         entries.append(f'{{"N": {m.N}, "prec": "f64", "epb": {epb}, "map": {mp}, "us": 0.0}}')
     cache.write_text('{"device": "%s", "entries": [\n  %s\n]}\n' % (dev, ",\n  ".join(entries)))
     plan = semax.Plan(_groups(meshes, ws), tune=False, cache_path=str(cache))
