@@ -47,10 +47,15 @@ __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / 
 template <typename T>
 __host__ __device__ constexpr int d_slots(int n) { return round_up(2 * n * n, 16 / (int)sizeof(T)); }
 
-// Shared-memory footprint (bytes) of D plus one tile of `epb` elements.
+template <typename T>
+__host__ __device__ constexpr int eo_elem_pitch(int n);
+
+// Shared-memory footprint (bytes) of D plus one tile of `epb` elements: four
+// element buffers (u and the three directions), padded for MAP_EO.
 template <typename T>
 __host__ __device__ constexpr size_t tile_smem_bytes(int n, int epb, int map) {
-    return sizeof(T) * ((size_t)d_slots<T>(n) + (size_t)epb * n * n * n * 4);
+    return sizeof(T) * ((size_t)d_slots<T>(n) +
+                        (size_t)epb * 4 * (map == 2 && n % 2 == 0 ? eo_elem_pitch<T>(n) : n * n * n));
 }
 
 template <typename T>
@@ -69,44 +74,6 @@ __device__ __forceinline__ void geo_multiply(const T *__restrict__ Gq, int n3, T
     wr = fma_(grt, ut, fma_(grs, us, grr * ur));
     ws = fma_(gst, ut, fma_(gss, us, grs * ur));
     wt = fma_(gtt, ut, fma_(gst, us, grt * ur));
-}
-
-// y = M x for one line of n values by the even/odd split (see MAP_EO),
-// reading x from and writing y to shared memory (stride apart; in place is
-// allowed).  P and Q are the (n/2 x n/2) blocks of M, row-major.
-template <typename T, int n>
-__device__ __forceinline__ void eo_line(const T *x, T *y, int stride, const T *__restrict__ P,
-                                        const T *__restrict__ Q) {
-    constexpr int h = n / 2;
-    T e[h], o[h];
-#pragma unroll
-    for (int l = 0; l < h; ++l) {
-        const T a = x[l * stride], b = x[(n - 1 - l) * stride];
-        e[l] = a + b;
-        o[l] = a - b;
-    }
-    // P and Q are re-read from shared memory (broadcast) for every line: kept
-    // in registers they would cost 4 h^2 registers and halve the occupancy
-#pragma unroll 1
-    for (int i = 0; i < h; ++i) {
-        T pe = T(0), qo = T(0);
-#pragma unroll
-        for (int l = 0; l < h; ++l) {
-            pe = fma_(P[i * h + l], e[l], pe);
-            qo = fma_(Q[i * h + l], o[l], qo);
-        }
-        y[i * stride] = qo + pe;
-        y[(n - 1 - i) * stride] = qo - pe;
-    }
-}
-
-// Line `ab` of direction `dir` in an element's [k][j][i] block:
-// r: (k, j) = (a, b), stride 1; s: (k, i), stride n; t: (j, i), stride n^2.
-template <int n>
-__device__ __forceinline__ void line_of(int dir, int ab, int &base, int &stride) {
-    const int a = ab / n, b = ab - (ab / n) * n;
-    base = dir == 0 ? (a * n + b) * n : (dir == 1 ? a * n * n + b : a * n + b);
-    stride = dir == 0 ? 1 : (dir == 1 ? n : n * n);
 }
 
 // Phases 2-3 with one thread per node (MAP_NODE).
@@ -150,66 +117,11 @@ __device__ __forceinline__ void tile_node_phases(int cnt, const T *__restrict__ 
     }
 }
 
-// Phases of MAP_EO after staging u.  sPQ holds P, Q of D then P, Q of D^T.
-//   1  r- and s-lines of the gradient -> sr, ss
-//   2  one thread per (i,j) column: the t-line of u -> st, then for each
-//      node of the column the geometric factor (G from global memory) in
-//      place, then the transposed t-line of wt in place.  Fusing the G loads
-//      into this pass spreads them among other warps' arithmetic.
-//   3  transposed r- and s-lines, in place
-//   4  w = r + s + t, one store
-template <typename T, int n>
-__device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G, T *__restrict__ w,
-                                               const T *__restrict__ scale, const T *__restrict__ sPQ,
-                                               const T *su, T *sr, T *ss, T *st) {
-    constexpr int n2 = n * n, n3 = n * n * n, h = n / 2;
-    const int nodes = cnt * n3, lines = cnt * n2;
-#pragma unroll 1
-    for (int dir = 0; dir < 2; ++dir) {
-        T *out = dir == 0 ? sr : ss;
-        for (int t = threadIdx.x; t < lines; t += blockDim.x) {
-            const int e = t / n2;
-            int base, stride;
-            line_of<n>(dir, t - e * n2, base, stride);
-            eo_line<T, n>(su + e * n3 + base, out + e * n3 + base, stride, sPQ, sPQ + h * h);
-        }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < lines; t += blockDim.x) {
-        const int e = t / n2, ji = t - e * n2;
-        const int off = e * n3 + ji;
-        eo_line<T, n>(su + off, st + off, n2, sPQ, sPQ + h * h);          // ut
-        const T *Ge = G + (size_t)e * 6 * n3 + ji;
-#pragma unroll 2
-        for (int k = 0; k < n; ++k) {
-            const int q = off + k * n2;
-            T wr, ws, wt;
-            geo_multiply(Ge + k * n2, n3, sr[q], ss[q], st[q], wr, ws, wt);
-            sr[q] = wr;
-            ss[q] = ws;
-            st[q] = wt;
-        }
-        eo_line<T, n>(st + off, st + off, n2, sPQ + 2 * h * h, sPQ + 3 * h * h);   // transposed t
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int dir = 0; dir < 2; ++dir) {
-        T *io = dir == 0 ? sr : ss;
-        for (int t = threadIdx.x; t < lines; t += blockDim.x) {
-            const int e = t / n2;
-            int base, stride;
-            line_of<n>(dir, t - e * n2, base, stride);
-            T *xy = io + e * n3 + base;
-            eo_line<T, n>(xy, xy, stride, sPQ + 2 * h * h, sPQ + 3 * h * h);
-        }
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < nodes; p += blockDim.x) {
-        T acc = (sr[p] + ss[p]) + st[p];
-        if (scale) acc *= scale[p / n3];
-        w[p] = acc;
-    }
-}
+}  // namespace semax
+
+#include "ax_eo.cuh"
+
+namespace semax {
 
 // Tile routine.  sD holds D (n x n) already, with d_slots(n) slots reserved;
 // `buf` is the tile's shared scratch (tile_smem_bytes minus the D part).
@@ -220,15 +132,14 @@ __device__ __forceinline__ void ax_tile(int cnt, const T *__restrict__ u, const 
                                         T *__restrict__ sD, T *__restrict__ buf) {
     constexpr int n2 = n * n, n3 = n * n * n;
     const int nodes = cnt * n3;
-    T *su = buf;
-    T *sr = su + nodes;
-    T *ss = sr + nodes;
-    T *st = ss + nodes;
-    copy_to_smem(su, u, nodes);
-    __syncthreads();
-
     if constexpr (MAP == MAP_EO && n % 2 == 0) {
-        constexpr int h = n / 2;
+        constexpr int h = n / 2, EP = eo_elem_pitch<T>(n);
+        T *su = buf;
+        T *sr = su + cnt * EP;
+        T *ss = sr + cnt * EP;
+        T *st = ss + cnt * EP;
+        eo_stage<T, n>(su, u, cnt);
+        __syncthreads();   // D (loaded by the caller) and the staged u are visible
         int ok = 1;
         for (int q = threadIdx.x; q < n2; q += blockDim.x) {
             const int i = q / n, l = q - (q / n) * n;
@@ -249,8 +160,24 @@ __device__ __forceinline__ void ax_tile(int cnt, const T *__restrict__ u, const 
             tile_eo_phases<T, n>(cnt, G, w, scale, sPQ, su, sr, ss, st);
             return;
         }
+        // D is not centro-antisymmetric: dense staging and the node phases
+        su = buf;
+        sr = su + nodes;
+        ss = sr + nodes;
+        st = ss + nodes;
+        copy_to_smem(su, u, nodes);
+        __syncthreads();
         tile_node_phases<T, n>(cnt, G, w, scale, sD, su, sr, ss, st);
-    } else if constexpr (MAP == MAP_COLUMN) {
+        return;
+    }
+    T *su = buf;
+    T *sr = su + nodes;
+    T *ss = sr + nodes;
+    T *st = ss + nodes;
+    copy_to_smem(su, u, nodes);
+    __syncthreads();
+
+    if constexpr (MAP == MAP_COLUMN) {
         const int c = threadIdx.x;  // column id within the tile
         const bool active = c < cnt * n2;
         const int e = active ? c / n2 : 0, ji = c - e * n2;
