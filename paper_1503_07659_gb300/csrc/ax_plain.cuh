@@ -11,14 +11,25 @@ struct TileConfig {
     int threads;
 };
 
-// Default tile shape: about 256 threads; even/odd lines for even n (the
-// GLL derivative is centro-antisymmetric), one (i,j) column per thread
-// otherwise.
+// Default tile shapes, from a sweep of (mapping, elements per tile, block
+// size) on GB300: even n takes the even/odd line mapping (the GLL derivative
+// is centro-antisymmetric), FP64 with 256 threads and 256/n^2 elements per
+// tile, FP32 up to n = 8 with small 64-thread tiles (many resident CTAs hide
+// the load latency best) and one element per 256-thread tile above; odd n
+// takes one (i,j) column per thread.
+template <typename T>
 inline TileConfig default_tile(int n) {
     TileConfig c;
-    c.map = (n % 2 == 0) ? MAP_EO : MAP_COLUMN;
-    c.epb = 256 / (n * n) > 0 ? 256 / (n * n) : 1;
-    c.threads = c.map == MAP_EO ? 256 : round_up(c.epb * n * n, 32);
+    if (n % 2 == 0) {
+        c.map = MAP_EO;
+        const int threads = (sizeof(T) == 4 && n <= 8) ? 64 : 256;
+        c.threads = threads;
+        c.epb = threads / (n * n) > 0 ? threads / (n * n) : 1;
+    } else {
+        c.map = MAP_COLUMN;
+        c.epb = 256 / (n * n) > 0 ? 256 / (n * n) : 1;
+        c.threads = round_up(c.epb * n * n, 32);
+    }
     return c;
 }
 

@@ -109,7 +109,8 @@ static bool choice_valid(int n, TileChoice c) {
     return tile_smem_bytes<double>(n, c.epb, c.map) + sizeof(double) * 256 <= 200 * 1024;
 }
 
-// Same shape as the plain launch's default (so the two agree bit for bit).
+// Same mapping and elements per tile as the plain FP64 launch's default (so
+// the two agree bit for bit).
 static TileChoice default_choice(int n) {
     TileChoice c{std::max(1, kBatchThreads / (n * n)), n % 2 == 0 ? MAP_EO : MAP_COLUMN};
     return c;

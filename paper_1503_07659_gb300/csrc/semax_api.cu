@@ -25,7 +25,7 @@ extern "C" int sem_ax(int64_t E, int N, const double *u, const double *G, const 
                       double *w, void *stream) {
     int st = check_args(E, N, u, G, D, w);
     if (st != SEMAX_OK || E == 0) return st;
-    return launch_plain<double>(E, N, default_tile(N + 1), u, G, D, w, nullptr,
+    return launch_plain<double>(E, N, default_tile<double>(N + 1), u, G, D, w, nullptr,
                                 (cudaStream_t)stream);
 }
 
@@ -36,7 +36,7 @@ extern "C" int sem_ax_f32(int64_t E, int N, const float *u, const float *G, cons
     if (G_scale && overlaps(w, (size_t)E * (N + 1) * (N + 1) * (N + 1) * sizeof(float), G_scale,
                             (size_t)E * sizeof(float)))
         return SEMAX_EALIAS;
-    return launch_plain<float>(E, N, default_tile(N + 1), u, G, D, w, G_scale,
+    return launch_plain<float>(E, N, default_tile<float>(N + 1), u, G, D, w, G_scale,
                                (cudaStream_t)stream);
 }
 
