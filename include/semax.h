@@ -30,10 +30,13 @@
  *          node i
  *
  * Conventions shared by every entry point:
- *   - All array pointers are DEVICE pointers owned by the caller.  The library
- *     never allocates, frees or synchronises inside sem_ax* calls; work is
- *     queued on `stream` (a cudaStream_t, NULL = legacy default stream) and
- *     the call returns before it finishes.
+ *   - All array pointers are owned by the caller and must be accessible from
+ *     the device at the address given: device memory, or host memory pinned
+ *     with cudaHostAlloc/cudaHostRegister (on NVLink-C2C systems such as
+ *     GB300 the kernel then streams the arrays over the coherent link with no
+ *     staging copy).  The library never allocates, frees or synchronises
+ *     inside sem_ax* calls; work is queued on `stream` (a cudaStream_t,
+ *     NULL = legacy default stream) and the call returns before it finishes.
  *   - 1 <= N <= 15 (n <= 16), else SEMAX_EUNSUPPORTED_N.
  *   - E == 0 is a no-op returning SEMAX_OK (pointers are not inspected).
  *     E < 0 or a NULL pointer with E > 0 returns SEMAX_EINVAL.
