@@ -88,6 +88,23 @@ def test_f64_general_D_takes_the_generic_path(semax, oracle_mod, N):
     assert rel_err(w32, ref) <= TOL_F32
 
 
+def test_pinned_host_arrays_stream_over_the_link(semax, oracle_mod):
+    """u, G, D and w in pinned host memory: the kernel reads and writes them
+    in place (coherent host access), bit-identical to device-resident arrays."""
+    m = si.make_mesh(np.random.default_rng(77), 33, 7)
+    u_h, G_h, D_h = m.u.pin_memory(), m.G.pin_memory(), m.D.pin_memory()
+    w_h = torch.full_like(u_h, float("nan")).pin_memory()
+    semax.sem_ax(u_h, G_h, D_h, w_h)
+    w_d = semax.sem_ax(u_h.cuda(), G_h.cuda(), D_h.cuda())
+    torch.cuda.synchronize()
+    assert torch.equal(w_h, w_d.cpu())
+    assert rel_err(w_h, oracle_mod.sem_ax(m.u, m.G, m.D)) <= TOL_F64
+    w32 = torch.empty_like(u_h, dtype=torch.float32).pin_memory()
+    semax.sem_ax_f32(u_h.float().pin_memory(), G_h.float().pin_memory(), D_h.float().pin_memory(), w32)
+    torch.cuda.synchronize()
+    assert torch.equal(w32, semax.sem_ax_f32(u_h.float().cuda(), G_h.float().cuda(), D_h.float().cuda()).cpu())
+
+
 def test_f64_empty_and_guard_band(semax, oracle_mod):
     m = si.make_mesh(np.random.default_rng(3), 7, 5)
     u, G, D = to_dev(m)
