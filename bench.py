@@ -357,13 +357,22 @@ def run_ours(args, rank, world):
                          "path": "cudaMemcpyAsync H2D of u, G, D; sem_ax; D2H of w"}}
     del bufs, u_h, G_h, w_h
 
+    # FP64-accurate double-float form on the same workload
+    wx = torch.empty_like(w)
+    t_x = time_region(lambda: semax.sem_ax_f64x(mesh.u, mesh.G, mesh.D, wx), args.steps, args.warmup,
+                      world) / args.steps
+    f64x = {"gdofs": world * dofs / t_x / 1e9, "hbm_gbs": world * dofs * bytes_per_node(8) / t_x / 1e9,
+            "us_per_call": t_x * 1e6, "rel_err_vs_f64": rel_err_gpu(semax, wx, w),
+            "arith": "double-float contractions on the FP32 pipe, FP64 geometric factor; FP64 in/out"}
+    del wx
+
     if rank != 0:
         return
     flops = E * flops_per_element(n)
     nbytes = dofs * bytes_per_node(8)
     achieved = flops / t_step / 1e12
     peaks = load_peaks()
-    roofline = {"bound": "alu", "kernel": "ax_plain_kernel<double, 8, column>",
+    roofline = {"bound": "alu", "kernel": "ax_plain_kernel<double, 8, even/odd lines>",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": profiled_traffic(),
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (GB300 nominal 1.25 TF)",
@@ -378,6 +387,7 @@ def run_ours(args, rank, world):
                        "l2": "inputs larger than L2 (1.07 GB per step vs 129 MB L2), no flush"},
             "hbm_gbs": world * nbytes / t_step / 1e9,
             "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline}
+    line["f64x"] = f64x
     if not args.no_variants:
         line["variants"] = variants(semax, reps=20)
     if not args.no_cpu_baseline and world == 1:

@@ -78,6 +78,19 @@ typedef enum { SEMAX_F64 = 0, SEMAX_F32 = 1 } semax_prec;
 int sem_ax(int64_t E, int N, const double *u, const double *G, const double *D,
            double *w, void *stream);
 
+/* FP64 inputs and outputs, FP64-accurate result; the six contractions run
+ * in double-float arithmetic (each value an unevaluated sum of two floats,
+ * ~47 significant bits) on the FP32 pipe, which GB300 issues 62.5 times
+ * faster than FP64, and the geometric-factor multiply in FP64.  Each
+ * element's u and its intermediate [wr ws wt] are scaled by powers of two
+ * (exact) so that their largest entry lies in [1, 2); entries more than
+ * 2^126 times smaller than their element's largest count as zero.  Error
+ * against the FP64 definition ~1e-14 of ||w||_inf.  Even n with a
+ * centro-antisymmetric D (the GLL derivative); other orders and matrices
+ * are computed by the FP64 kernel of sem_ax. */
+int sem_ax_f64x(int64_t E, int N, const double *u, const double *G, const double *D,
+                double *w, void *stream);
+
 /* FP32 storage and FP32 compute.  G_scale is NULL or [E] per-element factors
  * s_e: the kernel then treats the stored G as G_e / s_e and multiplies the
  * element's result by s_e (use powers of two so that this is exact). */

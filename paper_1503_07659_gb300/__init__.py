@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import SemaxError, semax_group, check, SEMAX_F32, SEMAX_F64
 
-__all__ = ["sem_ax", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_batched", "Plan", "reduce",
+__all__ = ["sem_ax", "sem_ax_f64x", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_batched", "Plan", "reduce",
            "sem_ax_from_host", "SemaxError", "library_path"]
 
 
@@ -49,6 +49,15 @@ def sem_ax(u: torch.Tensor, G: torch.Tensor, D: torch.Tensor, w: torch.Tensor | 
     E, N = _dims(u, D)
     w = _out(w, u)
     check(_lib.lib().sem_ax(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _stream(stream)), "sem_ax")
+    return w
+
+
+def sem_ax_f64x(u: torch.Tensor, G: torch.Tensor, D: torch.Tensor, w: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """FP64 in/out, FP64-accurate; contractions in double-float on the FP32 pipe."""
+    E, N = _dims(u, D)
+    w = _out(w, u)
+    check(_lib.lib().sem_ax_f64x(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _stream(stream)), "sem_ax_f64x")
     return w
 
 

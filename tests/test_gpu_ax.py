@@ -132,6 +132,54 @@ def test_f64_invariants_on_gpu(semax):
     assert semax.reduce(m.u, Au).cpu().numpy()[2] > 0
 
 
+# ---------------------------------------------------------------- FP64-accurate double-float form
+
+@pytest.mark.parametrize("N", list(range(1, 16)))
+@pytest.mark.parametrize("E", [1, 6, 37])
+def test_f64x_every_order_ragged(semax, oracle_mod, N, E):
+    m = si.make_mesh(np.random.default_rng(500 + N), E, N)
+    ref = oracle_mod.sem_ax(m.u, m.G, m.D)
+    u, G, D = to_dev(m)
+    w = semax.sem_ax_f64x(u, G, D)
+    torch.cuda.synchronize()
+    assert rel_err(w, ref) <= TOL_F64
+
+
+def test_f64x_full_size_sampled(semax, oracle_mod):
+    m = si.make_workload(1, device="cuda")[0]
+    w = semax.sem_ax_f64x(m.u, m.G, m.D)
+    w64 = semax.sem_ax(m.u, m.G, m.D)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(14).choice(m.E, size=m.E // 50, replace=False))
+    it = torch.from_numpy(idx).cuda()
+    ref = oracle_mod.sem_ax(m.u[it].cpu(), m.G[it].cpu(), m.D.cpu())
+    assert rel_err(w[it], ref) <= TOL_F64
+    r = semax.reduce(w, w64).cpu().numpy()
+    assert r[0] / r[1] <= TOL_F64                      # whole output against the FP64 kernel
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e-3, 1.0, 1e30])
+def test_f64x_is_scale_invariant(semax, oracle_mod, scale):
+    """Per-element power-of-two scaling keeps the double-float form accurate
+    for inputs far outside the float range's comfortable middle."""
+    m = si.make_mesh(np.random.default_rng(15), 12, 7)
+    u = m.u * scale
+    ref = oracle_mod.sem_ax(u, m.G, m.D)
+    w = semax.sem_ax_f64x(u.cuda(), m.G.cuda(), m.D.cuda())
+    torch.cuda.synchronize()
+    assert rel_err(w, ref) <= TOL_F64
+
+
+def test_f64x_general_D_falls_back(semax, oracle_mod):
+    m = si.make_mesh(np.random.default_rng(16), 5, 7)
+    D = m.D.clone()
+    D[2, 3] += 0.25
+    ref = oracle_mod.sem_ax(m.u, m.G, D)
+    w = semax.sem_ax_f64x(m.u.cuda(), m.G.cuda(), D.cuda())
+    torch.cuda.synchronize()
+    assert rel_err(w, ref) <= TOL_F64
+
+
 # ---------------------------------------------------------------- FP32
 
 @pytest.mark.parametrize("N,E", [(7, 300), (15, 20), (3, 77), (10, 9)])
