@@ -58,6 +58,31 @@ __device__ __forceinline__ df fma_df(df p, df x, df acc) {
     return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(acc.lo, r), s.lo));
 }
 
+// Dot-product accumulator in the manner of Ogita, Rump & Oishi's Dot2: s
+// carries the running float sum, c the sum of every rounding error (exact
+// product residuals, cross terms, two-sum errors); s + c is the result.
+struct acc2 {
+    float s, c;
+};
+
+// a += p * x  (p, x double-float)
+__device__ __forceinline__ void dot2_step(acc2 &a, df p, df x) {
+    const float m = __fmul_rn(p.hi, x.hi);
+    float r = __fmaf_rn(p.hi, x.hi, -m);
+    r = __fmaf_rn(p.hi, x.lo, r);
+    r = __fmaf_rn(p.lo, x.hi, r);
+    const df t = two_sum(a.s, m);
+    a.s = t.hi;
+    a.c = __fadd_rn(a.c, __fadd_rn(r, t.lo));
+}
+
+// (a.s + a.c) +/- (b.s + b.c) as a normalised double-float
+__device__ __forceinline__ df acc_add(acc2 a, acc2 b) {
+    const df t = two_sum(a.s, b.s);
+    return fast_two_sum(t.hi, __fadd_rn(__fadd_rn(a.c, b.c), t.lo));
+}
+__device__ __forceinline__ df acc_sub(acc2 a, acc2 b) { return acc_add(a, acc2{-b.s, -b.c}); }
+
 // 2^k as a float, k in [-126, 127]
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(k + 127) << 23); }
 
@@ -114,9 +139,11 @@ __device__ __forceinline__ void ld_coef(const df *p, df (&c)[h]) {
     }
 }
 
-// y = M x by the even/odd split (P, Q: h x h df, row-major)
+// y = M x by the even/odd split (P, Q: h x h df, row-major); each output
+// pair is written to shared memory as soon as it is formed (y[l * stride]),
+// so no output array stays live in registers.
 template <int n>
-__device__ __forceinline__ void eo_apply(const df (&x)[n], const df *P, const df *Q, df (&y)[n]) {
+__device__ __forceinline__ void eo_apply_st(const df (&x)[n], const df *P, const df *Q, df *y, int stride) {
     constexpr int h = n / 2;
     df e[h], o[h];
 #pragma unroll
@@ -124,19 +151,19 @@ __device__ __forceinline__ void eo_apply(const df (&x)[n], const df *P, const df
         e[l] = add(x[l], x[n - 1 - l]);
         o[l] = sub(x[l], x[n - 1 - l]);
     }
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < h; ++i) {
         df p[h], q[h];
         ld_coef<h>(P + i * h, p);
         ld_coef<h>(Q + i * h, q);
-        df pe{0.f, 0.f}, qo{0.f, 0.f};
+        acc2 pe{0.f, 0.f}, qo{0.f, 0.f};
 #pragma unroll
         for (int l = 0; l < h; ++l) {
-            pe = fma_df(p[l], e[l], pe);
-            qo = fma_df(q[l], o[l], qo);
+            dot2_step(pe, p[l], e[l]);
+            dot2_step(qo, q[l], o[l]);
         }
-        y[i] = add(qo, pe);
-        y[n - 1 - i] = sub(qo, pe);
+        y[i * stride] = acc_add(qo, pe);
+        y[(n - 1 - i) * stride] = acc_sub(qo, pe);
     }
 }
 
@@ -152,18 +179,6 @@ __device__ __forceinline__ void ld_line(const df *p, int stride, df (&x)[n]) {
     } else {
 #pragma unroll
         for (int l = 0; l < n; ++l) x[l] = p[l * stride];
-    }
-}
-
-template <int n>
-__device__ __forceinline__ void st_line(df *p, int stride, const df (&y)[n]) {
-    if (stride == 1) {
-#pragma unroll
-        for (int q = 0; q < n / 2; ++q)
-            reinterpret_cast<float4 *>(p)[q] = make_float4(y[2 * q].hi, y[2 * q].lo, y[2 * q + 1].hi, y[2 * q + 1].lo);
-    } else {
-#pragma unroll
-        for (int l = 0; l < n; ++l) p[l * stride] = y[l];
     }
 }
 
@@ -200,11 +215,11 @@ __host__ __device__ constexpr int elems_per_tile() { return kThreads / (n * n) >
 template <int n>
 __host__ __device__ constexpr size_t smem_bytes(int epb) {
     return sizeof(double) * (size_t)round_up(n * n, 2) + sizeof(df) * 4 * (n / 2) * (n / 2) +
-           sizeof(int) * (size_t)round_up(2 * epb, 4) + sizeof(df) * 4 * (size_t)epb * eo_elem_pitch<double>(n);
+           sizeof(int) * (size_t)round_up(2 * epb, 4) + sizeof(df) * 3 * (size_t)epb * eo_elem_pitch<double>(n);
 }
 
 template <int n>
-__global__ void __launch_bounds__(kThreads, (n <= 8 ? 2 : 1))
+__global__ void __launch_bounds__(kThreads, (n <= 8 ? 3 : 1))
 ax_f64x_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
                const double *__restrict__ D, double *__restrict__ w) {
     constexpr int n2 = n * n, n3 = n * n * n, h = n / 2, epb = elems_per_tile<n>();
@@ -216,7 +231,7 @@ ax_f64x_kernel(int64_t E, const double *__restrict__ u, const double *__restrict
     df *su = reinterpret_cast<df *>(sexp + round_up(2 * epb, 4));
     const int64_t e0 = (int64_t)blockIdx.x * epb;
     const int cnt = (int)(E - e0 < epb ? E - e0 : epb);
-    df *sr = su + cnt * EP, *ss = sr + cnt * EP, *st = ss + cnt * EP;
+    df *sr = su + cnt * EP, *ss = sr + cnt * EP;   // the t-direction reuses su
     const double *ue = u + e0 * n3;
     const double *Ge = G + e0 * 6 * n3;
     double *we = w + e0 * n3;
@@ -239,7 +254,7 @@ ax_f64x_kernel(int64_t E, const double *__restrict__ u, const double *__restrict
     }
     if (!__syncthreads_and(ok)) {
         // D is not centro-antisymmetric: the FP64 node phases on a dense copy
-        double *du = reinterpret_cast<double *>(su);
+        double *du = reinterpret_cast<double *>(su);   // 4 dense blocks fit in 3 padded ones
         double *dr = du + cnt * n3, *ds = dr + cnt * n3, *dt = ds + cnt * n3;
         copy_to_smem(du, ue, cnt * n3);
         __syncthreads();
@@ -280,30 +295,30 @@ ax_f64x_kernel(int64_t E, const double *__restrict__ u, const double *__restrict
             const int e = t / n2, ab = t - e * n2, a = ab / n, b = ab - a * n;
             const int off = e * EP + a * PP + (dir == 0 ? b * RP : b);
             const int stride = dir == 0 ? 1 : RP;
-            df x[n], y[n];
+            df x[n];
             ld_line<n>(su + off, stride, x);
-            eo_apply<n>(x, P, Q, y);
-            st_line<n>(out + off, stride, y);
+            eo_apply_st<n>(x, P, Q, out + off, stride);
         }
     }
     __syncthreads();
-    // columns: t-line, then the FP64 geometric factor per node; raw FP64 results
+    // columns: t-line of u into the column's own slots of su, then the FP64
+    // geometric factor per node; raw FP64 results wr -> sr, ws -> ss, wt -> su
     for (int t = threadIdx.x; t < lines; t += blockDim.x) {
         const int e = t / n2, ji = t - e * n2, j = ji / n, i = ji - j * n;
         const int off = e * EP + j * RP + i;
-        df x[n], y[n];
+        df x[n];
         ld_line<n>(su + off, PP, x);
-        eo_apply<n>(x, P, Q, y);
+        eo_apply_st<n>(x, P, Q, su + off, PP);
         const double *Gq = Ge + (size_t)e * 6 * n3 + ji;
         int mx = 0;
-#pragma unroll
+#pragma unroll 2
         for (int k = 0; k < n; ++k) {
             const int s = off + k * PP;
             double wr, ws, wt;
-            geo_multiply(Gq + k * n2, n3, to_double(sr[s]), to_double(ss[s]), to_double(y[k]), wr, ws, wt);
+            geo_multiply(Gq + k * n2, n3, to_double(sr[s]), to_double(ss[s]), to_double(su[s]), wr, ws, wt);
             reinterpret_cast<double *>(sr)[s] = wr;
             reinterpret_cast<double *>(ss)[s] = ws;
-            reinterpret_cast<double *>(st)[s] = wt;
+            reinterpret_cast<double *>(su)[s] = wt;
             mx = max(mx, max(biased_exponent(wr), max(biased_exponent(ws), biased_exponent(wt))));
         }
         exp_max(sexp + epb, e, mx);
@@ -312,15 +327,14 @@ ax_f64x_kernel(int64_t E, const double *__restrict__ u, const double *__restrict
     // transposed contractions, all three directions, split on load, in place
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
-        df *io = dir == 0 ? sr : (dir == 1 ? ss : st);
+        df *io = dir == 0 ? sr : (dir == 1 ? ss : su);
         for (int t = threadIdx.x; t < lines; t += blockDim.x) {
             const int e = t / n2, ab = t - e * n2, a = ab / n, b = ab - a * n;
             const int off = e * EP + (dir == 0 ? a * PP + b * RP : (dir == 1 ? a * PP + b : a * RP + b));
             const int stride = dir == 0 ? 1 : (dir == 1 ? RP : PP);
-            df x[n], y[n];
+            df x[n];
             ld_line_split<n>(io + off, stride, sexp[epb + e] - 1023, x);
-            eo_apply<n>(x, Pt, Qt, y);
-            st_line<n>(io + off, stride, y);
+            eo_apply_st<n>(x, Pt, Qt, io + off, stride);
         }
     }
     __syncthreads();
@@ -329,7 +343,7 @@ ax_f64x_kernel(int64_t E, const double *__restrict__ u, const double *__restrict
         const int e = f / n3, r = f - e * n3;
         const int k = r / n2, j = (r / n) % n, i = r % n;
         const int s = e * EP + k * PP + j * RP + i;
-        const df acc = add(add(sr[s], ss[s]), st[s]);
+        const df acc = add(add(sr[s], ss[s]), su[s]);
         const double su_scale = __longlong_as_double((long long)(sexp[e] > 0 ? sexp[e] : 1) << 52);
         const double sw_scale = __longlong_as_double((long long)(sexp[epb + e] > 0 ? sexp[epb + e] : 1) << 52);
         we[f] = (to_double(acc) * su_scale) * sw_scale;
