@@ -191,18 +191,47 @@ __device__ __forceinline__ void eo_stage(T *su, const T *__restrict__ u, int cnt
     }
 }
 
+// y = M x for one line x (registers) by the even/odd split, each output
+// pair stored as soon as it is formed (y[l * stride] in shared memory).
+template <typename T, int n>
+__device__ __forceinline__ void eo_apply_st(const T (&x)[n], const T *__restrict__ P,
+                                            const T *__restrict__ Q, T *y, int stride) {
+    constexpr int h = n / 2;
+    T e[h], o[h];
+#pragma unroll
+    for (int l = 0; l < h; ++l) {
+        e[l] = x[l] + x[n - 1 - l];
+        o[l] = x[l] - x[n - 1 - l];
+    }
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+        T p[h], q[h];
+        ld_coef<T, h>(P + i * h, p);
+        ld_coef<T, h>(Q + i * h, q);
+        T pe = T(0), qo = T(0);
+#pragma unroll
+        for (int l = 0; l < h; ++l) {
+            pe = fma_(p[l], e[l], pe);
+            qo = fma_(q[l], o[l], qo);
+        }
+        y[i * stride] = qo + pe;
+        y[(n - 1 - i) * stride] = qo - pe;
+    }
+}
+
 // Phases after staging (the caller has synchronised):
 //   1  r- and s-lines of the gradient -> sr, ss
-//   2  one thread per (i,j) column: t-line of u -> st; the geometric factor
-//      at each node of the column (G from global memory) in place; the
-//      transposed t-line in place.  Fusing the G loads into this pass spreads
-//      them among other warps' arithmetic.
+//   2  one thread per (i,j) column: the t-line of u; the geometric factor at
+//      each node of the column (G from global memory; wr, ws in place, wt in
+//      registers); the transposed t-line of wt written back over the column
+//      of u (only this thread touches it in this phase).  Fusing the G loads
+//      into this pass spreads them among other warps' arithmetic.
 //   3  transposed r- and s-lines in place
 //   4  w = r + s + t, one coalesced store
 template <typename T, int n>
 __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G, T *__restrict__ w,
                                                const T *__restrict__ scale, const T *__restrict__ sPQ,
-                                               const T *su, T *sr, T *ss, T *st) {
+                                               T *su, T *sr, T *ss) {
     constexpr int n2 = n * n, n3 = n * n * n, h = n / 2;
     constexpr int RP = eo_row_pitch<T>(n), PP = eo_plane_pitch<T>(n), EP = eo_elem_pitch<T>(n);
     const T *P = sPQ, *Q = sPQ + h * h, *Pt = sPQ + 2 * h * h, *Qt = sPQ + 3 * h * h;
@@ -216,10 +245,9 @@ __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G,
             const int e = t / n2, ab = t - e * n2, a = ab / n, b = ab - a * n;
             const int off = e * EP + a * PP + (dir == 0 ? b * RP : b);
             const int stride = dir == 0 ? 1 : RP;
-            T x[n], y[n];
+            T x[n];
             ld_line<T, n>(su + off, stride, x);
-            eo_apply<T, n>(x, P, Q, y);
-            st_line<T, n>(out + off, stride, y);
+            eo_apply_st<T, n>(x, P, Q, out + off, stride);
         }
     }
     __syncthreads();
@@ -240,8 +268,7 @@ __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G,
             sr[q] = wr;
             ss[q] = ws;
         }
-        eo_apply<T, n>(x, Pt, Qt, y);                       // transposed t
-        st_line<T, n>(st + off, PP, y);
+        eo_apply_st<T, n>(x, Pt, Qt, su + off, PP);          // transposed t, over u's column
     }
     __syncthreads();
 
@@ -253,10 +280,9 @@ __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G,
             const int e = t / n2, ab = t - e * n2, a = ab / n, b = ab - a * n;
             const int off = e * EP + a * PP + (dir == 0 ? b * RP : b);
             const int stride = dir == 0 ? 1 : RP;
-            T x[n], y[n];
+            T x[n];
             ld_line<T, n>(io + off, stride, x);
-            eo_apply<T, n>(x, Pt, Qt, y);
-            st_line<T, n>(io + off, stride, y);
+            eo_apply_st<T, n>(x, Pt, Qt, io + off, stride);
         }
     }
     __syncthreads();
@@ -266,7 +292,7 @@ __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G,
         const int e = p / n3, r = p - e * n3;
         const int k = r / n2, j = (r / n) % n, i = r % n;
         const int q = e * EP + k * PP + j * RP + i;
-        T acc = (sr[q] + ss[q]) + st[q];
+        T acc = (sr[q] + ss[q]) + su[q];
         if (scale) acc *= scale[e];
         w[p] = acc;
     }

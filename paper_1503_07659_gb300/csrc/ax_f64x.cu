@@ -118,6 +118,20 @@ __device__ __forceinline__ double f2d(float f) {
 
 __device__ __forceinline__ double to_double(df a) { return f2d(a.hi) + f2d(a.lo); }
 
+// f * 2^sh as a double by adding sh to the exponent field; false when the
+// result would leave the normal double range (the caller then multiplies).
+__device__ __forceinline__ bool f2d_scaled(float f, int sh, double &out) {
+    const unsigned b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0) { out = 0.0; return true; }
+    const int ed = e + 896 + sh;
+    if (ed < 1 || ed > 2046) return false;
+    out = __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) |
+                                           ((unsigned long long)ed << 52) |
+                                           ((unsigned long long)(b & 0x7fffffu) << 29)));
+    return true;
+}
+
 __device__ __forceinline__ int biased_exponent(double x) {
     return (int)((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7ffu);
 }
@@ -344,9 +358,15 @@ ax_f64x_kernel(int64_t E, const double *__restrict__ u, const double *__restrict
         const int k = r / n2, j = (r / n) % n, i = r % n;
         const int s = e * EP + k * PP + j * RP + i;
         const df acc = add(add(sr[s], ss[s]), su[s]);
-        const double su_scale = __longlong_as_double((long long)(sexp[e] > 0 ? sexp[e] : 1) << 52);
-        const double sw_scale = __longlong_as_double((long long)(sexp[epb + e] > 0 ? sexp[epb + e] : 1) << 52);
-        we[f] = (to_double(acc) * su_scale) * sw_scale;
+        const int su_e = sexp[e] > 0 ? sexp[e] : 1, sw_e = sexp[epb + e] > 0 ? sexp[epb + e] : 1;
+        double dh, dl;
+        if (f2d_scaled(acc.hi, su_e + sw_e - 2046, dh) && f2d_scaled(acc.lo, su_e + sw_e - 2046, dl)) {
+            we[f] = dh + dl;                       // exact scaling, one FP64 add
+        } else {
+            const double su_scale = __longlong_as_double((long long)su_e << 52);
+            const double sw_scale = __longlong_as_double((long long)sw_e << 52);
+            we[f] = (to_double(acc) * su_scale) * sw_scale;
+        }
     }
 }
 

@@ -51,11 +51,16 @@ template <typename T>
 __host__ __device__ constexpr int eo_elem_pitch(int n);
 
 // Shared-memory footprint (bytes) of D plus one tile of `epb` elements: four
-// element buffers (u and the three directions), padded for MAP_EO.
+// dense element buffers (u and the three directions), or for MAP_EO three
+// padded ones (the t-direction reuses u's slots), at least as large as the
+// four dense buffers of its fallback path.
 template <typename T>
 __host__ __device__ constexpr size_t tile_smem_bytes(int n, int epb, int map) {
     return sizeof(T) * ((size_t)d_slots<T>(n) +
-                        (size_t)epb * 4 * (map == 2 && n % 2 == 0 ? eo_elem_pitch<T>(n) : n * n * n));
+                        (size_t)epb * (map == 2 && n % 2 == 0
+                                           ? (3 * eo_elem_pitch<T>(n) > 4 * n * n * n ? 3 * eo_elem_pitch<T>(n)
+                                                                                     : 4 * n * n * n)
+                                           : 4 * n * n * n));
 }
 
 template <typename T>
@@ -137,7 +142,6 @@ __device__ __forceinline__ void ax_tile(int cnt, const T *__restrict__ u, const 
         T *su = buf;
         T *sr = su + cnt * EP;
         T *ss = sr + cnt * EP;
-        T *st = ss + cnt * EP;
         eo_stage<T, n>(su, u, cnt);
         __syncthreads();   // D (loaded by the caller) and the staged u are visible
         int ok = 1;
@@ -157,14 +161,14 @@ __device__ __forceinline__ void ax_tile(int cnt, const T *__restrict__ u, const 
                 sPQ[3 * h * h + q] = T(0.5) * (at - bt);
             }
             __syncthreads();
-            tile_eo_phases<T, n>(cnt, G, w, scale, sPQ, su, sr, ss, st);
+            tile_eo_phases<T, n>(cnt, G, w, scale, sPQ, su, sr, ss);
             return;
         }
         // D is not centro-antisymmetric: dense staging and the node phases
         su = buf;
         sr = su + nodes;
         ss = sr + nodes;
-        st = ss + nodes;
+        T *st = ss + nodes;
         copy_to_smem(su, u, nodes);
         __syncthreads();
         tile_node_phases<T, n>(cnt, G, w, scale, sD, su, sr, ss, st);
