@@ -365,6 +365,13 @@ def run_ours(args, rank, world):
             "us_per_call": t_x * 1e6, "rel_err_vs_f64": rel_err_gpu(semax, wx, w),
             "arith": "double-float contractions on the FP32 pipe, FP64 geometric factor; FP64 in/out"}
     del wx
+    # Helmholtz form w = h1 A u + h2 B u on the same workload (72 B/node)
+    Bm = si.mass_diagonal(mesh.X, mesh.N, device=dev)
+    wh = torch.empty_like(w)
+    t_h = time_region(lambda: semax.sem_ax_helmholtz(mesh.u, mesh.G, Bm, mesh.D, 1.0, 0.1, wh), args.steps,
+                      args.warmup, world) / args.steps
+    helm = {"gdofs": world * dofs / t_h / 1e9, "hbm_gbs": world * dofs * 72 / t_h / 1e9, "us_per_call": t_h * 1e6}
+    del wh, Bm
 
     if rank != 0:
         return
@@ -388,6 +395,7 @@ def run_ours(args, rank, world):
             "hbm_gbs": world * nbytes / t_step / 1e9,
             "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline}
     line["f64x"] = f64x
+    line["helmholtz_f64"] = helm
     if not args.no_variants:
         line["variants"] = variants(semax, reps=20)
     if not args.no_cpu_baseline and world == 1:

@@ -78,6 +78,17 @@ typedef enum { SEMAX_F64 = 0, SEMAX_F32 = 1 } semax_prec;
 int sem_ax(int64_t E, int N, const double *u, const double *G, const double *D,
            double *w, void *stream);
 
+/* Helmholtz form of the operator, FP64:
+ *     w = h1 A u + h2 B u,
+ * B [E][n][n][n] the diagonal GLL mass matrix (det(J) w_i w_j w_k per node),
+ * h1, h2 scalars.  The SEM Helmholtz operator of implicit time stepping and
+ * of the pressure/velocity solvers that apply Ax (Deville, Fischer & Mund
+ * 2002, Sec. 4.4); one extra read of B and two FP64 operations per node on
+ * top of Ax, fused into the same pass.  B follows the alignment and aliasing
+ * rules of G.  With h1 = 1, h2 = 0 it returns sem_ax's values. */
+int sem_ax_helmholtz(int64_t E, int N, const double *u, const double *G, const double *B,
+                     const double *D, double h1, double h2, double *w, void *stream);
+
 /* FP64 inputs and outputs, FP64-accurate result; the six contractions run
  * in double-float arithmetic (each value an unevaluated sum of two floats,
  * ~47 significant bits) on the FP32 pipe, which GB300 issues 62.5 times

@@ -6,6 +6,8 @@ no code.  Everything here is float64 on the host:
 
 * ``sem_ax``  -- the plain C loop nest in sem_ax_oracle.c (the operator's
   definition written out; OpenMP over elements, no FMA contraction);
+* ``sem_helmholtz`` -- h1 A u + h2 B u, the same loop nest plus the diagonal
+  mass term;
 * ``dense_element_matrix`` -- the same operator assembled as a dense
   n^3 x n^3 matrix from Kronecker products, an independent formulation used to
   pin the loop nest on small elements;
@@ -49,6 +51,9 @@ def _load():
         lib = ctypes.CDLL(build())
         lib.oracle_sem_ax.restype = ctypes.c_int
         lib.oracle_sem_ax.argtypes = [ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_int]
+        lib.oracle_sem_helmholtz.restype = ctypes.c_int
+        lib.oracle_sem_helmholtz.argtypes = ([ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 4 +
+                                             [ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_int])
         _lib = lib
     return _lib
 
@@ -71,6 +76,19 @@ def sem_ax(u, G, D, nthreads: int = 0, return_threads: bool = False):
     if used < 0:
         raise RuntimeError("oracle_sem_ax failed")
     return (w, used) if return_threads else w
+
+
+def sem_helmholtz(u, G, B, D, h1: float, h2: float, nthreads: int = 0):
+    """w = h1 A u + h2 B u (B [E,n,n,n] the diagonal mass), float64 on the host."""
+    u, G, B, D = _f64(u), _f64(G), _f64(B), _f64(D)
+    n = D.shape[0]
+    E = u.shape[0] if u.size else 0
+    assert B.shape == u.shape
+    w = np.empty_like(u)
+    if _load().oracle_sem_helmholtz(E, n - 1, u.ctypes.data, G.ctypes.data, B.ctypes.data, D.ctypes.data,
+                                    float(h1), float(h2), w.ctypes.data, int(nthreads)) < 0:
+        raise RuntimeError("oracle_sem_helmholtz failed")
+    return w
 
 
 def dense_element_matrix(D, G_e) -> np.ndarray:

@@ -103,3 +103,15 @@ int oracle_sem_ax(int64_t E, int N, const double *u, const double *G,
     }
     return failed ? -1 : used;
 }
+
+/* Helmholtz form w = h1 A u + h2 B u, B the diagonal mass matrix (one value
+ * per node): the operator above followed by the diagonal term, as defined. */
+int oracle_sem_helmholtz(int64_t E, int N, const double *u, const double *G, const double *B,
+                         const double *D, double h1, double h2, double *w, int nthreads)
+{
+    int used = oracle_sem_ax(E, N, u, G, D, w, nthreads);
+    if (used < 0) return used;
+    const int64_t count = E * (int64_t)(N + 1) * (N + 1) * (N + 1);
+    for (int64_t p = 0; p < count; ++p) w[p] = h1 * w[p] + h2 * B[p] * u[p];
+    return used;
+}

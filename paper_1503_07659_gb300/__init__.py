@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import SemaxError, semax_group, check, SEMAX_F32, SEMAX_F64
 
-__all__ = ["sem_ax", "sem_ax_f64x", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_batched", "Plan", "reduce",
+__all__ = ["sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_batched", "Plan", "reduce",
            "sem_ax_from_host", "SemaxError", "library_path"]
 
 
@@ -49,6 +49,16 @@ def sem_ax(u: torch.Tensor, G: torch.Tensor, D: torch.Tensor, w: torch.Tensor | 
     E, N = _dims(u, D)
     w = _out(w, u)
     check(_lib.lib().sem_ax(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _stream(stream)), "sem_ax")
+    return w
+
+
+def sem_ax_helmholtz(u: torch.Tensor, G: torch.Tensor, B: torch.Tensor, D: torch.Tensor, h1: float,
+                     h2: float, w: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """FP64 w = h1 A u + h2 B u (B the diagonal mass matrix, [E,n,n,n])."""
+    E, N = _dims(u, D)
+    w = _out(w, u)
+    check(_lib.lib().sem_ax_helmholtz(E, N, _ptr(u), _ptr(G), _ptr(B), _ptr(D), float(h1), float(h2), _ptr(w),
+                                      _stream(stream)), "sem_ax_helmholtz")
     return w
 
 

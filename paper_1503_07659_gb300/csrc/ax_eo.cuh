@@ -228,10 +228,10 @@ __device__ __forceinline__ void eo_apply_st(const T (&x)[n], const T *__restrict
 //      into this pass spreads them among other warps' arithmetic.
 //   3  transposed r- and s-lines in place
 //   4  w = r + s + t, one coalesced store
-template <typename T, int n>
+template <typename T, int n, bool HELM>
 __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G, T *__restrict__ w,
-                                               const T *__restrict__ scale, const T *__restrict__ sPQ,
-                                               T *su, T *sr, T *ss) {
+                                               const T *__restrict__ scale, Helm<T> helm,
+                                               const T *__restrict__ sPQ, T *su, T *sr, T *ss) {
     constexpr int n2 = n * n, n3 = n * n * n, h = n / 2;
     constexpr int RP = eo_row_pitch<T>(n), PP = eo_plane_pitch<T>(n), EP = eo_elem_pitch<T>(n);
     const T *P = sPQ, *Q = sPQ + h * h, *Pt = sPQ + 2 * h * h, *Qt = sPQ + 3 * h * h;
@@ -259,16 +259,32 @@ __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G,
         T x[n], y[n];
         ld_line<T, n>(su + off, PP, x);
         eo_apply<T, n>(x, P, Q, y);                         // ut
+        T m[HELM ? n : 1];                                  // h2 B u on this column
+        if constexpr (HELM) {
+#pragma unroll
+            for (int k = 0; k < n; ++k) m[k] = helm.h2 * helm.B[e * n3 + k * n2 + ji] * x[k];
+        }
         const T *Ge = G + (size_t)e * 6 * n3 + ji;
 #pragma unroll
         for (int k = 0; k < n; ++k) {
             const int q = off + k * PP;
             T wr, ws;
             geo_multiply(Ge + k * n2, n3, sr[q], ss[q], y[k], wr, ws, x[k]);
+            if constexpr (HELM) {
+                wr *= helm.h1;
+                ws *= helm.h1;
+                x[k] *= helm.h1;
+            }
             sr[q] = wr;
             ss[q] = ws;
         }
-        eo_apply_st<T, n>(x, Pt, Qt, su + off, PP);          // transposed t, over u's column
+        if constexpr (HELM) {                               // transposed t plus the mass term
+            eo_apply<T, n>(x, Pt, Qt, y);
+#pragma unroll
+            for (int k = 0; k < n; ++k) su[off + k * PP] = y[k] + m[k];
+        } else {
+            eo_apply_st<T, n>(x, Pt, Qt, su + off, PP);      // transposed t, over u's column
+        }
     }
     __syncthreads();
 

@@ -2,6 +2,6 @@
 #include "ax_plain.cuh"
 
 namespace semax {
-template int launch_plain<double>(int64_t, int, const TileConfig &, const double *, const double *,
-                                  const double *, double *, const double *, cudaStream_t);
+template int launch_plain<double, false>(int64_t, int, const TileConfig &, const double *, const double *,
+                                         const double *, double *, const double *, Helm<double>, cudaStream_t);
 }  // namespace semax

@@ -272,7 +272,7 @@ ax_f64x_kernel(int64_t E, const double *__restrict__ u, const double *__restrict
         double *dr = du + cnt * n3, *ds = dr + cnt * n3, *dt = ds + cnt * n3;
         copy_to_smem(du, ue, cnt * n3);
         __syncthreads();
-        tile_node_phases<double, n>(cnt, Ge, we, nullptr, sD, du, dr, ds, dt);
+        tile_node_phases<double, n>(cnt, Ge, we, nullptr, Helm<double>{nullptr, 1.0, 0.0}, sD, du, dr, ds, dt);
         return;
     }
     for (int q = threadIdx.x; q < h * h; q += blockDim.x) {

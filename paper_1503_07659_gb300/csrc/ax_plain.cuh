@@ -36,10 +36,10 @@ inline TileConfig default_tile(int n) {
 // Up to n = 8 a tile fits three times in shared memory, so registers are
 // capped for three resident CTAs per SM; an FP32 tile up to n = 16 fits
 // twice.
-template <typename T, int n, int MAP>
+template <typename T, int n, int MAP, bool HELM>
 __global__ void __launch_bounds__(256, (n <= 8 ? 3 : (sizeof(T) == 4 ? 2 : 1)))
 ax_plain_kernel(int64_t E, int epb, const T *__restrict__ u, const T *__restrict__ G,
-                const T *__restrict__ D, T *__restrict__ w, const T *__restrict__ scale) {
+                const T *__restrict__ D, T *__restrict__ w, const T *__restrict__ scale, Helm<T> helm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int n3 = n * n * n;
     T *sD = reinterpret_cast<T *>(smem_raw);
@@ -47,14 +47,15 @@ ax_plain_kernel(int64_t E, int epb, const T *__restrict__ u, const T *__restrict
     const int64_t e0 = (int64_t)blockIdx.x * epb;
     const int cnt = (int)(E - e0 < epb ? E - e0 : epb);
     load_D<T, n>(D, sD);
-    ax_tile<T, n, MAP>(cnt, u + e0 * n3, G + e0 * 6 * n3, w + e0 * n3,
-                       scale ? scale + e0 : nullptr, sD, buf);
+    if constexpr (HELM) helm.B += e0 * n3;
+    ax_tile<T, n, MAP, HELM>(cnt, u + e0 * n3, G + e0 * 6 * n3, w + e0 * n3,
+                             scale ? scale + e0 : nullptr, helm, sD, buf);
 }
 
-template <typename T, int n, int MAP>
+template <typename T, bool HELM, int n, int MAP>
 int launch_plain_nm(int64_t E, const TileConfig &c, const T *u, const T *G, const T *D, T *w,
-                    const T *scale, cudaStream_t s) {
-    auto kern = ax_plain_kernel<T, n, MAP>;
+                    const T *scale, Helm<T> helm, cudaStream_t s) {
+    auto kern = ax_plain_kernel<T, n, MAP, HELM>;
     const size_t smem = tile_smem_bytes<T>(n, c.epb, MAP);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -65,28 +66,31 @@ int launch_plain_nm(int64_t E, const TileConfig &c, const T *u, const T *G, cons
     }
     const int64_t tiles = (E + c.epb - 1) / c.epb;
     if (tiles > 0x7fffffffLL) return SEMAX_EINVAL;
-    kern<<<(unsigned)tiles, c.threads, smem, s>>>(E, c.epb, u, G, D, w, scale);
+    kern<<<(unsigned)tiles, c.threads, smem, s>>>(E, c.epb, u, G, D, w, scale, helm);
     return launch_status();
 }
 
-template <typename T, int n>
+template <typename T, bool HELM, int n>
 int launch_plain_n(int64_t E, const TileConfig &c, const T *u, const T *G, const T *D, T *w,
-                   const T *scale, cudaStream_t s) {
+                   const T *scale, Helm<T> helm, cudaStream_t s) {
     if (c.epb < 1 || c.threads < 32 || c.threads > 256 || (c.threads & 31)) return SEMAX_EINVAL;
     if (c.map == MAP_COLUMN) {
         if (c.epb * n * n > c.threads) return SEMAX_EINVAL;
-        return launch_plain_nm<T, n, MAP_COLUMN>(E, c, u, G, D, w, scale, s);
+        return launch_plain_nm<T, HELM, n, MAP_COLUMN>(E, c, u, G, D, w, scale, helm, s);
     }
-    if (c.map == MAP_EO && n % 2 == 0) return launch_plain_nm<T, n, MAP_EO>(E, c, u, G, D, w, scale, s);
-    return launch_plain_nm<T, n, MAP_NODE>(E, c, u, G, D, w, scale, s);
+    if (c.map == MAP_EO && n % 2 == 0)
+        return launch_plain_nm<T, HELM, n, MAP_EO>(E, c, u, G, D, w, scale, helm, s);
+    return launch_plain_nm<T, HELM, n, MAP_NODE>(E, c, u, G, D, w, scale, helm, s);
 }
 
-template <typename T>
+// Launch the plain kernel for order N with tile shape c.  HELM selects the
+// Helmholtz form (helm.B, h1, h2); otherwise helm is ignored.
+template <typename T, bool HELM = false>
 int launch_plain(int64_t E, int N, const TileConfig &c, const T *u, const T *G, const T *D, T *w,
-                 const T *scale, cudaStream_t s) {
+                 const T *scale, Helm<T> helm, cudaStream_t s) {
     switch (N + 1) {
 #define SEMAX_CASE(nn) \
-    case nn: return launch_plain_n<T, nn>(E, c, u, G, D, w, scale, s);
+    case nn: return launch_plain_n<T, HELM, nn>(E, c, u, G, D, w, scale, helm, s);
         SEMAX_CASE(2) SEMAX_CASE(3) SEMAX_CASE(4) SEMAX_CASE(5) SEMAX_CASE(6) SEMAX_CASE(7)
         SEMAX_CASE(8) SEMAX_CASE(9) SEMAX_CASE(10) SEMAX_CASE(11) SEMAX_CASE(12) SEMAX_CASE(13)
         SEMAX_CASE(14) SEMAX_CASE(15) SEMAX_CASE(16)
@@ -95,12 +99,15 @@ int launch_plain(int64_t E, int N, const TileConfig &c, const T *u, const T *G, 
     }
 }
 
-// Explicit instantiations live in ax_f64.cu / ax_f32.cu.
-extern template int launch_plain<double>(int64_t, int, const TileConfig &, const double *,
-                                         const double *, const double *, double *,
-                                         const double *, cudaStream_t);
-extern template int launch_plain<float>(int64_t, int, const TileConfig &, const float *,
-                                        const float *, const float *, float *, const float *,
-                                        cudaStream_t);
+// Explicit instantiations live in ax_f64.cu, ax_f32.cu and ax_helm.cu.
+extern template int launch_plain<double, false>(int64_t, int, const TileConfig &, const double *,
+                                                const double *, const double *, double *,
+                                                const double *, Helm<double>, cudaStream_t);
+extern template int launch_plain<float, false>(int64_t, int, const TileConfig &, const float *,
+                                               const float *, const float *, float *, const float *,
+                                               Helm<float>, cudaStream_t);
+extern template int launch_plain<double, true>(int64_t, int, const TileConfig &, const double *,
+                                               const double *, const double *, double *,
+                                               const double *, Helm<double>, cudaStream_t);
 
 }  // namespace semax

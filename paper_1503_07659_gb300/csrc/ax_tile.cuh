@@ -70,6 +70,15 @@ __device__ __forceinline__ double fma_(double a, double b, double c) { return __
 template <>
 __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// Helmholtz extension w = h1 A u + h2 B u (B the diagonal mass matrix, one
+// value per node, pointing at the tile's first element); used when the tile
+// routines are instantiated with HELM = true.
+template <typename T>
+struct Helm {
+    const T *B;
+    T h1, h2;
+};
+
 // Multiply by the symmetric factor: G components (rr, rs, rt, ss, st, tt).
 template <typename T>
 __device__ __forceinline__ void geo_multiply(const T *__restrict__ Gq, int n3, T ur, T us, T ut,
@@ -82,10 +91,10 @@ __device__ __forceinline__ void geo_multiply(const T *__restrict__ Gq, int n3, T
 }
 
 // Phases 2-3 with one thread per node (MAP_NODE).
-template <typename T, int n>
+template <typename T, int n, bool HELM = false>
 __device__ __forceinline__ void tile_node_phases(int cnt, const T *__restrict__ G, T *__restrict__ w,
-                                                 const T *__restrict__ scale, const T *__restrict__ sD,
-                                                 const T *su, T *sr, T *ss, T *st) {
+                                                 const T *__restrict__ scale, Helm<T> helm,
+                                                 const T *__restrict__ sD, const T *su, T *sr, T *ss, T *st) {
     constexpr int n2 = n * n, n3 = n * n * n;
     const int nodes = cnt * n3;
     for (int p = threadIdx.x; p < nodes; p += blockDim.x) {
@@ -117,6 +126,7 @@ __device__ __forceinline__ void tile_node_phases(int cnt, const T *__restrict__ 
         for (int l = 0; l < n; ++l) acc = fma_(sD[l * n + j], se[k * n2 + l * n + i], acc);
 #pragma unroll
         for (int l = 0; l < n; ++l) acc = fma_(sD[l * n + k], te[l * n2 + j * n + i], acc);
+        if constexpr (HELM) acc = fma_(helm.h2 * helm.B[p], su[p], helm.h1 * acc);
         if (scale) acc *= scale[e];
         w[p] = acc;
     }
@@ -131,9 +141,9 @@ namespace semax {
 // Tile routine.  sD holds D (n x n) already, with d_slots(n) slots reserved;
 // `buf` is the tile's shared scratch (tile_smem_bytes minus the D part).
 // u, G and w point at element e0.
-template <typename T, int n, int MAP>
+template <typename T, int n, int MAP, bool HELM = false>
 __device__ __forceinline__ void ax_tile(int cnt, const T *__restrict__ u, const T *__restrict__ G,
-                                        T *__restrict__ w, const T *__restrict__ scale,
+                                        T *__restrict__ w, const T *__restrict__ scale, Helm<T> helm,
                                         T *__restrict__ sD, T *__restrict__ buf) {
     constexpr int n2 = n * n, n3 = n * n * n;
     const int nodes = cnt * n3;
@@ -161,7 +171,7 @@ __device__ __forceinline__ void ax_tile(int cnt, const T *__restrict__ u, const 
                 sPQ[3 * h * h + q] = T(0.5) * (at - bt);
             }
             __syncthreads();
-            tile_eo_phases<T, n>(cnt, G, w, scale, sPQ, su, sr, ss);
+            tile_eo_phases<T, n, HELM>(cnt, G, w, scale, helm, sPQ, su, sr, ss);
             return;
         }
         // D is not centro-antisymmetric: dense staging and the node phases
@@ -171,7 +181,7 @@ __device__ __forceinline__ void ax_tile(int cnt, const T *__restrict__ u, const 
         T *st = ss + nodes;
         copy_to_smem(su, u, nodes);
         __syncthreads();
-        tile_node_phases<T, n>(cnt, G, w, scale, sD, su, sr, ss, st);
+        tile_node_phases<T, n, HELM>(cnt, G, w, scale, helm, sD, su, sr, ss, st);
         return;
     }
     T *su = buf;
@@ -220,12 +230,16 @@ __device__ __forceinline__ void ax_tile(int cnt, const T *__restrict__ u, const 
                 for (int l = 0; l < n; ++l) acc = fma_(sD[l * n + j], se[k * n2 + l * n + i], acc);
 #pragma unroll
                 for (int l = 0; l < n; ++l) acc = fma_(sD[l * n + k], te[l * n2 + ji], acc);
+                if constexpr (HELM) {
+                    const int q = e * n3 + k * n2 + ji;
+                    acc = fma_(helm.h2 * helm.B[q], su[q], helm.h1 * acc);
+                }
                 if (scale) acc *= sc;
                 w[(size_t)e * n3 + k * n2 + ji] = acc;
             }
         }
     } else {
-        tile_node_phases<T, n>(cnt, G, w, scale, sD, su, sr, ss, st);
+        tile_node_phases<T, n, HELM>(cnt, G, w, scale, helm, sD, su, sr, ss, st);
     }
 }
 

@@ -49,7 +49,8 @@ template <int n, int MAP>
 __device__ __forceinline__ void run_tile(const GroupDev &g, int64_t e0, int cnt, double *sD,
                                          double *buf) {
     constexpr int n3 = n * n * n;
-    ax_tile<double, n, MAP>(cnt, g.u + e0 * n3, g.G + e0 * 6 * n3, g.w + e0 * n3, nullptr, sD, buf);
+    ax_tile<double, n, MAP>(cnt, g.u + e0 * n3, g.G + e0 * 6 * n3, g.w + e0 * n3, nullptr,
+                            Helm<double>{nullptr, 1.0, 0.0}, sD, buf);
 }
 
 __global__ void __launch_bounds__(kBatchThreads)

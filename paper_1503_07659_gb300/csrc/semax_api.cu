@@ -26,7 +26,7 @@ extern "C" int sem_ax(int64_t E, int N, const double *u, const double *G, const 
     int st = check_args(E, N, u, G, D, w);
     if (st != SEMAX_OK || E == 0) return st;
     return launch_plain<double>(E, N, default_tile<double>(N + 1), u, G, D, w, nullptr,
-                                (cudaStream_t)stream);
+                                Helm<double>{nullptr, 1.0, 0.0}, (cudaStream_t)stream);
 }
 
 extern "C" int sem_ax_f32(int64_t E, int N, const float *u, const float *G, const float *D,
@@ -37,7 +37,19 @@ extern "C" int sem_ax_f32(int64_t E, int N, const float *u, const float *G, cons
                             (size_t)E * sizeof(float)))
         return SEMAX_EALIAS;
     return launch_plain<float>(E, N, default_tile<float>(N + 1), u, G, D, w, G_scale,
-                               (cudaStream_t)stream);
+                               Helm<float>{nullptr, 1.0f, 0.0f}, (cudaStream_t)stream);
+}
+
+extern "C" int sem_ax_helmholtz(int64_t E, int N, const double *u, const double *G, const double *B,
+                                const double *D, double h1, double h2, double *w, void *stream) {
+    int st = check_args(E, N, u, G, D, w);
+    if (st != SEMAX_OK || E == 0) return st;
+    if (!B) return SEMAX_EINVAL;
+    if (!aligned16(B)) return SEMAX_EALIGN;
+    const size_t ub = (size_t)E * (N + 1) * (N + 1) * (N + 1) * sizeof(double);
+    if (overlaps(w, ub, B, ub)) return SEMAX_EALIAS;
+    return launch_plain<double, true>(E, N, default_tile<double>(N + 1), u, G, D, w, nullptr,
+                                      Helm<double>{B, h1, h2}, (cudaStream_t)stream);
 }
 
 extern "C" const char *semax_strerror(int status) {

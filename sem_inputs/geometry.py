@@ -107,6 +107,22 @@ def geometric_factors(X: np.ndarray, N: int, device="cpu", chunk: int = 8192) ->
     return G.view(E, 6, n, n, n)
 
 
+def mass_diagonal(X: np.ndarray, N: int, device="cpu", chunk: int = 8192) -> torch.Tensor:
+    """B [E, n, n, n] = det(J) w_i w_j w_k at every GLL node: the diagonal of
+    the GLL-collocated mass matrix (Deville, Fischer & Mund 2002, Sec. 4.4)."""
+    n = N + 1
+    E = X.shape[0]
+    dev = torch.device(device)
+    dN = torch.from_numpy(_shape_gradients(N)).to(dev)
+    wq = torch.from_numpy(_node_weights(N)).to(dev)
+    B = torch.empty((E, n ** 3), dtype=torch.float64, device=dev)
+    Xt = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
+    for e0 in range(0, E, chunk):
+        J = torch.einsum("cva,pvd->cpad", Xt[e0:e0 + chunk], dN)
+        B[e0:e0 + chunk] = torch.linalg.det(J) * wq[None, :]
+    return B.view(E, n, n, n)
+
+
 def jacobian_determinants(X: np.ndarray, N: int) -> np.ndarray:
     """det(J) at every node, (E, n^3), float64 on the host (for checks)."""
     dN = _shape_gradients(N)

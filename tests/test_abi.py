@@ -90,3 +90,14 @@ def test_reduce_validation(lib):
     assert lib.semax_reduce_workspace_size(-1, ctypes.byref(size)) == -1
     assert lib.semax_reduce(100, A, 0, A + 4096, 2, A + 8192, A + 16384, 1 << 20, None) == -1  # bad prec
     assert lib.semax_reduce(100, A, 0, A + 4096, 0, A + 8192, None, 0, None) == -8
+
+
+def test_helmholtz_validation(lib):
+    import ctypes as C
+    f = lib.sem_ax_helmholtz
+    u, G, B, D, w = A, A + (1 << 32), A + (4 << 32), A + (2 << 32), A + (3 << 32)
+    assert f(0, 7, None, None, None, None, C.c_double(1.0), C.c_double(0.0), None, None) == 0
+    assert f(4, 7, u, G, None, D, C.c_double(1.0), C.c_double(0.0), w, None) == -1       # B missing
+    assert f(4, 7, u, G, B + 8, D, C.c_double(1.0), C.c_double(0.0), w, None) == -3      # B misaligned
+    assert f(4, 7, u, G, w + 64, D, C.c_double(1.0), C.c_double(0.0), w, None) == -4     # w overlaps B
+    assert f(4, 16, u, G, B, D, C.c_double(1.0), C.c_double(0.0), w, None) == -2

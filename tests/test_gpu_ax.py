@@ -132,6 +132,43 @@ def test_f64_invariants_on_gpu(semax):
     assert semax.reduce(m.u, Au).cpu().numpy()[2] > 0
 
 
+# ---------------------------------------------------------------- Helmholtz form
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 7, 8, 15])
+@pytest.mark.parametrize("E", [1, 19])
+def test_helmholtz_against_oracle(semax, oracle_mod, N, E):
+    m = si.make_mesh(np.random.default_rng(600 + N), E, N)
+    B = si.mass_diagonal(m.X, N)
+    h1, h2 = 0.625, 7.25
+    ref = oracle_mod.sem_helmholtz(m.u, m.G, B, m.D, h1, h2)
+    u, G, D = to_dev(m)
+    w = semax.sem_ax_helmholtz(u, G, B.cuda(), D, h1, h2)
+    torch.cuda.synchronize()
+    assert rel_err(w, ref) <= TOL_F64
+
+
+def test_helmholtz_reduces_to_ax_and_mass(semax):
+    m = si.make_mesh(np.random.default_rng(610), 40, 7, device="cuda")
+    B = si.mass_diagonal(m.X, 7, device="cuda")
+    w_ax = semax.sem_ax(m.u, m.G, m.D)
+    w_h = semax.sem_ax_helmholtz(m.u, m.G, B, m.D, 1.0, 0.0)
+    w_m = semax.sem_ax_helmholtz(torch.ones_like(m.u), m.G, B, m.D, 3.0, 2.0)
+    torch.cuda.synchronize()
+    assert torch.equal(w_ax, w_h)
+    assert (w_m - 2.0 * B).abs().max().item() <= 1e-12 * B.abs().max().item()
+
+
+def test_helmholtz_full_size_sampled(semax, oracle_mod):
+    m = si.make_workload(1, device="cuda")[0]
+    B = si.mass_diagonal(m.X, m.N, device="cuda")
+    w = semax.sem_ax_helmholtz(m.u, m.G, B, m.D, 1.0, 0.1)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(17).choice(m.E, size=m.E // 50, replace=False))
+    it = torch.from_numpy(idx).cuda()
+    ref = oracle_mod.sem_helmholtz(m.u[it].cpu(), m.G[it].cpu(), B[it].cpu(), m.D.cpu(), 1.0, 0.1)
+    assert rel_err(w[it], ref) <= TOL_F64
+
+
 # ---------------------------------------------------------------- FP64-accurate double-float form
 
 @pytest.mark.parametrize("N", list(range(1, 16)))

@@ -217,3 +217,47 @@ def test_batched_order_mix_reaches_target():
     # geometric law: lower orders are drawn more often
     ks = [counts[N] for N in sorted(counts)]
     assert ks == sorted(ks, reverse=True)
+
+
+# ---------------------------------------------------------------- Helmholtz form h1 A u + h2 B u
+
+def test_mass_diagonal_closed_forms():
+    """B = det(J) w_i w_j w_k: (h/2)^3 w_i w_j w_k on the cube; its sum is the
+    element volume, exactly 8 det(A_e) for an affine element."""
+    N = 5
+    h = 0.7
+    cube = si.make_mesh(np.random.default_rng(40), 3, N, kind="cube", h=h)
+    w = si.gll_weights(N)
+    B = si.mass_diagonal(cube.X, N).numpy()
+    np.testing.assert_allclose(B, np.broadcast_to((h / 2) ** 3 * np.einsum("k,j,i->kji", w, w, w), B.shape),
+                               rtol=1e-14)
+    assert np.allclose(B.reshape(3, -1).sum(1), h ** 3, rtol=1e-14)
+    aff = si.make_mesh(np.random.default_rng(41), 4, N, kind="affine")
+    A_e = np.einsum("eva,vb->eab", aff.X, np.array(
+        [[2 * (v & 1) - 1, 2 * ((v >> 1) & 1) - 1, 2 * ((v >> 2) & 1) - 1] for v in range(8)])) / 8.0
+    Ba = si.mass_diagonal(aff.X, N).numpy().reshape(4, -1)
+    np.testing.assert_allclose(Ba.sum(1), 8.0 * np.linalg.det(A_e), rtol=1e-13)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5])
+def test_oracle_helmholtz_matches_dense_and_reduces_to_ax(oracle_mod, N):
+    m = si.make_mesh(np.random.default_rng(42 + N), 3, N)
+    B = si.mass_diagonal(m.X, N)
+    h1, h2 = 0.75, 3.5
+    w = oracle_mod.sem_helmholtz(m.u, m.G, B, m.D, h1, h2)
+    for e in range(3):
+        H = h1 * oracle_mod.dense_element_matrix(m.D, m.G[e]) + h2 * np.diag(B[e].numpy().ravel())
+        ref = H @ m.u[e].numpy().ravel()
+        assert np.max(np.abs(w[e].ravel() - ref)) / np.max(np.abs(ref)) < 1e-13
+        ev = np.linalg.eigvalsh(0.5 * (H + H.T))
+        assert ev[0] > 0                                   # SPD once h2 > 0
+    assert np.array_equal(oracle_mod.sem_helmholtz(m.u, m.G, B, m.D, 1.0, 0.0), oracle_mod.sem_ax(m.u, m.G, m.D))
+
+
+def test_oracle_helmholtz_of_constant_is_mass(oracle_mod):
+    """A 1 = 0, so H 1 = h2 B (and sums to h2 times the volume)."""
+    m = si.make_mesh(np.random.default_rng(45), 6, 4)
+    B = si.mass_diagonal(m.X, 4)
+    one = np.ones_like(m.u.numpy())
+    w = oracle_mod.sem_helmholtz(one, m.G, B, m.D, 2.0, 0.5)
+    assert np.max(np.abs(w - 0.5 * B.numpy())) <= 1e-12 * np.max(np.abs(B.numpy()))

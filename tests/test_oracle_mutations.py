@@ -78,3 +78,25 @@ def test_planted_mistake_is_caught(tmp_path, oracle_mod, name):
     assert src.count(old) == 1, "mutation anchor not found"
     lib = _compile(tmp_path, "mut", src.replace(old, new))
     assert not _pins_pass(lib, oracle_mod)
+
+
+def test_planted_helmholtz_mistake_is_caught(tmp_path, oracle_mod):
+    """The mass term applied to w instead of u, or with h1 and h2 swapped,
+    fails the dense Helmholtz pin."""
+    src = open(SRC).read()
+    anchor = "w[p] = h1 * w[p] + h2 * B[p] * u[p];"
+    assert src.count(anchor) == 1
+    m = si.make_mesh(np.random.default_rng(46), 2, 3)
+    B = si.mass_diagonal(m.X, 3).numpy()
+    for idx, bad in enumerate(("w[p] = h1 * w[p] + h2 * B[p] * w[p];", "w[p] = h2 * w[p] + h1 * B[p] * u[p];")):
+        lib = _compile(tmp_path, f"helm{idx}", src.replace(anchor, bad))
+        lib.oracle_sem_helmholtz.restype = ctypes.c_int
+        lib.oracle_sem_helmholtz.argtypes = ([ctypes.c_int64, ctypes.c_int] + [ctypes.c_void_p] * 4 +
+                                             [ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_int])
+        u, G, D = (np.ascontiguousarray(x.numpy()) for x in (m.u, m.G, m.D))
+        w = np.empty_like(u)
+        lib.oracle_sem_helmholtz(2, 3, u.ctypes.data, G.ctypes.data, B.ctypes.data, D.ctypes.data,
+                                 0.75, 3.5, w.ctypes.data, 1)
+        H = 0.75 * oracle_mod.dense_element_matrix(m.D, m.G[0]) + 3.5 * np.diag(B[0].ravel())
+        ref = H @ u[0].ravel()
+        assert np.max(np.abs(w[0].ravel() - ref)) / np.max(np.abs(ref)) > 1e-6
