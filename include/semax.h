@@ -165,6 +165,43 @@ int sem_ax_plan_destroy(semax_plan *plan);
  * Returns SEMAX_EINVAL if N is not in the plan. */
 int sem_ax_plan_config(const semax_plan *plan, int N, int *elems_per_tile, int *mapping);
 
+/* ---------------------------------------------------------------- solver around Ax */
+
+/* Direct stiffness summation (gather-scatter) on vectors in local element
+ * form: every local value becomes the sum of the local values that share its
+ * global node (Q Q^T in the usual notation; Deville, Fischer & Mund 2002,
+ * Sec. 4.5).  local_to_global (HOST array, nlocal entries in [0, nglobal))
+ * gives each local node's global node; dirichlet (HOST, nglobal bytes, or
+ * NULL) marks global nodes held at zero when apply_mask is set.  The sums use
+ * a fixed order, so the result is deterministic.  Creating the handle
+ * allocates device memory; applying it does not. */
+typedef struct semax_gs semax_gs;
+int semax_gs_create(semax_gs **gs, int64_t nlocal, const int64_t *local_to_global, int64_t nglobal,
+                    const unsigned char *dirichlet);
+int semax_gs_apply(const semax_gs *gs, double *v, int apply_mask, void *stream);
+int semax_gs_destroy(semax_gs *gs);
+
+/* diag(A_e) of every element (FP64, layout of u): the Jacobi preconditioner's
+ * element part. */
+int sem_ax_diag(int64_t E, int N, const double *G, const double *D, double *diag, void *stream);
+
+/* Jacobi-preconditioned conjugate gradients for Q A_L Q^T x = b with the
+ * homogeneous Dirichlet nodes of gs held at zero -- the PDE solve that
+ * applies Ax once per iteration.  Vectors are continuous local vectors (E n^3
+ * doubles, equal copies at shared nodes); b must already be summed (gs) and
+ * masked.  Create allocates the work vectors and computes the preconditioner;
+ * G, D and gs stay bound to the solver.  Solve starts from x (in/out) and
+ * stops when ||r|| <= rtol ||r_0|| (norms weighted by 1/multiplicity) or after
+ * max_iter iterations, checked every 10 iterations: a block of 10 iterations
+ * is one CUDA-graph launch with all scalars in device memory.  Solve blocks
+ * the host until it returns; it is ordered after earlier work on `stream` and
+ * later work on `stream` is ordered after it. */
+typedef struct semax_pcg semax_pcg;
+int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G, const double *D, const semax_gs *gs);
+int sem_pcg_solve(semax_pcg *pcg, const double *b, double *x, int max_iter, double rtol, int *iters,
+                  double *rel_res, void *stream);
+int sem_pcg_destroy(semax_pcg *pcg);
+
 /* ---------------------------------------------------------------- FP64 checks */
 
 /* FP64 reductions over `count` entries, on the GPU:

@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import SemaxError, semax_group, check, SEMAX_F32, SEMAX_F64
 
-__all__ = ["sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_batched", "Plan", "reduce",
+__all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_batched", "Plan", "reduce",
            "sem_ax_from_host", "SemaxError", "library_path"]
 
 
@@ -176,3 +176,69 @@ def sem_ax_from_host(u_host: torch.Tensor, G_host: torch.Tensor, D_host: torch.T
         sem_ax(bufs["u"], bufs["G"], bufs["D"], bufs["w"], stream=s)
         w_host.copy_(bufs["w"], non_blocking=True)
     return bufs
+
+
+class GatherScatter:
+    """Direct stiffness summation over shared nodes (semax_gs_*)."""
+
+    def __init__(self, local_to_global, nglobal: int, dirichlet=None):
+        import numpy as np
+        l2g = np.ascontiguousarray(local_to_global, dtype=np.int64)
+        self._dir = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8)
+        self._handle = ctypes.c_void_p()
+        check(_lib.lib().semax_gs_create(ctypes.byref(self._handle), l2g.size, l2g.ctypes.data, int(nglobal),
+                                         None if self._dir is None else self._dir.ctypes.data),
+              "semax_gs_create")
+        self.nlocal = l2g.size
+
+    def __call__(self, v: torch.Tensor, mask: bool = True, stream=None) -> torch.Tensor:
+        check(_lib.lib().semax_gs_apply(self._handle, _ptr(v), int(bool(mask)), _stream(stream)), "semax_gs_apply")
+        return v
+
+    def close(self) -> None:
+        if self._handle:
+            check(_lib.lib().semax_gs_destroy(self._handle), "semax_gs_destroy")
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sem_ax_diag(G: torch.Tensor, D: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    n = D.shape[0]
+    E = G.shape[0]
+    if out is None:
+        out = torch.empty((E, n, n, n), dtype=torch.float64, device=G.device)
+    check(_lib.lib().sem_ax_diag(E, n - 1, _ptr(G), _ptr(D), _ptr(out), _stream(stream)), "sem_ax_diag")
+    return out
+
+
+class PCG:
+    """Jacobi-PCG on Q A_L Q^T (sem_pcg_*); G, D and the gather-scatter stay bound."""
+
+    def __init__(self, G: torch.Tensor, D: torch.Tensor, gs: GatherScatter):
+        self._keep = (G, D, gs)
+        self._handle = ctypes.c_void_p()
+        check(_lib.lib().sem_pcg_create(ctypes.byref(self._handle), G.shape[0], D.shape[0] - 1, _ptr(G), _ptr(D),
+                                        gs._handle), "sem_pcg_create")
+
+    def solve(self, b: torch.Tensor, x: torch.Tensor, max_iter: int = 1000, rtol: float = 1e-10,
+              stream=None) -> tuple[int, float]:
+        it, rel = ctypes.c_int(0), ctypes.c_double(0.0)
+        check(_lib.lib().sem_pcg_solve(self._handle, _ptr(b), _ptr(x), int(max_iter), float(rtol), ctypes.byref(it),
+                                       ctypes.byref(rel), _stream(stream)), "sem_pcg_solve")
+        return it.value, rel.value
+
+    def close(self) -> None:
+        if self._handle:
+            check(_lib.lib().sem_pcg_destroy(self._handle), "sem_pcg_destroy")
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -26,6 +26,8 @@ EXPORTS = (
     "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f32", "sem_ax_bf16x3",
     "sem_ax_batched_workspace_size", "sem_ax_batched",
     "sem_ax_plan_create", "sem_ax_plan_exec", "sem_ax_plan_destroy", "sem_ax_plan_config",
+    "semax_gs_create", "semax_gs_apply", "semax_gs_destroy", "sem_ax_diag",
+    "sem_pcg_create", "sem_pcg_solve", "sem_pcg_destroy",
     "semax_reduce_workspace_size", "semax_reduce", "semax_reduce_noalloc",
     "semax_strerror", "semax_last_cuda_error",
 )
@@ -62,6 +64,13 @@ def _load():
         "sem_ax_plan_exec": [vp, vp],
         "sem_ax_plan_destroy": [vp],
         "sem_ax_plan_config": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "semax_gs_create": [ctypes.POINTER(vp), i64, vp, i64, vp],
+        "semax_gs_apply": [vp, vp, i32, vp],
+        "semax_gs_destroy": [vp],
+        "sem_ax_diag": [i64, i32, vp, vp, vp, vp],
+        "sem_pcg_create": [ctypes.POINTER(vp), i64, i32, vp, vp, vp],
+        "sem_pcg_solve": [vp, vp, vp, i32, ctypes.c_double, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double), vp],
+        "sem_pcg_destroy": [vp],
         "semax_reduce_workspace_size": [i64, ctypes.POINTER(sz)],
         "semax_reduce": [i64, vp, i32, vp, i32, vp, vp, sz, vp],
         "semax_reduce_noalloc": [i64, vp, i32, vp, i32, vp, vp],

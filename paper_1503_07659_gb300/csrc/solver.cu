@@ -1,0 +1,461 @@
+// A conjugate-gradient solver around Ax: direct stiffness summation
+// (gather-scatter), the operator's diagonal (Jacobi preconditioner), and a
+// Jacobi-PCG whose iteration is captured once in a CUDA graph and replayed,
+// with every scalar (alpha, beta, residual) kept in device memory so that no
+// host round trip sits inside an iteration.  This is the PDE-solver setting
+// the paper's Section 1 names as Loo.py's first use case.
+//
+// Vectors are kept in local (element) form, E n^3 values; a continuous vector
+// has equal copies at nodes shared by elements.  Direct stiffness summation
+// replaces every local value by the sum of the copies of its global node
+// (Q Q^T); global inner products weight each local product by 1 / (number of
+// copies).  Homogeneous Dirichlet nodes are held at zero by the
+// gather-scatter's mask.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ax_plain.cuh"
+
+namespace semax {
+
+constexpr int kSolverThreads = 256;
+constexpr int kSolverMaxBlocks = 1024;
+
+static int solver_blocks(int64_t count) {
+    int64_t b = (count + kSolverThreads * 4 - 1) / (kSolverThreads * 4);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, kSolverMaxBlocks));
+}
+
+// ---------------------------------------------------------------- gather-scatter
+
+__global__ void __launch_bounds__(kSolverThreads)
+gs_kernel(int64_t nglobal, const int64_t *__restrict__ offsets, const int64_t *__restrict__ locals,
+          const unsigned char *__restrict__ dirichlet, double *__restrict__ v) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nglobal; g += stride) {
+        const int64_t q0 = offsets[g], q1 = offsets[g + 1];
+        double s = 0.0;
+        for (int64_t q = q0; q < q1; ++q) s += v[locals[q]];
+        if (dirichlet && dirichlet[g]) s = 0.0;
+        for (int64_t q = q0; q < q1; ++q) v[locals[q]] = s;
+    }
+}
+
+// ---------------------------------------------------------------- operator diagonal
+
+// diag(A_e) at node (k, j, i):
+//   sum_l D[l][i]^2 Grr[k][j][l] + sum_l D[l][j]^2 Gss[k][l][i] + sum_l D[l][k]^2 Gtt[l][j][i]
+//   + 2 (D[i][i] D[j][j] Grs + D[i][i] D[k][k] Grt + D[j][j] D[k][k] Gst)[k][j][i]
+// (the cross terms D_a^T G_ab D_b touch the diagonal only through q = p).
+template <int n>
+__global__ void __launch_bounds__(kSolverThreads)
+diag_kernel(int64_t E, const double *__restrict__ G, const double *__restrict__ D, double *__restrict__ d) {
+    constexpr int n2 = n * n, n3 = n * n * n;
+    __shared__ double sD[n2];
+    for (int q = threadIdx.x; q < n2; q += blockDim.x) sD[q] = D[q];
+    __syncthreads();
+    const int64_t total = E * n3, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
+        const int64_t e = p / n3;
+        const int q = (int)(p - e * n3), k = q / n2, j = (q / n) % n, i = q % n;
+        const double *Ge = G + e * 6 * n3;
+        double s = 0.0;
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+            s = __fma_rn(sD[l * n + i] * sD[l * n + i], Ge[0 * n3 + k * n2 + j * n + l], s);
+            s = __fma_rn(sD[l * n + j] * sD[l * n + j], Ge[3 * n3 + k * n2 + l * n + i], s);
+            s = __fma_rn(sD[l * n + k] * sD[l * n + k], Ge[5 * n3 + l * n2 + j * n + i], s);
+        }
+        const double di = sD[i * n + i], dj = sD[j * n + j], dk = sD[k * n + k];
+        s += 2.0 * (di * dj * Ge[1 * n3 + q] + di * dk * Ge[2 * n3 + q] + dj * dk * Ge[4 * n3 + q]);
+        d[p] = s;
+    }
+}
+
+// ---------------------------------------------------------------- PCG kernels
+
+enum { S_RZ = 0, S_PAP, S_RR, S_RR0, S_ALPHA, S_BETA, S_COUNT };
+
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *out2) {
+    __shared__ double sh[2][kSolverThreads / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sh[0][warp] = a; sh[1][warp] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < kSolverThreads / 32; ++q) { a += sh[0][q]; b += sh[1][q]; }
+        out2[0] = a;
+        out2[1] = b;
+    }
+}
+
+// partials of sum a b wt and sum c c wt
+__global__ void __launch_bounds__(kSolverThreads)
+dot_kernel(int64_t count, const double *__restrict__ a, const double *__restrict__ b,
+           const double *__restrict__ c, const double *__restrict__ wt, double *__restrict__ part) {
+    double s0 = 0.0, s1 = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride) {
+        s0 = __fma_rn(a[q] * b[q], wt[q], s0);
+        if (c) s1 = __fma_rn(c[q] * c[q], wt[q], s1);
+    }
+    block_sum2(s0, s1, part + 2 * blockIdx.x);
+}
+
+// What to do with the two sums of the partials.
+enum { FIN_PAP = 0, FIN_RZ_RR = 1, FIN_INIT = 2 };
+
+__global__ void __launch_bounds__(kSolverThreads)
+final_kernel(int nparts, const double *__restrict__ part, double *__restrict__ scal, int mode) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += blockDim.x) {
+        s0 += part[2 * q];
+        s1 += part[2 * q + 1];
+    }
+    __shared__ double out[2];
+    block_sum2(s0, s1, out);
+    if (threadIdx.x == 0) {
+        const double a = out[0], b = out[1];
+        if (mode == FIN_PAP) {
+            scal[S_PAP] = a;
+            scal[S_ALPHA] = a != 0.0 ? scal[S_RZ] / a : 0.0;
+        } else if (mode == FIN_RZ_RR) {
+            scal[S_BETA] = scal[S_RZ] != 0.0 ? a / scal[S_RZ] : 0.0;
+            scal[S_RZ] = a;
+            scal[S_RR] = b;
+        } else {
+            scal[S_RZ] = a;
+            scal[S_RR] = b;
+            scal[S_RR0] = b;
+        }
+    }
+}
+
+// x += alpha p; r -= alpha w; z = invdiag r; partials of r.z and r.r (weighted)
+__global__ void __launch_bounds__(kSolverThreads)
+update_kernel(int64_t count, double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
+              const double *__restrict__ p, const double *__restrict__ w, const double *__restrict__ invdiag,
+              const double *__restrict__ wt, const double *__restrict__ scal, double *__restrict__ part) {
+    const double alpha = scal[S_ALPHA];
+    double s0 = 0.0, s1 = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride) {
+        x[q] = __fma_rn(alpha, p[q], x[q]);
+        const double rq = __fma_rn(-alpha, w[q], r[q]);
+        r[q] = rq;
+        const double zq = invdiag[q] * rq;
+        z[q] = zq;
+        s0 = __fma_rn(rq * zq, wt[q], s0);
+        s1 = __fma_rn(rq * rq, wt[q], s1);
+    }
+    block_sum2(s0, s1, part + 2 * blockIdx.x);
+}
+
+// p = z + beta p  (beta_slot < 0: p = z)
+__global__ void __launch_bounds__(kSolverThreads)
+pupdate_kernel(int64_t count, double *__restrict__ p, const double *__restrict__ z,
+               const double *__restrict__ scal, int use_beta) {
+    const double beta = use_beta ? scal[S_BETA] : 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride)
+        p[q] = use_beta ? __fma_rn(beta, p[q], z[q]) : z[q];
+}
+
+// r = b - w; z = invdiag r
+__global__ void __launch_bounds__(kSolverThreads)
+residual_kernel(int64_t count, const double *__restrict__ b, const double *__restrict__ w,
+                const double *__restrict__ invdiag, double *__restrict__ r, double *__restrict__ z) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride) {
+        const double rq = b[q] - w[q];
+        r[q] = rq;
+        z[q] = invdiag[q] * rq;
+    }
+}
+
+// invdiag = free ? 1 / d : 0 (d already summed; Dirichlet nodes were zeroed)
+__global__ void __launch_bounds__(kSolverThreads)
+invert_kernel(int64_t count, double *__restrict__ d) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride)
+        d[q] = d[q] != 0.0 ? 1.0 / d[q] : 0.0;
+}
+
+template <int n>
+static int launch_diag(int64_t E, const double *G, const double *D, double *d, cudaStream_t s) {
+    const int64_t total = E * n * n * n;
+    const int64_t blocks = std::min<int64_t>((total + kSolverThreads - 1) / kSolverThreads, 65535LL * 16);
+    diag_kernel<n><<<(unsigned)blocks, kSolverThreads, 0, s>>>(E, G, D, d);
+    return launch_status();
+}
+
+static int launch_diag_N(int64_t E, int N, const double *G, const double *D, double *d, cudaStream_t s) {
+    switch (N + 1) {
+#define SEMAX_CASE(nn) \
+    case nn: return launch_diag<nn>(E, G, D, d, s);
+        SEMAX_CASE(2) SEMAX_CASE(3) SEMAX_CASE(4) SEMAX_CASE(5) SEMAX_CASE(6) SEMAX_CASE(7)
+        SEMAX_CASE(8) SEMAX_CASE(9) SEMAX_CASE(10) SEMAX_CASE(11) SEMAX_CASE(12) SEMAX_CASE(13)
+        SEMAX_CASE(14) SEMAX_CASE(15) SEMAX_CASE(16)
+#undef SEMAX_CASE
+        default: return SEMAX_EUNSUPPORTED_N;
+    }
+}
+
+}  // namespace semax
+
+using namespace semax;
+
+// ---------------------------------------------------------------- gather-scatter handle
+
+struct semax_gs {
+    int64_t nlocal = 0, nglobal = 0;
+    int64_t *offsets = nullptr;        // [nglobal + 1]
+    int64_t *locals = nullptr;         // [nlocal], grouped by global node
+    unsigned char *dirichlet = nullptr;
+    double *inv_mult = nullptr;        // [nlocal]
+    unsigned magic = 0x95u;
+};
+
+static void gs_free(semax_gs *g) {
+    if (!g) return;
+    cudaFree(g->offsets);
+    cudaFree(g->locals);
+    cudaFree(g->dirichlet);
+    cudaFree(g->inv_mult);
+    g->magic = 0;
+    delete g;
+}
+
+extern "C" int semax_gs_create(semax_gs **gs, int64_t nlocal, const int64_t *l2g, int64_t nglobal,
+                               const unsigned char *dirichlet) {
+    if (!gs) return SEMAX_EINVAL;
+    *gs = nullptr;
+    if (nlocal <= 0 || nglobal <= 0 || !l2g) return SEMAX_EINVAL;
+    std::vector<int64_t> off(nglobal + 1, 0);
+    for (int64_t l = 0; l < nlocal; ++l) {
+        if (l2g[l] < 0 || l2g[l] >= nglobal) return SEMAX_EINVAL;
+        ++off[l2g[l] + 1];
+    }
+    for (int64_t g = 0; g < nglobal; ++g) off[g + 1] += off[g];
+    std::vector<int64_t> loc(nlocal), fill(off.begin(), off.end() - 1);
+    for (int64_t l = 0; l < nlocal; ++l) loc[fill[l2g[l]]++] = l;
+    std::vector<double> im(nlocal);
+    for (int64_t l = 0; l < nlocal; ++l) im[l] = 1.0 / (double)(off[l2g[l] + 1] - off[l2g[l]]);
+    semax_gs *g = new semax_gs();
+    g->nlocal = nlocal;
+    g->nglobal = nglobal;
+    int st = cuda_status(cudaMalloc(&g->offsets, sizeof(int64_t) * (nglobal + 1)));
+    if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&g->locals, sizeof(int64_t) * nlocal));
+    if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&g->inv_mult, sizeof(double) * nlocal));
+    if (st == SEMAX_OK) st = cuda_status(cudaMemcpy(g->offsets, off.data(), sizeof(int64_t) * (nglobal + 1), cudaMemcpyHostToDevice));
+    if (st == SEMAX_OK) st = cuda_status(cudaMemcpy(g->locals, loc.data(), sizeof(int64_t) * nlocal, cudaMemcpyHostToDevice));
+    if (st == SEMAX_OK) st = cuda_status(cudaMemcpy(g->inv_mult, im.data(), sizeof(double) * nlocal, cudaMemcpyHostToDevice));
+    if (st == SEMAX_OK && dirichlet) {
+        st = cuda_status(cudaMalloc(&g->dirichlet, nglobal));
+        if (st == SEMAX_OK) st = cuda_status(cudaMemcpy(g->dirichlet, dirichlet, nglobal, cudaMemcpyHostToDevice));
+    }
+    if (st != SEMAX_OK) {
+        gs_free(g);
+        return st;
+    }
+    *gs = g;
+    return SEMAX_OK;
+}
+
+static int gs_enqueue(const semax_gs *gs, double *v, int apply_mask, cudaStream_t s) {
+    const int blocks = solver_blocks(gs->nglobal);
+    gs_kernel<<<blocks, kSolverThreads, 0, s>>>(gs->nglobal, gs->offsets, gs->locals,
+                                                 apply_mask ? gs->dirichlet : nullptr, v);
+    return launch_status();
+}
+
+extern "C" int semax_gs_apply(const semax_gs *gs, double *v, int apply_mask, void *stream) {
+    if (!gs || gs->magic != 0x95u) return SEMAX_ENOPLAN;
+    if (!v) return SEMAX_EINVAL;
+    return gs_enqueue(gs, v, apply_mask, (cudaStream_t)stream);
+}
+
+extern "C" int semax_gs_destroy(semax_gs *gs) {
+    if (!gs || gs->magic != 0x95u) return SEMAX_ENOPLAN;
+    gs_free(gs);
+    return SEMAX_OK;
+}
+
+extern "C" int sem_ax_diag(int64_t E, int N, const double *G, const double *D, double *diag, void *stream) {
+    if (E < 0) return SEMAX_EINVAL;
+    if (N < 1 || N > kMaxN) return SEMAX_EUNSUPPORTED_N;
+    if (E == 0) return SEMAX_OK;
+    if (!G || !D || !diag) return SEMAX_EINVAL;
+    return launch_diag_N(E, N, G, D, diag, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- PCG
+
+struct semax_pcg {
+    int64_t E = 0;
+    int N = 0;
+    int64_t count = 0;
+    const double *G = nullptr, *D = nullptr;
+    const semax_gs *gs = nullptr;
+    double *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *invdiag = nullptr;
+    double *part = nullptr, *scal = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double *x_bound = nullptr;          // the x the graph was captured with
+    unsigned magic = 0x9c9u;
+};
+
+static const int kItersPerGraph = 10;
+
+static void pcg_free(semax_pcg *s) {
+    if (!s) return;
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    if (s->cs) cudaStreamDestroy(s->cs);
+    cudaFree(s->r);
+    cudaFree(s->z);
+    cudaFree(s->p);
+    cudaFree(s->w);
+    cudaFree(s->invdiag);
+    cudaFree(s->part);
+    cudaFree(s->scal);
+    s->magic = 0;
+    delete s;
+}
+
+// One PCG iteration on stream cs (x is the caller's solution vector).
+static int pcg_iteration(semax_pcg *s, double *x, cudaStream_t cs) {
+    const int blocks = solver_blocks(s->count);
+    int st = launch_plain<double>(s->E, s->N, default_tile<double>(s->N + 1), s->p, s->G, s->D, s->w, nullptr,
+                                  Helm<double>{nullptr, 1.0, 0.0}, cs);
+    if (st == SEMAX_OK) st = gs_enqueue(s->gs, s->w, 1, cs);
+    if (st != SEMAX_OK) return st;
+    dot_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->w, nullptr, s->gs->inv_mult, s->part);
+    final_kernel<<<1, kSolverThreads, 0, cs>>>(blocks, s->part, s->scal, FIN_PAP);
+    update_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, x, s->r, s->z, s->p, s->w, s->invdiag,
+                                                     s->gs->inv_mult, s->scal, s->part);
+    final_kernel<<<1, kSolverThreads, 0, cs>>>(blocks, s->part, s->scal, FIN_RZ_RR);
+    pupdate_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->z, s->scal, 1);
+    return launch_status();
+}
+
+extern "C" int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G, const double *D,
+                              const semax_gs *gs) {
+    if (!pcg) return SEMAX_EINVAL;
+    *pcg = nullptr;
+    if (E <= 0 || !G || !D || !gs || gs->magic != 0x95u) return SEMAX_EINVAL;
+    if (N < 1 || N > kMaxN) return SEMAX_EUNSUPPORTED_N;
+    const int64_t count = E * (N + 1) * (N + 1) * (N + 1);
+    if (gs->nlocal != count) return SEMAX_EINVAL;
+    semax_pcg *s = new semax_pcg();
+    s->E = E;
+    s->N = N;
+    s->count = count;
+    s->G = G;
+    s->D = D;
+    s->gs = gs;
+    const size_t vb = sizeof(double) * (size_t)count;
+    int st = SEMAX_OK;
+    for (double **v : {&s->r, &s->z, &s->p, &s->w, &s->invdiag})
+        if (st == SEMAX_OK) st = cuda_status(cudaMalloc(v, vb));
+    if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->part, sizeof(double) * 2 * kSolverMaxBlocks));
+    if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->scal, sizeof(double) * S_COUNT));
+    if (st == SEMAX_OK) st = cuda_status(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
+    // Jacobi: invdiag = 1 / (Q Q^T diag(A_L)) at free nodes, 0 at Dirichlet nodes
+    if (st == SEMAX_OK) st = launch_diag_N(E, N, G, D, s->invdiag, s->cs);
+    if (st == SEMAX_OK) st = gs_enqueue(gs, s->invdiag, 1, s->cs);
+    if (st == SEMAX_OK) {
+        invert_kernel<<<solver_blocks(count), kSolverThreads, 0, s->cs>>>(count, s->invdiag);
+        st = launch_status();
+    }
+    if (st == SEMAX_OK) st = cuda_status(cudaStreamSynchronize(s->cs));
+    if (st != SEMAX_OK) {
+        pcg_free(s);
+        return st;
+    }
+    *pcg = s;
+    return SEMAX_OK;
+}
+
+extern "C" int sem_pcg_solve(semax_pcg *s, const double *b, double *x, int max_iter, double rtol, int *iters,
+                             double *rel_res, void *stream) {
+    if (!s || s->magic != 0x9c9u) return SEMAX_ENOPLAN;
+    if (!b || !x || max_iter < 0 || !(rtol >= 0.0)) return SEMAX_EINVAL;
+    if (overlaps(x, sizeof(double) * s->count, b, sizeof(double) * s->count)) return SEMAX_EALIAS;
+    cudaStream_t us = (cudaStream_t)stream;
+    cudaStream_t cs = s->cs;
+    // order the solver's stream after the caller's work
+    cudaEvent_t ev;
+    int st = cuda_status(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    if (st != SEMAX_OK) return st;
+    st = cuda_status(cudaEventRecord(ev, us));
+    if (st == SEMAX_OK) st = cuda_status(cudaStreamWaitEvent(cs, ev, 0));
+    // initial residual
+    const int blocks = solver_blocks(s->count);
+    if (st == SEMAX_OK)
+        st = launch_plain<double>(s->E, s->N, default_tile<double>(s->N + 1), x, s->G, s->D, s->w, nullptr,
+                                  Helm<double>{nullptr, 1.0, 0.0}, cs);
+    if (st == SEMAX_OK) st = gs_enqueue(s->gs, s->w, 1, cs);
+    if (st == SEMAX_OK) {
+        residual_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, b, s->w, s->invdiag, s->r, s->z);
+        dot_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->r, s->z, s->r, s->gs->inv_mult, s->part);
+        final_kernel<<<1, kSolverThreads, 0, cs>>>(blocks, s->part, s->scal, FIN_INIT);
+        pupdate_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->z, s->scal, 0);
+        st = launch_status();
+    }
+    // (re)capture a block of iterations bound to this x
+    if (st == SEMAX_OK && s->x_bound != x) {
+        if (s->exec) { cudaGraphExecDestroy(s->exec); s->exec = nullptr; }
+        if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
+        cudaStream_t cap = nullptr;
+        st = cuda_status(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        if (st == SEMAX_OK) st = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        if (st == SEMAX_OK) {
+            int lst = SEMAX_OK;
+            for (int it = 0; it < kItersPerGraph && lst == SEMAX_OK; ++it) lst = pcg_iteration(s, x, cap);
+            int est = cuda_status(cudaStreamEndCapture(cap, &s->graph));
+            st = lst != SEMAX_OK ? lst : est;
+        }
+        if (st == SEMAX_OK) st = cuda_status(cudaGraphInstantiate(&s->exec, s->graph, 0));
+        if (cap) cudaStreamDestroy(cap);
+        s->x_bound = st == SEMAX_OK ? x : nullptr;
+    }
+    double h[S_COUNT] = {0};
+    if (st == SEMAX_OK) st = cuda_status(cudaMemcpyAsync(h, s->scal, sizeof h, cudaMemcpyDeviceToHost, cs));
+    if (st == SEMAX_OK) st = cuda_status(cudaStreamSynchronize(cs));
+    const double rr0 = h[S_RR0];
+    int done = 0;
+    double rel = rr0 > 0.0 ? 1.0 : 0.0;
+    while (st == SEMAX_OK && done < max_iter && rel > rtol) {
+        const int left = max_iter - done;
+        if (left >= kItersPerGraph) {
+            st = cuda_status(cudaGraphLaunch(s->exec, cs));
+            done += kItersPerGraph;
+        } else {
+            for (int it = 0; it < left && st == SEMAX_OK; ++it) st = pcg_iteration(s, x, cs);
+            done += left;
+        }
+        if (st == SEMAX_OK) st = cuda_status(cudaMemcpyAsync(h, s->scal, sizeof h, cudaMemcpyDeviceToHost, cs));
+        if (st == SEMAX_OK) st = cuda_status(cudaStreamSynchronize(cs));
+        rel = rr0 > 0.0 ? std::sqrt(std::max(h[S_RR], 0.0) / rr0) : 0.0;
+    }
+    // the caller's stream continues after the solve
+    if (st == SEMAX_OK) st = cuda_status(cudaEventRecord(ev, cs));
+    if (st == SEMAX_OK) st = cuda_status(cudaStreamWaitEvent(us, ev, 0));
+    cudaEventDestroy(ev);
+    if (iters) *iters = done;
+    if (rel_res) *rel_res = rel;
+    return st;
+}
+
+extern "C" int sem_pcg_destroy(semax_pcg *s) {
+    if (!s || s->magic != 0x9c9u) return SEMAX_ENOPLAN;
+    pcg_free(s);
+    return SEMAX_OK;
+}

@@ -23,6 +23,7 @@ import torch
 from .gll import gll_nodes, gll_weights, gll_diff_matrix, legendre
 from .geometry import (G_COMPONENTS, draw_geometry, vertices, geometric_factors,
                        jacobian_determinants, mass_diagonal)
+from .box import BoxMesh, box_mesh, box_operator_data
 
 SEED_BASE = (1503, 7659)
 
@@ -123,5 +124,5 @@ __all__ = [
     "SEED_BASE", "WORKLOADS", "Mesh", "make_mesh", "make_workload", "batched_orders",
     "rng_for", "per_element_g_scale", "gll_nodes", "gll_weights", "gll_diff_matrix",
     "legendre", "G_COMPONENTS", "draw_geometry", "vertices", "geometric_factors",
-    "jacobian_determinants", "mass_diagonal",
+    "jacobian_determinants", "mass_diagonal", "BoxMesh", "box_mesh", "box_operator_data",
 ]
