@@ -310,24 +310,25 @@ def variants(semax, reps: int) -> dict:
     gs = semax.GatherScatter(bm.l2g, bm.nglobal, bm.boundary)
     b = (B * 3 * torch.pi ** 2 * ue).contiguous()
     gs(b, mask=True)
-    pcg = semax.PCG(G, D, gs)
-    x = torch.zeros_like(b)
-    pcg.solve(b, x, max_iter=20, rtol=0.0)                  # warm-up (captures the graph)
-    x.zero_()
-    torch.cuda.synchronize()
-    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    iters, rel = pcg.solve(b, x, max_iter=5000, rtol=1e-8)
-    c.record()
-    torch.cuda.synchronize()
-    t = a.elapsed_time(c) / 1e3
-    dofs = bm.E * bm.n ** 3
-    out["pcg_jacobi_N7_16x16x16"] = {"iterations": iters, "rel_residual": rel, "seconds": t,
-                                     "us_per_iteration": t / max(iters, 1) * 1e6,
-                                     "gdofs_per_iteration": dofs * iters / t / 1e9,
-                                     "max_error_vs_exact": float((x - ue).abs().max().item()),
-                                     "global_nodes": bm.nglobal}
-    pcg.close()
+    for name, f64x in (("pcg_jacobi_N7_16x16x16", False), ("pcg_jacobi_f64x_N7_16x16x16", True)):
+        pcg = semax.PCG(G, D, gs, f64x=f64x)
+        x = torch.zeros_like(b)
+        pcg.solve(b, x, max_iter=20, rtol=0.0)              # warm-up (captures the graph)
+        x.zero_()
+        torch.cuda.synchronize()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        iters, rel = pcg.solve(b, x, max_iter=5000, rtol=1e-8)
+        c.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(c) / 1e3
+        dofs = bm.E * bm.n ** 3
+        out[name] = {"iterations": iters, "rel_residual": rel, "seconds": t,
+                     "us_per_iteration": t / max(iters, 1) * 1e6,
+                     "gdofs_per_iteration": dofs * iters / t / 1e9,
+                     "max_error_vs_exact": float((x - ue).abs().max().item()),
+                     "global_nodes": bm.nglobal}
+        pcg.close()
     gs.close()
     del G, B, D, ue, b, x
     torch.cuda.empty_cache()

@@ -68,7 +68,7 @@ def _load():
         "semax_gs_apply": [vp, vp, i32, vp],
         "semax_gs_destroy": [vp],
         "sem_ax_diag": [i64, i32, vp, vp, vp, vp],
-        "sem_pcg_create": [ctypes.POINTER(vp), i64, i32, vp, vp, vp],
+        "sem_pcg_create": [ctypes.POINTER(vp), i64, i32, vp, vp, vp, i32],
         "sem_pcg_solve": [vp, vp, vp, i32, ctypes.c_double, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double), vp],
         "sem_pcg_destroy": [vp],
         "semax_reduce_workspace_size": [i64, ctypes.POINTER(sz)],

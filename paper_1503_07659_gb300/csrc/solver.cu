@@ -156,7 +156,7 @@ update_kernel(int64_t count, double *__restrict__ x, double *__restrict__ r, dou
     block_sum2(s0, s1, part + 2 * blockIdx.x);
 }
 
-// p = z + beta p  (beta_slot < 0: p = z)
+// p = z + beta p  (use_beta = 0: p = z)
 __global__ void __launch_bounds__(kSolverThreads)
 pupdate_kernel(int64_t count, double *__restrict__ p, const double *__restrict__ z,
                const double *__restrict__ scal, int use_beta) {
@@ -308,8 +308,19 @@ struct semax_pcg {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     double *x_bound = nullptr;          // the x the graph was captured with
+    int flags = 0;
     unsigned magic = 0x9c9u;
 };
+
+extern "C" int sem_ax_f64x(int64_t E, int N, const double *u, const double *G, const double *D, double *w,
+                           void *stream);
+
+// w = A_L v with the operator the solver was created with
+static int pcg_apply_a(semax_pcg *s, const double *v, double *w, cudaStream_t cs) {
+    if (s->flags & SEMAX_PCG_F64X) return sem_ax_f64x(s->E, s->N, v, s->G, s->D, w, cs);
+    return launch_plain<double>(s->E, s->N, default_tile<double>(s->N + 1), v, s->G, s->D, w, nullptr,
+                                Helm<double>{nullptr, 1.0, 0.0}, cs);
+}
 
 static const int kItersPerGraph = 10;
 
@@ -332,8 +343,7 @@ static void pcg_free(semax_pcg *s) {
 // One PCG iteration on stream cs (x is the caller's solution vector).
 static int pcg_iteration(semax_pcg *s, double *x, cudaStream_t cs) {
     const int blocks = solver_blocks(s->count);
-    int st = launch_plain<double>(s->E, s->N, default_tile<double>(s->N + 1), s->p, s->G, s->D, s->w, nullptr,
-                                  Helm<double>{nullptr, 1.0, 0.0}, cs);
+    int st = pcg_apply_a(s, s->p, s->w, cs);
     if (st == SEMAX_OK) st = gs_enqueue(s->gs, s->w, 1, cs);
     if (st != SEMAX_OK) return st;
     dot_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->w, nullptr, s->gs->inv_mult, s->part);
@@ -346,10 +356,10 @@ static int pcg_iteration(semax_pcg *s, double *x, cudaStream_t cs) {
 }
 
 extern "C" int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G, const double *D,
-                              const semax_gs *gs) {
+                              const semax_gs *gs, int flags) {
     if (!pcg) return SEMAX_EINVAL;
     *pcg = nullptr;
-    if (E <= 0 || !G || !D || !gs || gs->magic != 0x95u) return SEMAX_EINVAL;
+    if (E <= 0 || !G || !D || !gs || gs->magic != 0x95u || (flags & ~SEMAX_PCG_F64X)) return SEMAX_EINVAL;
     if (N < 1 || N > kMaxN) return SEMAX_EUNSUPPORTED_N;
     const int64_t count = E * (N + 1) * (N + 1) * (N + 1);
     if (gs->nlocal != count) return SEMAX_EINVAL;
@@ -360,6 +370,7 @@ extern "C" int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G
     s->G = G;
     s->D = D;
     s->gs = gs;
+    s->flags = flags;
     const size_t vb = sizeof(double) * (size_t)count;
     int st = SEMAX_OK;
     for (double **v : {&s->r, &s->z, &s->p, &s->w, &s->invdiag})
@@ -398,9 +409,7 @@ extern "C" int sem_pcg_solve(semax_pcg *s, const double *b, double *x, int max_i
     if (st == SEMAX_OK) st = cuda_status(cudaStreamWaitEvent(cs, ev, 0));
     // initial residual
     const int blocks = solver_blocks(s->count);
-    if (st == SEMAX_OK)
-        st = launch_plain<double>(s->E, s->N, default_tile<double>(s->N + 1), x, s->G, s->D, s->w, nullptr,
-                                  Helm<double>{nullptr, 1.0, 0.0}, cs);
+    if (st == SEMAX_OK) st = pcg_apply_a(s, x, s->w, cs);
     if (st == SEMAX_OK) st = gs_enqueue(s->gs, s->w, 1, cs);
     if (st == SEMAX_OK) {
         residual_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, b, s->w, s->invdiag, s->r, s->z);

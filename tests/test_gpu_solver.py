@@ -101,6 +101,23 @@ def test_pcg_converges_to_dense_solution(semax, solver_oracle):
     gs.close()
 
 
+def test_pcg_with_double_float_operator_matches(semax, solver_oracle):
+    m, G, B, D, ue, mask = _setup((2, 2, 3), 7, 5)
+    b = mask * solver_oracle.gather_scatter(B.numpy() * 3 * np.pi ** 2 * ue, m.l2g, m.nglobal)
+    gs = semax.GatherScatter(m.l2g, m.nglobal, m.boundary)
+    bd = torch.from_numpy(b).cuda()
+    sols = []
+    for f64x in (False, True):
+        pcg = semax.PCG(G.cuda(), D.cuda(), gs, f64x=f64x)
+        x = torch.zeros_like(bd)
+        it, rel = pcg.solve(bd, x, max_iter=1000, rtol=1e-12)
+        assert rel <= 1e-12
+        sols.append(x.cpu().numpy())
+        pcg.close()
+    assert np.max(np.abs(sols[0] - sols[1])) <= 1e-10 * np.max(np.abs(sols[0]))
+    gs.close()
+
+
 def test_pcg_manufactured_solution_spectral_accuracy(semax, solver_oracle):
     m, G, B, D, ue, mask = _setup((4, 4, 4), 7, 4)
     b = mask * solver_oracle.gather_scatter(B.numpy() * 3 * np.pi ** 2 * ue, m.l2g, m.nglobal)
