@@ -119,7 +119,10 @@ def mass_diagonal(X: np.ndarray, N: int, device="cpu", chunk: int = 8192) -> tor
     Xt = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
     for e0 in range(0, E, chunk):
         J = torch.einsum("cva,pvd->cpad", Xt[e0:e0 + chunk], dN)
-        B[e0:e0 + chunk] = torch.linalg.det(J) * wq[None, :]
+        det = (J[..., 0, 0] * (J[..., 1, 1] * J[..., 2, 2] - J[..., 1, 2] * J[..., 2, 1])
+               - J[..., 0, 1] * (J[..., 1, 0] * J[..., 2, 2] - J[..., 1, 2] * J[..., 2, 0])
+               + J[..., 0, 2] * (J[..., 1, 0] * J[..., 2, 1] - J[..., 1, 1] * J[..., 2, 0]))
+        B[e0:e0 + chunk] = det * wq[None, :]
     return B.view(E, n, n, n)
 
 
