@@ -33,11 +33,10 @@ inline TileConfig default_tile(int n) {
     return c;
 }
 
-// Up to n = 8 a tile fits three times in shared memory, so registers are
-// capped for three resident CTAs per SM; an FP32 tile up to n = 16 fits
-// twice.
+// Registers are capped for three resident CTAs per SM wherever three tiles
+// fit in shared memory: FP64 up to n = 8, FP32 up to n = 16.
 template <typename T, int n, int MAP, bool HELM>
-__global__ void __launch_bounds__(256, (n <= 8 ? 3 : (sizeof(T) == 4 ? 2 : 1)))
+__global__ void __launch_bounds__(256, (n <= 8 || sizeof(T) == 4 ? 3 : 1))
 ax_plain_kernel(int64_t E, int epb, const T *__restrict__ u, const T *__restrict__ G,
                 const T *__restrict__ D, T *__restrict__ w, const T *__restrict__ scale, Helm<T> helm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
