@@ -274,6 +274,8 @@ def variants(semax, reps: int) -> dict:
     dofs = m.dofs
     ref = semax.sem_ax(m.u, m.G, m.D)
     u, G, D = m.u.float(), m.G.float(), m.D.float()
+    X = torch.from_numpy(m.X).float().cuda().contiguous()
+    xq = torch.cat([torch.from_numpy(si.gll_nodes(m.N)), torch.from_numpy(si.gll_weights(m.N))]).float().cuda()
     del m
     w = torch.empty_like(u)
     for name, fn in [("f32", lambda: semax.sem_ax_f32(u, G, D, w)),
@@ -282,7 +284,12 @@ def variants(semax, reps: int) -> dict:
         r = rate(fn, dofs, dofs * bytes_per_node(4))
         r["rel_err_vs_f64"] = rel_err_gpu(semax, w, ref)
         out[f"{name}_N15_E8192"] = r
-    del u, G, D, w, ref
+    # geometric factor recomputed from the vertices: 8 B/node + 96 B/element
+    for name, terms in (("bf16x3_geo", 3), ("bf16x6_geo", 6)):
+        r = rate(lambda: semax.sem_ax_bf16x3_geo(u, X, xq, D, w, terms=terms), dofs, dofs * 8 + 96 * (dofs // 4096))
+        r["rel_err_vs_f64"] = rel_err_gpu(semax, w, ref)
+        out[f"{name}_N15_E8192"] = r
+    del u, G, D, w, ref, X, xq
     torch.cuda.empty_cache()
 
     # uneven orders, one persistent graph-captured launch vs per-order launches

@@ -119,6 +119,19 @@ int sem_ax_f32(int64_t E, int N, const float *u, const float *G, const float *D,
 int sem_ax_bf16x3(int64_t E, int N, const float *u, const float *G, const float *D,
                   float *w, const float *G_scale, int terms, void *stream);
 
+/* The BF16-split tensor-core form with the geometric factor recomputed at
+ * every node instead of read: X [E][8][3] holds each element's vertices
+ * (FP32; vertex v = a + 2b + 4c at reference corner ((-1)^(a+1), (-1)^(b+1),
+ * (-1)^(c+1))), the map is trilinear, and G = w_i w_j w_k adj(J) adj(J)^T /
+ * det(J) is formed in FP32 from the map's coefficients.  xi_wq [32] (device)
+ * holds the 16 GLL nodes then the 16 GLL weights.  A call reads 8 bytes per
+ * node (u, w) plus 96 bytes per element instead of 32 bytes per node.  This
+ * is the paper's store-versus-recompute trade-off (Section 4.1, turning a
+ * stored temporary back into a substitution rule that is recomputed where it
+ * is used).  N = 15 only; terms as in sem_ax_bf16x3. */
+int sem_ax_bf16x3_geo(int64_t E, int N, const float *u, const float *X, const float *xi_wq,
+                      const float *D, float *w, int terms, void *stream);
+
 /* ---------------------------------------------------------------- batched form */
 
 /* One group of E elements of order N (FP64), with its own arrays. */

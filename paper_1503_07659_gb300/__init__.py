@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import SemaxError, semax_group, check, SEMAX_F32, SEMAX_F64
 
-__all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_batched", "Plan", "reduce",
+__all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_bf16x3_geo", "sem_ax_batched", "Plan", "reduce",
            "sem_ax_from_host", "SemaxError", "library_path"]
 
 
@@ -86,6 +86,15 @@ def sem_ax_bf16x3(u, G, D, w=None, G_scale=None, terms: int = 3, stream=None) ->
     w = _out(w, u)
     check(_lib.lib().sem_ax_bf16x3(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _ptr(G_scale),
                                    int(terms), _stream(stream)), "sem_ax_bf16x3")
+    return w
+
+
+def sem_ax_bf16x3_geo(u, X, xi_wq, D, w=None, terms: int = 3, stream=None) -> torch.Tensor:
+    """BF16-split tensor-core form with G recomputed from the vertices X [E,8,3]."""
+    E, N = _dims(u, D)
+    w = _out(w, u)
+    check(_lib.lib().sem_ax_bf16x3_geo(E, N, _ptr(u), _ptr(X), _ptr(xi_wq), _ptr(D), _ptr(w), int(terms),
+                                       _stream(stream)), "sem_ax_bf16x3_geo")
     return w
 
 

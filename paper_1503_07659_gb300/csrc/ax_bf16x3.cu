@@ -145,15 +145,52 @@ __device__ __forceinline__ void load_dfrag(const float *__restrict__ D, DFrag<NP
     }
 }
 
-template <int NP>
+// Geometric factors at node (r, s, t) = (xi_i, xi_j, xi_k) of an element
+// whose trilinear map is x_c = sum_m a[c][m] mono_m(r, s, t), monomials
+// (1, r, s, t, rs, rt, st, rst): J = dx/dxi, G = w adj(J) adj(J)^T / det(J),
+// components (rr, rs, rt, ss, st, tt).  FP32.
+__device__ __forceinline__ void geo_from_map(const float *__restrict__ a, float r, float s, float t, float wq,
+                                             float (&G6)[6]) {
+    float J[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float *ac = a + 8 * c;
+        J[c][0] = __fmaf_rn(ac[7], s * t, __fmaf_rn(ac[5], t, __fmaf_rn(ac[4], s, ac[1])));
+        J[c][1] = __fmaf_rn(ac[7], r * t, __fmaf_rn(ac[6], t, __fmaf_rn(ac[4], r, ac[2])));
+        J[c][2] = __fmaf_rn(ac[7], r * s, __fmaf_rn(ac[6], s, __fmaf_rn(ac[5], r, ac[3])));
+    }
+    const float A = J[0][0], B = J[0][1], C = J[0][2];
+    const float Dd = J[1][0], Ee = J[1][1], F = J[1][2];
+    const float Gg = J[2][0], H = J[2][1], I = J[2][2];
+    const float adj[3][3] = {{Ee * I - F * H, C * H - B * I, B * F - C * Ee},
+                             {F * Gg - Dd * I, A * I - C * Gg, C * Dd - A * F},
+                             {Dd * H - Ee * Gg, B * Gg - A * H, A * Ee - B * Dd}};
+    const float det = A * adj[0][0] + B * adj[1][0] + C * adj[2][0];
+    const float sc = wq * __frcp_rn(det);
+    int m = 0;
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = p; q < 3; ++q)
+            G6[m++] = sc * (adj[p][0] * adj[q][0] + adj[p][1] * adj[q][1] + adj[p][2] * adj[q][2]);
+}
+
+// GEO = false: G is the stored [E][6][16][16][16] factor.
+// GEO = true:  G is the element vertices [E][8][3] (FP32) and xq = (GLL nodes
+// [16], GLL weights [16]); the factor is recomputed at every node from the
+// trilinear map (96 bytes per element read instead of 96 KB).
+template <int NP, bool GEO>
 __global__ void __launch_bounds__(kThreads, 2)
 ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__ G,
-               const float *__restrict__ D, float *__restrict__ w, const float *__restrict__ scale) {
+               const float *__restrict__ D, float *__restrict__ w, const float *__restrict__ scale,
+               const float *__restrict__ xq) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *upc = smem;                                // NP pieces of u
     unsigned char *wpc = smem + NP * kPieceBytes;             // NP pieces of wt
     float *W = reinterpret_cast<float *>(smem + 2 * NP * kPieceBytes);
+    float *sgeo = W + kWBytes / 4;                            // GEO: map coefficients [3][8], xi [16], wq [16]
     const uint32_t upc_s = smem_addr(upc), wpc_s = smem_addr(wpc);
+    if (GEO && threadIdx.x < 32) sgeo[24 + threadIdx.x] = xq[threadIdx.x];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
@@ -164,8 +201,20 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
 
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         const float *ue = u + e * 4096;
-        const float *Ge = G + e * 6 * 4096;
+        const float *Ge = G + e * (GEO ? 24 : 6 * 4096);
         float *we = w + e * 4096;
+        if (GEO && tid < 24) {   // trilinear map coefficients of this element
+            const int c = tid >> 3, m = tid & 7;
+            float acc = 0.f;
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const float sr = (v & 1) ? 1.f : -1.f, ss = (v & 2) ? 1.f : -1.f, st = (v & 4) ? 1.f : -1.f;
+                const float b = m == 0 ? 1.f : m == 1 ? sr : m == 2 ? ss : m == 3 ? st
+                              : m == 4 ? sr * ss : m == 5 ? sr * st : m == 6 ? ss * st : sr * ss * st;
+                acc = __fmaf_rn(b, Ge[3 * v + c], acc);
+            }
+            sgeo[8 * c + m] = 0.125f * acc;
+        }
 
         // ---- load u, split into pieces
 #pragma unroll
@@ -211,18 +260,34 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
             const int k = 2 * warp + kk;
             // geometric factors of this thread's 8 nodes (2 n-tiles x 2 row halves)
             float2 gv[6][2][2];
-#pragma unroll
-            for (int comp = 0; comp < 6; ++comp)
+            if constexpr (GEO) {
+                const float tk = sgeo[24 + k], wk = sgeo[40 + k];
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const float *p = Ge + comp * 4096 + k * 256 + (g + 8 * h) * 16 + 8 * nt + 2 * t;
-                        float2 v;
-                        asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0,%1}, [%2];"
-                                     : "=f"(v.x), "=f"(v.y) : "l"(p));
-                        gv[comp][nt][h] = v;
+                        const int j = g + 8 * h, i0 = 8 * nt + 2 * t;
+                        const float sj = sgeo[24 + j], wjk = sgeo[40 + j] * wk;
+                        float g0[6], g1[6];
+                        geo_from_map(sgeo, sgeo[24 + i0], sj, tk, sgeo[40 + i0] * wjk, g0);
+                        geo_from_map(sgeo, sgeo[25 + i0], sj, tk, sgeo[41 + i0] * wjk, g1);
+#pragma unroll
+                        for (int comp = 0; comp < 6; ++comp) gv[comp][nt][h] = make_float2(g0[comp], g1[comp]);
                     }
+            } else {
+#pragma unroll
+                for (int comp = 0; comp < 6; ++comp)
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float *p = Ge + comp * 4096 + k * 256 + (g + 8 * h) * 16 + 8 * nt + 2 * t;
+                            float2 v;
+                            asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0,%1}, [%2];"
+                                         : "=f"(v.x), "=f"(v.y) : "l"(p));
+                            gv[comp][nt][h] = v;
+                        }
+            }
             uint32_t au[NP][4], bu[NP][4];
             const uint32_t off = swz(k, lr + 8 * (lm & 1), 8 * (lm >> 1));
 #pragma unroll
@@ -348,11 +413,11 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
     }
 }
 
-template <int NP>
+template <int NP, bool GEO>
 static int launch(int64_t E, const float *u, const float *G, const float *D, float *w, const float *scale,
-                  cudaStream_t s) {
-    const size_t smem = 2 * NP * kPieceBytes + kWBytes;
-    auto kern = ax_bf16_kernel<NP>;
+                  const float *xq, cudaStream_t s) {
+    const size_t smem = 2 * NP * kPieceBytes + kWBytes + (GEO ? 64 * sizeof(float) : 0);
+    auto kern = ax_bf16_kernel<NP, GEO>;
     int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (st != SEMAX_OK) return st;
     int per_sm = 0;
@@ -361,7 +426,7 @@ static int launch(int64_t E, const float *u, const float *G, const float *D, flo
     if (per_sm < 1) return SEMAX_EINVAL;
     int64_t grid = (int64_t)per_sm * device_sm_count();
     if (grid > E) grid = E;
-    kern<<<(unsigned)grid, kThreads, smem, s>>>(E, u, G, D, w, scale);
+    kern<<<(unsigned)grid, kThreads, smem, s>>>(E, u, G, D, w, scale, xq);
     return launch_status();
 }
 
@@ -378,6 +443,24 @@ extern "C" int sem_ax_bf16x3(int64_t E, int N, const float *u, const float *G, c
     if (N != 15) return SEMAX_EUNSUPPORTED_N;
     if (G_scale && overlaps(w, (size_t)E * 4096 * sizeof(float), G_scale, (size_t)E * sizeof(float)))
         return SEMAX_EALIAS;
-    if (terms == 3) return tc::launch<2>(E, u, G, D, w, G_scale, (cudaStream_t)stream);
-    return tc::launch<3>(E, u, G, D, w, G_scale, (cudaStream_t)stream);
+    if (terms == 3) return tc::launch<2, false>(E, u, G, D, w, G_scale, nullptr, (cudaStream_t)stream);
+    return tc::launch<3, false>(E, u, G, D, w, G_scale, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int sem_ax_bf16x3_geo(int64_t E, int N, const float *u, const float *X, const float *xi_wq,
+                                 const float *D, float *w, int terms, void *stream) {
+    if (terms != 3 && terms != 6) return SEMAX_EINVAL;
+    if (E < 0) return SEMAX_EINVAL;
+    if (N < 1 || N > kMaxN) return SEMAX_EUNSUPPORTED_N;
+    if (E == 0) return SEMAX_OK;
+    if (!u || !X || !xi_wq || !D || !w) return SEMAX_EINVAL;
+    if (N != 15) return SEMAX_EUNSUPPORTED_N;
+    if (!aligned16(u) || !aligned16(w) || ((uintptr_t)X & 3u) || ((uintptr_t)xi_wq & 3u) || ((uintptr_t)D & 3u))
+        return SEMAX_EALIGN;
+    const size_t ub = (size_t)E * 4096 * sizeof(float);
+    if (overlaps(w, ub, u, ub) || overlaps(w, ub, X, (size_t)E * 24 * sizeof(float)) ||
+        overlaps(w, ub, D, 256 * sizeof(float)) || overlaps(w, ub, xi_wq, 32 * sizeof(float)))
+        return SEMAX_EALIAS;
+    if (terms == 3) return tc::launch<2, true>(E, u, X, D, w, nullptr, xi_wq, (cudaStream_t)stream);
+    return tc::launch<3, true>(E, u, X, D, w, nullptr, xi_wq, (cudaStream_t)stream);
 }

@@ -101,3 +101,14 @@ def test_helmholtz_validation(lib):
     assert f(4, 7, u, G, B + 8, D, C.c_double(1.0), C.c_double(0.0), w, None) == -3      # B misaligned
     assert f(4, 7, u, G, w + 64, D, C.c_double(1.0), C.c_double(0.0), w, None) == -4     # w overlaps B
     assert f(4, 16, u, G, B, D, C.c_double(1.0), C.c_double(0.0), w, None) == -2
+
+
+def test_bf16_geo_validation(lib):
+    f = lib.sem_ax_bf16x3_geo
+    u, X, xq, D, w = A, A + (1 << 32), A + (5 << 32), A + (2 << 32), A + (3 << 32)
+    assert f(0, 15, None, None, None, None, None, 3, None) == 0
+    assert f(4, 15, u, X, xq, D, w, 4, None) == -1
+    assert f(4, 7, u, X, xq, D, w, 3, None) == -2
+    assert f(4, 15, u, None, xq, D, w, 3, None) == -1
+    assert f(4, 15, u + 4, X, xq, D, w, 3, None) == -3
+    assert f(4, 15, u, X, xq, D, u + 64, 3, None) == -4

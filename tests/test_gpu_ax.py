@@ -264,6 +264,38 @@ def test_bf16_split_scaled_matches_unscaled(semax, terms):
     assert torch.equal(w0, w1)
 
 
+def _geo_inputs(m):
+    X = torch.from_numpy(m.X).float().cuda().contiguous()
+    xq = torch.cat([torch.from_numpy(si.gll_nodes(m.N)), torch.from_numpy(si.gll_weights(m.N))]).float().cuda()
+    return X, xq
+
+
+@pytest.mark.parametrize("terms", [3, 6])
+@pytest.mark.parametrize("E", [1, 5, 130])
+def test_bf16_geo_against_f64_oracle(semax, oracle_mod, terms, E):
+    """G recomputed from FP32 vertices inside the kernel; the oracle uses the
+    FP64 G of the same (FP64) vertices."""
+    m = si.make_mesh(np.random.default_rng(800 + E), E, 15)
+    ref = oracle_mod.sem_ax(m.u, m.G, m.D)
+    X, xq = _geo_inputs(m)
+    w = semax.sem_ax_bf16x3_geo(m.u.float().cuda(), X, xq, m.D.float().cuda(), terms=terms)
+    torch.cuda.synchronize()
+    err = rel_err(w, ref)
+    assert err <= TOL_BF16[terms], err
+
+
+def test_bf16_geo_matches_stored_g_form(semax):
+    """Recomputed and stored (FP32-rounded) geometric factors agree to FP32
+    rounding, so the two forms agree far inside the BF16 split's error."""
+    m = si.make_mesh(np.random.default_rng(810), 64, 15, device="cuda")
+    X, xq = _geo_inputs(m)
+    u, D = m.u.float(), m.D.float()
+    a = semax.sem_ax_bf16x3_geo(u, X, xq, D, terms=6)
+    b = semax.sem_ax_bf16x3(u, m.G.float(), D, terms=6)
+    torch.cuda.synchronize()
+    assert ((a - b).abs().max() / b.abs().max()).item() <= 2e-6
+
+
 def test_bf16_rejects_other_orders(semax):
     m = si.make_mesh(np.random.default_rng(1), 2, 7, device="cuda")
     with pytest.raises(semax.SemaxError, match="UNSUPPORTED_N"):
