@@ -145,20 +145,11 @@ __device__ __forceinline__ void load_dfrag(const float *__restrict__ D, DFrag<NP
     }
 }
 
-// Geometric factors at node (r, s, t) = (xi_i, xi_j, xi_k) of an element
-// whose trilinear map is x_c = sum_m a[c][m] mono_m(r, s, t), monomials
-// (1, r, s, t, rs, rt, st, rst): J = dx/dxi, G = w adj(J) adj(J)^T / det(J),
-// components (rr, rs, rt, ss, st, tt).  FP32.
-__device__ __forceinline__ void geo_from_map(const float *__restrict__ a, float r, float s, float t, float wq,
-                                             float (&G6)[6]) {
-    float J[3][3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float *ac = a + 8 * c;
-        J[c][0] = __fmaf_rn(ac[7], s * t, __fmaf_rn(ac[5], t, __fmaf_rn(ac[4], s, ac[1])));
-        J[c][1] = __fmaf_rn(ac[7], r * t, __fmaf_rn(ac[6], t, __fmaf_rn(ac[4], r, ac[2])));
-        J[c][2] = __fmaf_rn(ac[7], r * s, __fmaf_rn(ac[6], s, __fmaf_rn(ac[5], r, ac[3])));
-    }
+// G = wq adj(J) adj(J)^T / det(J), components (rr, rs, rt, ss, st, tt), for
+// the Jacobian J[c][d] = dx_c / dxi_d of an element's trilinear map at one
+// node (the map x_c = sum_m a[c][m] mono_m(r, s, t) over the monomials
+// (1, r, s, t, rs, rt, st, rst) is evaluated by the caller).  FP32.
+__device__ __forceinline__ void geo_from_jacobian(const float (&J)[3][3], float wq, float (&G6)[6]) {
     const float A = J[0][0], B = J[0][1], C = J[0][2];
     const float Dd = J[1][0], Ee = J[1][1], F = J[1][2];
     const float Gg = J[2][0], H = J[2][1], I = J[2][2];
@@ -261,19 +252,43 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
             // geometric factors of this thread's 8 nodes (2 n-tiles x 2 row halves)
             float2 gv[6][2][2];
             if constexpr (GEO) {
+                // Along a line of fixed (s, t) = (xi_j, xi_k), dx/dr is constant and
+                // dx/ds, dx/dt are linear in r: 15 line constants serve 4 nodes.
                 const float tk = sgeo[24 + k], wk = sgeo[40 + k];
 #pragma unroll
-                for (int nt = 0; nt < 2; ++nt)
+                for (int h = 0; h < 2; ++h) {
+                    const int j = g + 8 * h;
+                    const float sj = sgeo[24 + j], wjk = sgeo[40 + j] * wk;
+                    float j0[3], j1a[3], j1b[3], j2a[3], j2b[3];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int j = g + 8 * h, i0 = 8 * nt + 2 * t;
-                        const float sj = sgeo[24 + j], wjk = sgeo[40 + j] * wk;
-                        float g0[6], g1[6];
-                        geo_from_map(sgeo, sgeo[24 + i0], sj, tk, sgeo[40 + i0] * wjk, g0);
-                        geo_from_map(sgeo, sgeo[25 + i0], sj, tk, sgeo[41 + i0] * wjk, g1);
-#pragma unroll
-                        for (int comp = 0; comp < 6; ++comp) gv[comp][nt][h] = make_float2(g0[comp], g1[comp]);
+                    for (int c = 0; c < 3; ++c) {
+                        const float *ac = sgeo + 8 * c;
+                        j0[c] = __fmaf_rn(ac[7], sj * tk, __fmaf_rn(ac[5], tk, __fmaf_rn(ac[4], sj, ac[1])));
+                        j1a[c] = __fmaf_rn(ac[6], tk, ac[2]);
+                        j1b[c] = __fmaf_rn(ac[7], tk, ac[4]);
+                        j2a[c] = __fmaf_rn(ac[6], sj, ac[3]);
+                        j2b[c] = __fmaf_rn(ac[7], sj, ac[5]);
                     }
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) {
+                        float gg[2][6];
+#pragma unroll
+                        for (int x = 0; x < 2; ++x) {
+                            const int i = 8 * nt + 2 * t + x;
+                            const float r = sgeo[24 + i];
+                            float J[3][3];
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                J[c][0] = j0[c];
+                                J[c][1] = __fmaf_rn(j1b[c], r, j1a[c]);
+                                J[c][2] = __fmaf_rn(j2b[c], r, j2a[c]);
+                            }
+                            geo_from_jacobian(J, sgeo[40 + i] * wjk, gg[x]);
+                        }
+#pragma unroll
+                        for (int comp = 0; comp < 6; ++comp) gv[comp][nt][h] = make_float2(gg[0][comp], gg[1][comp]);
+                    }
+                }
             } else {
 #pragma unroll
                 for (int comp = 0; comp < 6; ++comp)
