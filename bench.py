@@ -302,6 +302,14 @@ def variants(semax, reps: int) -> dict:
     out["batched_plan_mix"] = r
     out["per_order_launches_mix"] = rate(lambda: [semax.sem_ax(x.u, x.G, x.D, w) for x, w in zip(mix, ws)],
                                          dofs, dofs * bytes_per_node(8))
+    ref_ws = [w.clone() for w in ws]
+    planx = semax.Plan([(x.N, x.u, x.G, x.D, w) for x, w in zip(mix, ws)], f64x=True)
+    r = rate(planx, dofs, dofs * bytes_per_node(8))
+    r["rel_err_vs_f64"] = max(rel_err_gpu(semax, w, rw) for w, rw in zip(ws, ref_ws))
+    r["arith"] = "double-float tiles (FP64 in/out, FP64-accurate) in the one persistent launch"
+    out["batched_plan_f64x_mix"] = r
+    planx.close()
+    del ref_ws
     out["mix_orders"] = {x.N: x.E for x in mix}
     plan.close()
     del mix, ws

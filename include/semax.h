@@ -165,16 +165,21 @@ int sem_ax_batched(const semax_group *groups, int ngroups, void *workspace,
  *   tune = 1: time the candidate (elements per tile, thread mapping) pairs for
  *             every order present on the current device and keep the fastest;
  *             the choice is written to cache_path (JSON) if not NULL.
+ *   flags = SEMAX_PLAN_F64X: even orders take the double-float FP64-accurate
+ *             tile (error ~1e-14 of ||w||_inf) instead of the FP64 tiles and
+ *             are not tuned; odd orders are unaffected.
  * The group arrays are bound into the plan: they must stay valid while the
  * plan is used (tuning runs the kernel on them, overwriting their w). */
 typedef struct semax_plan semax_plan;
+enum { SEMAX_PLAN_F64X = 1 };   /* even orders use the double-float FP64-accurate tile of sem_ax_f64x */
 int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, int ngroups,
-                       int tune, const char *cache_path);
+                       int tune, const char *cache_path, int flags);
 int sem_ax_plan_exec(semax_plan *plan, void *stream);
 int sem_ax_plan_destroy(semax_plan *plan);
 /* The configuration the plan uses for order N: elements per tile and thread
  * mapping (0 = one thread per node, 1 = one thread per (i,j) column,
- * 2 = one thread per line with the even/odd split of D, even n only).
+ * 2 = one thread per line with the even/odd split of D, even n only,
+ * 3 = the double-float tile of sem_ax_f64x, chosen by SEMAX_PLAN_F64X).
  * Returns SEMAX_EINVAL if N is not in the plan. */
 int sem_ax_plan_config(const semax_plan *plan, int N, int *elems_per_tile, int *mapping);
 

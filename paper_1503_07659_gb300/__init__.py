@@ -121,11 +121,11 @@ def sem_ax_batched(groups, workspace: torch.Tensor | None = None, stream=None) -
 class Plan:
     """Graph-captured persistent batched launch (see sem_ax_plan_create)."""
 
-    def __init__(self, groups, tune: bool = False, cache_path: str | None = None):
+    def __init__(self, groups, tune: bool = False, cache_path: str | None = None, f64x: bool = False):
         self._arr, ng = _groups(groups)
         self._handle = ctypes.c_void_p()
         check(_lib.lib().sem_ax_plan_create(ctypes.byref(self._handle), self._arr, ng, int(bool(tune)),
-                                            cache_path.encode() if cache_path else None),
+                                            cache_path.encode() if cache_path else None, 1 if f64x else 0),
               "sem_ax_plan_create")
 
     def __call__(self, stream=None) -> None:

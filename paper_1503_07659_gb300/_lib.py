@@ -61,7 +61,7 @@ def _load():
         "sem_ax_bf16x3_geo": [i64, i32, vp, vp, vp, vp, vp, i32, vp],
         "sem_ax_batched_workspace_size": [vp, i32, ctypes.POINTER(sz)],
         "sem_ax_batched": [vp, i32, vp, sz, vp],
-        "sem_ax_plan_create": [ctypes.POINTER(vp), vp, i32, i32, ctypes.c_char_p],
+        "sem_ax_plan_create": [ctypes.POINTER(vp), vp, i32, i32, ctypes.c_char_p, i32],
         "sem_ax_plan_exec": [vp, vp],
         "sem_ax_plan_destroy": [vp],
         "sem_ax_plan_config": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],

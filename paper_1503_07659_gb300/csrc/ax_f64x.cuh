@@ -1,0 +1,385 @@
+// FP64-accurate Ax with the six contractions in double-float arithmetic.
+//
+// GB300 issues FP32 62.5 times faster than FP64 (2 DFMA/clk/SM), so the FP64
+// form of Ax is bound by the FP64 pipe at 1.73 flop/B.  This kernel keeps
+// FP64 inputs, outputs and geometric-factor multiply, but runs the
+// contractions on the FP32 pipe with each value held as an unevaluated sum
+// hi + lo of two floats (double-float, ~47 significant bits):
+//   * per element, u is scaled by a power of two so that its largest entry
+//     lies in [1, 2) (exact), and split hi + lo by integer bit operations
+//     (hi = the top 24 significant bits, lo = the next 23);
+//   * products use the exact FMA residual (p = a*b, fma(a, b, -p)) and sums
+//     the error-free two-sum, so each operation errs by ~2^-46 of its
+//     operands' magnitude;
+//   * the gradient (even/odd lines, as MAP_EO) is converted to FP64 for the
+//     G multiply, the result is scaled per element by a power of two again,
+//     split, and the transposed contractions run in double-float;
+//   * the final sum is converted to FP64 and the two scales are undone.
+// The error against the FP64 definition stays near 1e-14 of ||w||_inf,
+// inside the 1e-12 that FP64 Ax is held to.  Intended for even n with a
+// centro-antisymmetric D (the GLL derivative); anything else takes the FP64
+// tile.  The published double-word algorithms (Dekker 1971; Joldes, Muller
+// & Popescu, ACM TOMS 2017) are the basis of the arithmetic.
+#pragma once
+
+#include "ax_tile.cuh"
+
+namespace semax {
+namespace dfx {
+
+struct __align__(8) df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df add(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(a.lo, b.lo), s.lo));
+}
+
+__device__ __forceinline__ df sub(df a, df b) { return add(a, df{-b.hi, -b.lo}); }
+
+// acc + p * x
+__device__ __forceinline__ df fma_df(df p, df x, df acc) {
+    const float m = __fmul_rn(p.hi, x.hi);
+    float r = __fmaf_rn(p.hi, x.hi, -m);
+    r = __fmaf_rn(p.hi, x.lo, r);
+    r = __fmaf_rn(p.lo, x.hi, r);
+    const df s = two_sum(acc.hi, m);
+    return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(acc.lo, r), s.lo));
+}
+
+// Dot-product accumulator in the manner of Ogita, Rump & Oishi's Dot2: s
+// carries the running float sum, c the sum of every rounding error (exact
+// product residuals, cross terms, two-sum errors); s + c is the result.
+struct acc2 {
+    float s, c;
+};
+
+// a += p * x  (p, x double-float)
+__device__ __forceinline__ void dot2_step(acc2 &a, df p, df x) {
+    const float m = __fmul_rn(p.hi, x.hi);
+    float r = __fmaf_rn(p.hi, x.hi, -m);
+    r = __fmaf_rn(p.hi, x.lo, r);
+    r = __fmaf_rn(p.lo, x.hi, r);
+    const df t = two_sum(a.s, m);
+    a.s = t.hi;
+    a.c = __fadd_rn(a.c, __fadd_rn(r, t.lo));
+}
+
+// (a.s + a.c) +/- (b.s + b.c) as a normalised double-float
+__device__ __forceinline__ df acc_add(acc2 a, acc2 b) {
+    const df t = two_sum(a.s, b.s);
+    return fast_two_sum(t.hi, __fadd_rn(__fadd_rn(a.c, b.c), t.lo));
+}
+__device__ __forceinline__ df acc_sub(acc2 a, acc2 b) { return acc_add(a, acc2{-b.s, -b.c}); }
+
+// 2^k as a float, k in [-126, 127]
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(k + 127) << 23); }
+
+// x * 2^-sh split into hi + lo by bit operations (no FP64 instruction).
+// Values whose scaled magnitude is below the float range flush to zero.
+__device__ __forceinline__ df split_double(double x, int sh) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+    const int eb = (int)((hi32 >> 20) & 0x7ffu);
+    const int ef = eb - sh - 1023 + 127;             // biased float exponent of hi
+    if (eb == 0 || ef < 1) return {0.f, 0.f};
+    const unsigned sign = hi32 & 0x80000000u;
+    const unsigned mh = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+    const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | mh);
+    const unsigned r23 = (lo32 >> 6) & 0x7fffffu;
+    const float r = __fsub_rn(__uint_as_float(0x4B000000u | r23), 8388608.0f);   // = r23 exactly
+    const int k = ef - 127 - 46;                      // lo = r23 * 2^k
+    float lo = k >= -126 ? __fmul_rn(r, pow2f(k)) : __fmul_rn(__fmul_rn(r, pow2f(k + 64)), pow2f(-64));
+    if (sign) lo = -lo;
+    return {hi, lo};
+}
+
+// a float (normal or zero) as a double, exactly, by bit operations
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0) return 0.0;
+    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+__device__ __forceinline__ double to_double(df a) { return f2d(a.hi) + f2d(a.lo); }
+
+// f * 2^sh as a double by adding sh to the exponent field; false when the
+// result would leave the normal double range (the caller then multiplies).
+__device__ __forceinline__ bool f2d_scaled(float f, int sh, double &out) {
+    const unsigned b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0) { out = 0.0; return true; }
+    const int ed = e + 896 + sh;
+    if (ed < 1 || ed > 2046) return false;
+    out = __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) |
+                                           ((unsigned long long)ed << 52) |
+                                           ((unsigned long long)(b & 0x7fffffu) << 29)));
+    return true;
+}
+
+__device__ __forceinline__ int biased_exponent(double x) {
+    return (int)((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7ffu);
+}
+
+// h coefficients (df) from shared memory; volatile so they are not hoisted
+template <int h>
+__device__ __forceinline__ void ld_coef(const df *p, df (&c)[h]) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    if constexpr (h % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < h / 2; ++q)
+            asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                         : "=f"(c[2 * q].hi), "=f"(c[2 * q].lo), "=f"(c[2 * q + 1].hi), "=f"(c[2 * q + 1].lo)
+                         : "r"(a + 16 * q));
+    } else {
+#pragma unroll
+        for (int q = 0; q < h; ++q)
+            asm volatile("ld.shared.v2.f32 {%0,%1}, [%2];" : "=f"(c[q].hi), "=f"(c[q].lo) : "r"(a + 8 * q));
+    }
+}
+
+// y = M x by the even/odd split (P, Q: h x h df, row-major); each output
+// pair is written to shared memory as soon as it is formed (y[l * stride]),
+// so no output array stays live in registers.
+template <int n>
+__device__ __forceinline__ void eo_apply_st(const df (&x)[n], const df *P, const df *Q, df *y, int stride) {
+    constexpr int h = n / 2;
+    df e[h], o[h];
+#pragma unroll
+    for (int l = 0; l < h; ++l) {
+        e[l] = add(x[l], x[n - 1 - l]);
+        o[l] = sub(x[l], x[n - 1 - l]);
+    }
+#pragma unroll 1
+    for (int i = 0; i < h; ++i) {
+        df p[h], q[h];
+        ld_coef<h>(P + i * h, p);
+        ld_coef<h>(Q + i * h, q);
+        acc2 pe{0.f, 0.f}, qo{0.f, 0.f};
+#pragma unroll
+        for (int l = 0; l < h; ++l) {
+            dot2_step(pe, p[l], e[l]);
+            dot2_step(qo, q[l], o[l]);
+        }
+        y[i * stride] = acc_add(qo, pe);
+        y[(n - 1 - i) * stride] = acc_sub(qo, pe);
+    }
+}
+
+template <int n>
+__device__ __forceinline__ void ld_line(const df *p, int stride, df (&x)[n]) {
+    if (stride == 1) {
+#pragma unroll
+        for (int q = 0; q < n / 2; ++q) {
+            const float4 v = reinterpret_cast<const float4 *>(p)[q];
+            x[2 * q] = {v.x, v.y};
+            x[2 * q + 1] = {v.z, v.w};
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < n; ++l) x[l] = p[l * stride];
+    }
+}
+
+// raw FP64 line -> df with shift sh
+template <int n>
+__device__ __forceinline__ void ld_line_split(const df *p, int stride, int sh, df (&x)[n]) {
+    const double *d = reinterpret_cast<const double *>(p);
+    if (stride == 1) {
+#pragma unroll
+        for (int q = 0; q < n / 2; ++q) {
+            const double2 v = reinterpret_cast<const double2 *>(d)[q];
+            x[2 * q] = split_double(v.x, sh);
+            x[2 * q + 1] = split_double(v.y, sh);
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < n; ++l) x[l] = split_double(d[l * stride], sh);
+    }
+}
+
+// Per-element maximum of biased exponents: lanes of a warp that work on the
+// same element combine first, then one shared atomic per group.
+__device__ __forceinline__ void exp_max(int *slot_base, int e, int ex) {
+    const unsigned grp = __match_any_sync(__activemask(), e);
+    const int m = __reduce_max_sync(grp, ex);
+    if ((__ffs(grp) - 1) == (int)(threadIdx.x & 31)) atomicMax(slot_base + e, m);
+}
+
+constexpr int kThreads = 256;
+
+template <int n>
+__host__ __device__ constexpr int elems_per_tile() { return kThreads / (n * n) > 0 ? kThreads / (n * n) : 1; }
+
+template <int n>
+__host__ __device__ constexpr size_t smem_bytes(int epb) {
+    return sizeof(double) * (size_t)round_up(n * n, 2) + sizeof(df) * 4 * (n / 2) * (n / 2) +
+           sizeof(int) * (size_t)round_up(2 * epb, 4) + sizeof(df) * 3 * (size_t)epb * eo_elem_pitch<double>(n);
+}
+
+// One tile of cnt (<= epb) consecutive elements; ue, Ge, we point at its
+// first element; smem_raw holds smem_bytes<n>(epb) bytes.  All threads of the
+// block take part (blockDim.x = kThreads).
+template <int n>
+__device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__restrict__ ue,
+                                          const double *__restrict__ Ge, const double *__restrict__ D,
+                                          double *__restrict__ we, unsigned char *smem_raw) {
+    constexpr int n2 = n * n, n3 = n * n * n, h = n / 2;
+    constexpr int RP = eo_row_pitch<double>(n), PP = eo_plane_pitch<double>(n), EP = eo_elem_pitch<double>(n);
+    double *sD = reinterpret_cast<double *>(smem_raw);
+    df *coef = reinterpret_cast<df *>(sD + round_up(n2, 2));
+    int *sexp = reinterpret_cast<int *>(coef + 4 * h * h);      // [0, epb): u, [epb, 2 epb): w
+    df *su = reinterpret_cast<df *>(sexp + round_up(2 * epb, 4));
+    df *sr = su + cnt * EP, *ss = sr + cnt * EP;   // the t-direction reuses su
+
+    for (int q = threadIdx.x; q < n2; q += blockDim.x) sD[q] = D[q];
+    if (threadIdx.x < 2 * epb) sexp[threadIdx.x] = 0;
+    // stage u (raw FP64) in the padded layout, tracking each element's largest exponent
+    for (int q = threadIdx.x; q < cnt * n3 / 2; q += blockDim.x) {
+        const int f = 2 * q, e = f / n3, r = f - e * n3;
+        const int k = r / n2, j = (r / n) % n, i = r % n;
+        double2 v;
+        asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(ue + f));
+        *reinterpret_cast<double2 *>(su + e * EP + k * PP + j * RP + i) = v;
+    }
+    __syncthreads();
+    int ok = 1;
+    for (int q = threadIdx.x; q < n2; q += blockDim.x) {
+        const int i = q / n, l = q - (q / n) * n;
+        if (sD[q] != -sD[(n - 1 - i) * n + (n - 1 - l)]) ok = 0;
+    }
+    if (!__syncthreads_and(ok)) {
+        // D is not centro-antisymmetric: the FP64 node phases on a dense copy
+        double *du = reinterpret_cast<double *>(su);   // 4 dense blocks fit in 3 padded ones
+        double *dr = du + cnt * n3, *ds = dr + cnt * n3, *dt = ds + cnt * n3;
+        copy_to_smem(du, ue, cnt * n3);
+        __syncthreads();
+        tile_node_phases<double, n>(cnt, Ge, we, nullptr, Helm<double>{nullptr, 1.0, 0.0}, sD, du, dr, ds, dt);
+        return;
+    }
+    for (int q = threadIdx.x; q < h * h; q += blockDim.x) {
+        const int i = q / h, l = q - (q / h) * h;
+        const double a = sD[i * n + l], b = sD[i * n + (n - 1 - l)];
+        const double at = sD[l * n + i], bt = sD[(n - 1 - l) * n + i];
+        coef[q] = split_double(0.5 * (a + b), 0);
+        coef[h * h + q] = split_double(0.5 * (a - b), 0);
+        coef[2 * h * h + q] = split_double(0.5 * (at + bt), 0);
+        coef[3 * h * h + q] = split_double(0.5 * (at - bt), 0);
+    }
+    for (int f = threadIdx.x; f < cnt * n3; f += blockDim.x) {
+        const int e = f / n3, r = f - e * n3;
+        const int k = r / n2, j = (r / n) % n, i = r % n;
+        exp_max(sexp, e, biased_exponent(reinterpret_cast<const double *>(su)[e * EP + k * PP + j * RP + i]));
+    }
+    __syncthreads();
+    // u -> double-float, scaled so that each element's largest entry is in [1, 2)
+    for (int f = threadIdx.x; f < cnt * n3; f += blockDim.x) {
+        const int e = f / n3, r = f - e * n3;
+        const int k = r / n2, j = (r / n) % n, i = r % n;
+        const int s = e * EP + k * PP + j * RP + i;
+        su[s] = split_double(reinterpret_cast<const double *>(su)[s], sexp[e] - 1023);
+    }
+    __syncthreads();
+
+    const df *P = coef, *Q = coef + h * h, *Pt = coef + 2 * h * h, *Qt = coef + 3 * h * h;
+    const int lines = cnt * n2;
+    // gradient, r- and s-lines
+#pragma unroll 1
+    for (int dir = 0; dir < 2; ++dir) {
+        df *out = dir == 0 ? sr : ss;
+        for (int t = threadIdx.x; t < lines; t += blockDim.x) {
+            const int e = t / n2, ab = t - e * n2, a = ab / n, b = ab - a * n;
+            const int off = e * EP + a * PP + (dir == 0 ? b * RP : b);
+            const int stride = dir == 0 ? 1 : RP;
+            df x[n];
+            ld_line<n>(su + off, stride, x);
+            eo_apply_st<n>(x, P, Q, out + off, stride);
+        }
+    }
+    __syncthreads();
+    // columns: t-line of u into the column's own slots of su, then the FP64
+    // geometric factor per node; raw FP64 results wr -> sr, ws -> ss, wt -> su
+    for (int t = threadIdx.x; t < lines; t += blockDim.x) {
+        const int e = t / n2, ji = t - e * n2, j = ji / n, i = ji - j * n;
+        const int off = e * EP + j * RP + i;
+        df x[n];
+        ld_line<n>(su + off, PP, x);
+        eo_apply_st<n>(x, P, Q, su + off, PP);
+        const double *Gq = Ge + (size_t)e * 6 * n3 + ji;
+        int mx = 0;
+#pragma unroll 2
+        for (int k = 0; k < n; ++k) {
+            const int s = off + k * PP;
+            double wr, ws, wt;
+            geo_multiply(Gq + k * n2, n3, to_double(sr[s]), to_double(ss[s]), to_double(su[s]), wr, ws, wt);
+            reinterpret_cast<double *>(sr)[s] = wr;
+            reinterpret_cast<double *>(ss)[s] = ws;
+            reinterpret_cast<double *>(su)[s] = wt;
+            mx = max(mx, max(biased_exponent(wr), max(biased_exponent(ws), biased_exponent(wt))));
+        }
+        exp_max(sexp + epb, e, mx);
+    }
+    __syncthreads();
+    // transposed contractions, all three directions, split on load, in place
+#pragma unroll 1
+    for (int dir = 0; dir < 3; ++dir) {
+        df *io = dir == 0 ? sr : (dir == 1 ? ss : su);
+        for (int t = threadIdx.x; t < lines; t += blockDim.x) {
+            const int e = t / n2, ab = t - e * n2, a = ab / n, b = ab - a * n;
+            const int off = e * EP + (dir == 0 ? a * PP + b * RP : (dir == 1 ? a * PP + b : a * RP + b));
+            const int stride = dir == 0 ? 1 : (dir == 1 ? RP : PP);
+            df x[n];
+            ld_line_split<n>(io + off, stride, sexp[epb + e] - 1023, x);
+            eo_apply_st<n>(x, Pt, Qt, io + off, stride);
+        }
+    }
+    __syncthreads();
+    // sum, back to FP64, undo both scales, one coalesced store
+    for (int f = threadIdx.x; f < cnt * n3; f += blockDim.x) {
+        const int e = f / n3, r = f - e * n3;
+        const int k = r / n2, j = (r / n) % n, i = r % n;
+        const int s = e * EP + k * PP + j * RP + i;
+        const df acc = add(add(sr[s], ss[s]), su[s]);
+        const int su_e = sexp[e] > 0 ? sexp[e] : 1, sw_e = sexp[epb + e] > 0 ? sexp[epb + e] : 1;
+        double dh, dl;
+        if (f2d_scaled(acc.hi, su_e + sw_e - 2046, dh) && f2d_scaled(acc.lo, su_e + sw_e - 2046, dl)) {
+            we[f] = dh + dl;                       // exact scaling, one FP64 add
+        } else {
+            const double su_scale = __longlong_as_double((long long)su_e << 52);
+            const double sw_scale = __longlong_as_double((long long)sw_e << 52);
+            we[f] = (to_double(acc) * su_scale) * sw_scale;
+        }
+    }
+}
+
+
+template <int n>
+__global__ void __launch_bounds__(kThreads, (n <= 8 ? 3 : 1))
+ax_f64x_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
+               const double *__restrict__ D, double *__restrict__ w) {
+    constexpr int n3 = n * n * n, epb = elems_per_tile<n>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t e0 = (int64_t)blockIdx.x * epb;
+    const int cnt = (int)(E - e0 < epb ? E - e0 : epb);
+    f64x_tile<n>(cnt, epb, u + e0 * n3, G + e0 * 6 * n3, D, w + e0 * n3, smem_raw);
+}
+
+}  // namespace dfx
+}  // namespace semax

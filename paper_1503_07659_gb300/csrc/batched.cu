@@ -20,11 +20,12 @@
 #include <string>
 #include <vector>
 
-#include "ax_tile.cuh"
+#include "ax_f64x.cuh"
 
 namespace semax {
 
 constexpr int kMaxGroups = 32;
+constexpr int MAP_F64X = 3;   // the double-float FP64-accurate tile (even n)
 constexpr int kBatchThreads = 256;
 
 struct GroupDev {
@@ -69,13 +70,18 @@ ax_batched_kernel(const __grid_constant__ BatchParams P, unsigned long long *cou
         const GroupDev &g = P.g[gi];
         const int64_t e0 = (t - P.tile_start[gi]) * g.epb;
         const int cnt = (int)(g.E - e0 < g.epb ? g.E - e0 : g.epb);
-        for (int q = threadIdx.x; q < g.n * g.n; q += blockDim.x) sD[q] = g.D[q];
-        switch (g.n * 3 + g.map) {
+        if (g.map != MAP_F64X)   // the double-float tile stages D itself
+            for (int q = threadIdx.x; q < g.n * g.n; q += blockDim.x) sD[q] = g.D[q];
+        switch (g.n * 4 + g.map) {
 #define SEMAX_CASE(nn)                                                                \
-    case nn * 3 + MAP_NODE: run_tile<nn, MAP_NODE>(g, e0, cnt, sD, buf); break;       \
-    case nn * 3 + MAP_COLUMN: run_tile<nn, MAP_COLUMN>(g, e0, cnt, sD, buf); break;
+    case nn * 4 + MAP_NODE: run_tile<nn, MAP_NODE>(g, e0, cnt, sD, buf); break;       \
+    case nn * 4 + MAP_COLUMN: run_tile<nn, MAP_COLUMN>(g, e0, cnt, sD, buf); break;
 #define SEMAX_CASE_EVEN(nn) SEMAX_CASE(nn) \
-    case nn * 3 + MAP_EO: run_tile<nn, MAP_EO>(g, e0, cnt, sD, buf); break;
+    case nn * 4 + MAP_EO: run_tile<nn, MAP_EO>(g, e0, cnt, sD, buf); break; \
+    case nn * 4 + MAP_F64X: \
+        dfx::f64x_tile<nn>(cnt, g.epb, g.u + e0 * nn * nn * nn, g.G + e0 * 6 * nn * nn * nn, g.D, \
+                           g.w + e0 * nn * nn * nn, smem_raw); \
+        break;
             SEMAX_CASE_EVEN(2) SEMAX_CASE(3) SEMAX_CASE_EVEN(4) SEMAX_CASE(5) SEMAX_CASE_EVEN(6)
             SEMAX_CASE(7) SEMAX_CASE_EVEN(8) SEMAX_CASE(9) SEMAX_CASE_EVEN(10) SEMAX_CASE(11)
             SEMAX_CASE_EVEN(12) SEMAX_CASE(13) SEMAX_CASE_EVEN(14) SEMAX_CASE(15) SEMAX_CASE_EVEN(16)
@@ -94,15 +100,37 @@ struct TileChoice {
     int map;
 };
 
+// Elements per tile and shared bytes of the double-float tile for order n.
+static int f64x_epb(int n) { return std::max(1, dfx::kThreads / (n * n)); }
+static size_t f64x_smem(int n, int epb) {
+    switch (n) {
+        case 2: return dfx::smem_bytes<2>(epb);
+        case 4: return dfx::smem_bytes<4>(epb);
+        case 6: return dfx::smem_bytes<6>(epb);
+        case 8: return dfx::smem_bytes<8>(epb);
+        case 10: return dfx::smem_bytes<10>(epb);
+        case 12: return dfx::smem_bytes<12>(epb);
+        case 14: return dfx::smem_bytes<14>(epb);
+        case 16: return dfx::smem_bytes<16>(epb);
+        default: return 0;
+    }
+}
+
 static size_t batch_smem(const BatchParams &P) {
     size_t m = 0;
-    for (int q = 0; q < P.ngroups; ++q)
-        m = std::max(m, tile_smem_bytes<double>(P.g[q].n, P.g[q].epb, P.g[q].map) -
-                            sizeof(double) * d_slots<double>(P.g[q].n));
-    return m + sizeof(double) * d_slots<double>(16);
+    for (int q = 0; q < P.ngroups; ++q) {
+        const GroupDev &g = P.g[q];
+        if (g.map == MAP_F64X)
+            m = std::max(m, f64x_smem(g.n, g.epb));
+        else
+            m = std::max(m, tile_smem_bytes<double>(g.n, g.epb, g.map) - sizeof(double) * d_slots<double>(g.n) +
+                                sizeof(double) * d_slots<double>(16));
+    }
+    return m;
 }
 
 static bool choice_valid(int n, TileChoice c) {
+    if (c.map == MAP_F64X) return n % 2 == 0 && c.epb == f64x_epb(n);
     if (c.epb < 1) return false;
     if (c.map == MAP_COLUMN && c.epb * n * n > kBatchThreads) return false;
     if (c.map == MAP_EO && n % 2 != 0) return false;
@@ -348,9 +376,10 @@ static void destroy_plan(semax_plan *p) {
 }
 
 extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, int ngroups, int tune,
-                                  const char *cache_path) {
+                                  const char *cache_path, int flags) {
     if (!plan) return SEMAX_EINVAL;
     *plan = nullptr;
+    if (flags & ~SEMAX_PLAN_F64X) return SEMAX_EINVAL;
     int st = check_groups(groups, ngroups);
     if (st != SEMAX_OK) return st;
     semax_plan *p = new semax_plan();
@@ -368,6 +397,7 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
     if (st == SEMAX_OK && tune) {
         // the largest group of each order stands for that order
         for (int n = 2; n <= 16 && st == SEMAX_OK; ++n) {
+            if ((flags & SEMAX_PLAN_F64X) && n % 2 == 0) continue;   // fixed double-float tile
             int best_g = -1;
             for (int q = 0; q < ngroups; ++q)
                 if (groups[q].N + 1 == n && groups[q].E > 0 && (best_g < 0 || groups[q].E > groups[best_g].E))
@@ -386,6 +416,8 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
         if (st == SEMAX_OK && cache_path && !write_cache(cache_path, dev, p->choice, have, us)) st = SEMAX_EIO;
     }
 
+    if (st == SEMAX_OK && (flags & SEMAX_PLAN_F64X))
+        for (int n = 2; n <= 16; n += 2) p->choice[n] = TileChoice{f64x_epb(n), MAP_F64X};
     if (st == SEMAX_OK) {
         build_params(p->P, groups, ngroups, p->choice);
         LaunchShape ls;

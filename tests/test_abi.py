@@ -80,7 +80,8 @@ def test_batched_validation_and_workspace_size(lib):
     assert lib.sem_ax_batched(g, 2, A + (9 << 32), 4096, None) == -2
     assert lib.sem_ax_batched_workspace_size(g, 40, ctypes.byref(size)) == -1   # too many groups
     plan = ctypes.c_void_p()
-    assert lib.sem_ax_plan_create(ctypes.byref(plan), g, 2, 0, None) == -2
+    assert lib.sem_ax_plan_create(ctypes.byref(plan), g, 2, 0, None, 0) == -2
+    assert lib.sem_ax_plan_create(ctypes.byref(plan), g, 2, 0, None, 4) == -1       # unknown flag
     assert lib.sem_ax_plan_exec(None, None) == -7 and lib.sem_ax_plan_destroy(None) == -7
 
 

@@ -84,6 +84,39 @@ def test_plan_graph_and_tuner_cache(semax, mix, tmp_path):
     again.close()
 
 
+def test_plan_with_double_float_tiles(semax, mix, oracle_mod):
+    """SEMAX_PLAN_F64X: every (even n) group through the double-float tile in
+    the one persistent launch equals the plain sem_ax_f64x call bit for bit,
+    and the oracle to 1e-12."""
+    ws = [torch.full_like(m.u, float("nan")) for m in mix]
+    plan = semax.Plan(_groups(mix, ws), f64x=True)
+    plan()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(19)
+    for m, w in zip(mix, ws):
+        assert plan.config(m.N)[1] == 3
+        assert torch.equal(w, semax.sem_ax_f64x(m.u, m.G, m.D)), m.N
+        idx = np.sort(rng.choice(m.E, size=min(m.E, 30), replace=False))
+        it = torch.from_numpy(idx).cuda()
+        ref = oracle_mod.sem_ax(m.u[it].cpu(), m.G[it].cpu(), m.D.cpu())
+        assert np.max(np.abs(w[it].cpu().numpy() - ref)) / np.max(np.abs(ref)) <= 1e-12, m.N
+    plan.close()
+
+
+def test_plan_f64x_with_odd_orders_and_tuning(semax, oracle_mod):
+    rng = np.random.default_rng(23)
+    meshes = [si.make_mesh(rng, E, N, device="cuda") for N, E in [(2, 7), (7, 5), (4, 9), (15, 2)]]
+    ws = [torch.empty_like(m.u) for m in meshes]
+    plan = semax.Plan(_groups(meshes, ws), tune=True, f64x=True)
+    plan()
+    torch.cuda.synchronize()
+    for m, w in zip(meshes, ws):
+        assert plan.config(m.N)[1] == (3 if (m.N + 1) % 2 == 0 else plan.config(m.N)[1])
+        ref = oracle_mod.sem_ax(m.u.cpu(), m.G.cpu(), m.D.cpu())
+        assert np.max(np.abs(w.cpu().numpy() - ref)) / np.max(np.abs(ref)) <= 1e-12, m.N
+    plan.close()
+
+
 @pytest.mark.parametrize("count", [1, 1000, 3 * 1024 * 1024 + 7])
 def test_reduce_against_definition(semax, oracle_mod, count):
     g = torch.Generator(device="cpu").manual_seed(count)
