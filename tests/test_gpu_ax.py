@@ -319,3 +319,50 @@ def test_mixed_full_size_sampled(semax, oracle_mod):
         assert rel_err(w[it], ref) <= tol, name
         red = semax.reduce(w[it].contiguous(), ref_t).cpu().numpy()
         assert abs(red[0] / red[1] - rel_err(w[it], ref)) <= 1e-12, name
+
+
+# ---------------------------------------------------------------- maximum sizes
+
+@pytest.fixture(scope="module")
+def big_n16():
+    """E = 140000 elements of order 15 (573M nodes): G's element offsets pass
+    2^31 values (e * 6 * 4096 > 2^31 from e = 87382 on).  Built by tiling a
+    64-element seeded mesh, u from a seeded generator."""
+    base = si.make_mesh(np.random.default_rng(900), 64, 15, device="cuda")
+    E = 140000
+    reps = (E + 63) // 64
+    G = base.G.repeat(reps, 1, 1, 1, 1)[:E].contiguous()
+    gen = torch.Generator(device="cuda").manual_seed(901)
+    u = torch.rand((E, 16, 16, 16), generator=gen, dtype=torch.float64, device="cuda") * 2 - 1
+    return base, u, G
+
+
+def _check_tail(w, u, base, oracle_mod, tol):
+    E = u.shape[0]
+    idx = np.array([0, 87381, 87382, 100000, E - 2, E - 1])
+    it = torch.from_numpy(idx).cuda()
+    Gs = base.G[it.remainder(64)].cpu()
+    ref = oracle_mod.sem_ax(u[it].cpu(), Gs, base.D.cpu())
+    got = w[it].double().cpu().numpy()
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= tol
+
+
+def test_max_size_f64_and_f64x(semax, oracle_mod, big_n16):
+    base, u, G = big_n16
+    w = semax.sem_ax(u, G, base.D)
+    torch.cuda.synchronize()
+    _check_tail(w, u, base, oracle_mod, TOL_F64)
+    semax.sem_ax_f64x(u, G, base.D, w)
+    torch.cuda.synchronize()
+    _check_tail(w, u, base, oracle_mod, TOL_F64)
+
+
+def test_max_size_f32_and_bf16(semax, oracle_mod, big_n16):
+    base, u64, G64 = big_n16
+    u, G, D = u64.float(), G64.float(), base.D.float()
+    w = semax.sem_ax_f32(u, G, D)
+    torch.cuda.synchronize()
+    _check_tail(w, u64, base, oracle_mod, TOL_F32)
+    semax.sem_ax_bf16x3(u, G, D, w, terms=6)
+    torch.cuda.synchronize()
+    _check_tail(w, u64, base, oracle_mod, TOL_BF16[6])
