@@ -228,9 +228,7 @@ __device__ __forceinline__ void eo_apply_st(const T (&x)[n], const T *__restrict
 //      into this pass spreads them among other warps' arithmetic.
 //   3  transposed r- and s-lines in place
 //   4  w = r + s + t, one coalesced store
-// SG: G points at the tile's staged copy in shared memory (asynchronous
-// copies in flight, waited for before the column pass).
-template <typename T, int n, bool HELM, bool SG = false>
+template <typename T, int n, bool HELM>
 __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G, T *__restrict__ w,
                                                const T *__restrict__ scale, Helm<T> helm,
                                                const T *__restrict__ sPQ, T *su, T *sr, T *ss) {
@@ -252,7 +250,6 @@ __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G,
             eo_apply_st<T, n>(x, P, Q, out + off, stride);
         }
     }
-    if constexpr (SG) asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
 
     // 2: columns (j, i)
@@ -272,10 +269,7 @@ __device__ __forceinline__ void tile_eo_phases(int cnt, const T *__restrict__ G,
         for (int k = 0; k < n; ++k) {
             const int q = off + k * PP;
             T wr, ws;
-            if constexpr (SG)
-                geo_multiply_smem(Ge + k * n2, n3, sr[q], ss[q], y[k], wr, ws, x[k]);
-            else
-                geo_multiply(Ge + k * n2, n3, sr[q], ss[q], y[k], wr, ws, x[k]);
+            geo_multiply(Ge + k * n2, n3, sr[q], ss[q], y[k], wr, ws, x[k]);
             if constexpr (HELM) {
                 wr *= helm.h1;
                 ws *= helm.h1;

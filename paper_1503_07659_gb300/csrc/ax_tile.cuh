@@ -50,23 +50,16 @@ __host__ __device__ constexpr int d_slots(int n) { return round_up(2 * n * n, 16
 template <typename T>
 __host__ __device__ constexpr int eo_elem_pitch(int n);
 
-// FP32 tiles up to n = 8 stage each element's G (6 n^3 values, <= 12 KB) in
-// shared memory with asynchronous copies issued when the tile starts, so
-// that the loads fly while u is staged and the r- and s-lines run.
-template <typename T>
-__host__ __device__ constexpr bool eo_stage_g(int n) { return sizeof(T) == 4 && n <= 8 && n % 2 == 0; }
-
 // Shared-memory footprint (bytes) of D plus one tile of `epb` elements: four
 // dense element buffers (u and the three directions), or for MAP_EO three
 // padded ones (the t-direction reuses u's slots), at least as large as the
-// four dense buffers of its fallback path, plus the staged G where used.
+// four dense buffers of its fallback path.
 template <typename T>
 __host__ __device__ constexpr size_t tile_smem_bytes(int n, int epb, int map) {
     return sizeof(T) * ((size_t)d_slots<T>(n) +
                         (size_t)epb * (map == 2 && n % 2 == 0
                                            ? (3 * eo_elem_pitch<T>(n) > 4 * n * n * n ? 3 * eo_elem_pitch<T>(n)
-                                                                                     : 4 * n * n * n) +
-                                                 (eo_stage_g<T>(n) ? 6 * n * n * n : 0)
+                                                                                     : 4 * n * n * n)
                                            : 4 * n * n * n));
 }
 
@@ -92,16 +85,6 @@ __device__ __forceinline__ void geo_multiply(const T *__restrict__ Gq, int n3, T
                                              T &wr, T &ws, T &wt) {
     const T grr = ld_stream(Gq), grs = ld_stream(Gq + n3), grt = ld_stream(Gq + 2 * n3);
     const T gss = ld_stream(Gq + 3 * n3), gst = ld_stream(Gq + 4 * n3), gtt = ld_stream(Gq + 5 * n3);
-    wr = fma_(grt, ut, fma_(grs, us, grr * ur));
-    ws = fma_(gst, ut, fma_(gss, us, grs * ur));
-    wt = fma_(gtt, ut, fma_(gst, us, grt * ur));
-}
-
-// geo_multiply with G read from shared memory (a staged copy).
-template <typename T>
-__device__ __forceinline__ void geo_multiply_smem(const T *Gq, int n3, T ur, T us, T ut, T &wr, T &ws, T &wt) {
-    const T grr = Gq[0], grs = Gq[n3], grt = Gq[2 * n3];
-    const T gss = Gq[3 * n3], gst = Gq[4 * n3], gtt = Gq[5 * n3];
     wr = fma_(grt, ut, fma_(grs, us, grr * ur));
     ws = fma_(gst, ut, fma_(gss, us, grs * ur));
     wt = fma_(gtt, ut, fma_(gst, us, grt * ur));
@@ -166,19 +149,9 @@ __device__ __forceinline__ void ax_tile(int cnt, const T *__restrict__ u, const 
     const int nodes = cnt * n3;
     if constexpr (MAP == MAP_EO && n % 2 == 0) {
         constexpr int h = n / 2, EP = eo_elem_pitch<T>(n);
-        constexpr bool SG = eo_stage_g<T>(n);
-        T *sG = buf;                                  // SG: cnt * 6 n^3 staged values of G
-        T *su = buf + (SG ? cnt * 6 * n3 : 0);
+        T *su = buf;
         T *sr = su + cnt * EP;
         T *ss = sr + cnt * EP;
-        if constexpr (SG) {
-            const int chunks = cnt * 6 * n3 * (int)sizeof(T) / 16;
-            const char *src = reinterpret_cast<const char *>(G);
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(sG);
-            for (int q = threadIdx.x; q < chunks; q += blockDim.x)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * q), "l"(src + 16 * q));
-            asm volatile("cp.async.commit_group;" ::);
-        }
         eo_stage<T, n>(su, u, cnt);
         __syncthreads();   // D (loaded by the caller) and the staged u are visible
         int ok = 1;
@@ -198,12 +171,10 @@ __device__ __forceinline__ void ax_tile(int cnt, const T *__restrict__ u, const 
                 sPQ[3 * h * h + q] = T(0.5) * (at - bt);
             }
             __syncthreads();
-            tile_eo_phases<T, n, HELM, SG>(cnt, SG ? sG : G, w, scale, helm, sPQ, su, sr, ss);
+            tile_eo_phases<T, n, HELM>(cnt, G, w, scale, helm, sPQ, su, sr, ss);
             return;
         }
         // D is not centro-antisymmetric: dense staging and the node phases
-        if constexpr (SG) asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
         su = buf;
         sr = su + nodes;
         ss = sr + nodes;
