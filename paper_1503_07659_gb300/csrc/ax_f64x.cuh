@@ -50,17 +50,6 @@ __device__ __forceinline__ df add(df a, df b) {
 
 __device__ __forceinline__ df sub(df a, df b) { return add(a, df{-b.hi, -b.lo}); }
 
-// The same sums left unnormalised: hi is the rounded sum of the high parts,
-// lo collects every error term, |lo| <= ~1.5 ulp(hi).  Every consumer here
-// (products through dot2_step, further sums, conversion to FP64) takes such
-// pairs without loss, and the final normalising two-sum (3 instructions) is
-// saved.
-__device__ __forceinline__ df add_un(df a, df b) {
-    const df s = two_sum(a.hi, b.hi);
-    return {s.hi, __fadd_rn(__fadd_rn(a.lo, b.lo), s.lo)};
-}
-__device__ __forceinline__ df sub_un(df a, df b) { return add_un(a, df{-b.hi, -b.lo}); }
-
 // acc + p * x
 __device__ __forceinline__ df fma_df(df p, df x, df acc) {
     const float m = __fmul_rn(p.hi, x.hi);
@@ -89,10 +78,10 @@ __device__ __forceinline__ void dot2_step(acc2 &a, df p, df x) {
     a.c = __fadd_rn(a.c, __fadd_rn(r, t.lo));
 }
 
-// (a.s + a.c) +/- (b.s + b.c), unnormalised (see add_un)
+// (a.s + a.c) +/- (b.s + b.c) as a normalised double-float
 __device__ __forceinline__ df acc_add(acc2 a, acc2 b) {
     const df t = two_sum(a.s, b.s);
-    return {t.hi, __fadd_rn(__fadd_rn(a.c, b.c), t.lo)};
+    return fast_two_sum(t.hi, __fadd_rn(__fadd_rn(a.c, b.c), t.lo));
 }
 __device__ __forceinline__ df acc_sub(acc2 a, acc2 b) { return acc_add(a, acc2{-b.s, -b.c}); }
 
@@ -175,8 +164,8 @@ __device__ __forceinline__ void eo_apply_st(const df (&x)[n], const df *P, const
     df e[h], o[h];
 #pragma unroll
     for (int l = 0; l < h; ++l) {
-        e[l] = add_un(x[l], x[n - 1 - l]);
-        o[l] = sub_un(x[l], x[n - 1 - l]);
+        e[l] = add(x[l], x[n - 1 - l]);
+        o[l] = sub(x[l], x[n - 1 - l]);
     }
 #pragma unroll 1
     for (int i = 0; i < h; ++i) {
