@@ -89,11 +89,13 @@ __device__ __forceinline__ df acc_sub(acc2 a, acc2 b) { return acc_add(a, acc2{-
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(k + 127) << 23); }
 
 // x * 2^-sh split into hi + lo by bit operations (no FP64 instruction).
-// Values whose scaled magnitude is below the float range flush to zero.
+// Values whose scaled magnitude is below the float range flush to zero;
+// Inf and NaN pass through (as hi) so that they propagate like in FP64.
 __device__ __forceinline__ df split_double(double x, int sh) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
     const int eb = (int)((hi32 >> 20) & 0x7ffu);
+    if (eb == 0x7ff) return {__double2float_rn(x), 0.f};    // Inf and NaN propagate
     const int ef = eb - sh - 1023 + 127;             // biased float exponent of hi
     if (eb == 0 || ef < 1) return {0.f, 0.f};
     const unsigned sign = hi32 & 0x80000000u;

@@ -207,6 +207,24 @@ def test_f64x_is_scale_invariant(semax, oracle_mod, scale):
     assert rel_err(w, ref) <= TOL_F64
 
 
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_nonfinite_input_stays_in_its_element(semax, oracle_mod, bad):
+    """A NaN or Inf in one element's u makes that element's output non-finite
+    (as in the definition) and leaves every other element exact, in the FP64,
+    double-float and FP32 forms."""
+    m = si.make_mesh(np.random.default_rng(20), 6, 7)
+    u = m.u.clone()
+    u[3, 2, 5, 1] = bad
+    ref = oracle_mod.sem_ax(np.delete(u.numpy(), 3, 0), np.delete(m.G.numpy(), 3, 0), m.D)
+    for fn, dt, tol in ((semax.sem_ax, torch.float64, TOL_F64), (semax.sem_ax_f64x, torch.float64, TOL_F64),
+                        (semax.sem_ax_f32, torch.float32, TOL_F32)):
+        w = fn(u.to("cuda", dt), m.G.to("cuda", dt), m.D.to("cuda", dt))
+        torch.cuda.synchronize()
+        wc = w.double().cpu().numpy()
+        assert not np.isfinite(wc[3]).all()
+        assert rel_err(np.delete(wc, 3, 0), ref) <= tol
+
+
 def test_f64x_general_D_falls_back(semax, oracle_mod):
     m = si.make_mesh(np.random.default_rng(16), 5, 7)
     D = m.D.clone()
