@@ -11,7 +11,8 @@
 // the prior art for staging u_e and the intermediates here.
 //
 // Per element, one CTA of 8 warps:
-//   load   u (FP32, 128-bit loads) -> BF16 pieces in shared memory (XOR
+//   load   u (FP32, prefetched with cp.async into the piece region while the
+//          previous element's pass T' runs) -> BF16 pieces in shared memory (XOR
 //          swizzled so that every ldmatrix and fragment store is free of bank
 //          conflicts along both the j and the k axis);
 //   pass T ut = D (x) I (x) I u: warp w owns rows j = 2w, 2w+1, output
@@ -190,6 +191,20 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
     DFrag<NP> f;
     load_dfrag<NP>(D, f);
 
+    // u of the CTA's first element, raw FP32, into the u-piece region: each
+    // thread copies (and later reads back) its own four 16-byte chunks
+    const unsigned raw_s = smem_addr(upc);
+    auto prefetch_u = [&](int64_t ep) {
+        const char *src = reinterpret_cast<const char *>(u + ep * 4096);
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            const int q = tid + it * kThreads;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(raw_s + 16 * q), "l"(src + 16 * q));
+        }
+        asm volatile("cp.async.commit_group;" ::);
+    };
+    if (blockIdx.x < E) prefetch_u(blockIdx.x);
+
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         const float *ue = u + e * 4096;
         const float *Ge = G + e * (GEO ? 24 : 6 * 4096);
@@ -207,11 +222,16 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
             sgeo[8 * c + m] = 0.125f * acc;
         }
 
-        // ---- load u, split into pieces
+        // ---- u (prefetched raw into the piece region), split into pieces
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        float4 vr[4];
+#pragma unroll
+        for (int it = 0; it < 4; ++it) vr[it] = reinterpret_cast<const float4 *>(upc)[tid + it * kThreads];
+        __syncthreads();   // every thread has its raw values before pieces overwrite the region
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
             const int q = tid + it * kThreads;  // float4 index, 0..1023
-            const float4 v = ld_stream4(reinterpret_cast<const float4 *>(ue) + q);
+            const float4 v = vr[it];
             const int k = q >> 6, j = (q >> 2) & 15, i = (q & 3) << 2;
             uint32_t lo[NP], hi[NP];
             split2<NP>(v.x, v.y, lo);
@@ -397,6 +417,7 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
             }
         }
         __syncthreads();
+        if (e + gridDim.x < E) prefetch_u(e + gridDim.x);   // the u pieces are dead from here on
 
         // ---- pass T': w += sum_l D[l][k] wt[l][j][i]; store
         const float sc = scale ? scale[e] : 1.f;
