@@ -413,6 +413,15 @@ def run_ours(args, rank, world):
             "us_per_call": t_x * 1e6, "rel_err_vs_f64": rel_err_gpu(semax, wx, w),
             "arith": "double-float contractions on the FP32 pipe, FP64 geometric factor; FP64 in/out"}
     del wx
+    # FP64-accurate tensor-core form (exact digit slicing) on the same workload
+    wt = torch.empty_like(w)
+    t_t = time_region(lambda: semax.sem_ax_f64tc(mesh.u, mesh.G, mesh.D, wt), args.steps, args.warmup,
+                      world) / args.steps
+    f64tc = {"gdofs": world * dofs / t_t / 1e9, "hbm_gbs": world * dofs * bytes_per_node(8) / t_t / 1e9,
+             "us_per_call": t_t * 1e6, "rel_err_vs_f64": rel_err_gpu(semax, wt, w),
+             "arith": "contractions on BF16 tensor cores by exact base-256 digit slicing (levels 2..7), "
+                      "double-float level sums and geometric factor; FP64 in/out"}
+    del wt
     # Helmholtz form w = h1 A u + h2 B u on the same workload (72 B/node)
     Bm = si.mass_diagonal(mesh.X, mesh.N, device=dev)
     wh = torch.empty_like(w)
@@ -443,6 +452,7 @@ def run_ours(args, rank, world):
             "hbm_gbs": world * nbytes / t_step / 1e9,
             "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline}
     line["f64x"] = f64x
+    line["f64tc"] = f64tc
     line["helmholtz_f64"] = helm
     if not args.no_variants:
         line["variants"] = variants(semax, reps=20)

@@ -102,6 +102,23 @@ int sem_ax_helmholtz(int64_t E, int N, const double *u, const double *G, const d
 int sem_ax_f64x(int64_t E, int N, const double *u, const double *G, const double *D,
                 double *w, void *stream);
 
+/* FP64 inputs and outputs, FP64-accurate result; the six contractions run
+ * on BF16 tensor cores by exact slicing (the Ozaki scheme).  Per element, u
+ * and the intermediate [wr ws wt] are scaled by a power of two and written
+ * as six balanced base-256 digits (integers of magnitude <= 256, exact in
+ * BF16), D likewise once per call; the digit products of levels 2..7 (21
+ * pairs per contraction) are summed on tensor cores in FP32 accumulators
+ * that stay below 2^22 and are therefore exact, and the level sums are
+ * combined in double-float.  The geometric-factor multiply runs in
+ * double-float with G split by bit operations after a per-node power-of-two
+ * scale.  Error against the FP64 definition ~1e-14 of ||w||_inf; entries
+ * more than ~2^48 times smaller than their element's largest count only to
+ * that precision.  An element with an Inf or NaN input returns NaN in every
+ * entry.  Order N = 7 (n = 8) on tensor cores, any D; other orders are
+ * computed by sem_ax_f64x. */
+int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const double *D,
+                 double *w, void *stream);
+
 /* FP32 storage and FP32 compute.  G_scale is NULL or [E] per-element factors
  * s_e: the kernel then treats the stored G as G_e / s_e and multiplies the
  * element's result by s_e (use powers of two so that this is exact). */

@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import SemaxError, semax_group, check, SEMAX_F32, SEMAX_F64
 
-__all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_bf16x3_geo", "sem_ax_batched", "Plan", "reduce",
+__all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_bf16x3_geo", "sem_ax_batched", "Plan", "reduce",
            "sem_ax_from_host", "SemaxError", "library_path"]
 
 
@@ -68,6 +68,15 @@ def sem_ax_f64x(u: torch.Tensor, G: torch.Tensor, D: torch.Tensor, w: torch.Tens
     E, N = _dims(u, D)
     w = _out(w, u)
     check(_lib.lib().sem_ax_f64x(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _stream(stream)), "sem_ax_f64x")
+    return w
+
+
+def sem_ax_f64tc(u: torch.Tensor, G: torch.Tensor, D: torch.Tensor, w: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """FP64 in/out, FP64-accurate; contractions on BF16 tensor cores by exact digit slicing (N = 7)."""
+    E, N = _dims(u, D)
+    w = _out(w, u)
+    check(_lib.lib().sem_ax_f64tc(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _stream(stream)), "sem_ax_f64tc")
     return w
 
 

@@ -1,0 +1,468 @@
+// FP64-accurate Ax with the six contractions on BF16 tensor cores by exact
+// slicing (the Ozaki scheme: Ozaki, Ogita, Oishi & Rump, Numer. Algorithms
+// 59, 2012; its tensor-core forms: Mukunoki, Ozaki, Ogita & Imamura, ICCS
+// 2020; Ootomo, Ozaki & Yokota, IJHPCA 2024).  Order n = 8 (N = 7).
+//
+// Slicing.  An operand x with one power-of-two scale 2^s per element is
+// written in balanced base-256 digits,
+//     x = 2^s sum_{q=1..6} d_q 2^(-8q) + (error <= 2^(s-49)),
+// with every d_q an integer of magnitude <= 256, which BF16 holds exactly.
+// A digit of D times a digit of u is an integer below 2^16 in magnitude; one
+// m16n8k16 product sums 16 of them (two digit pairs of the same level, 8
+// terms each), and one level L = p + q collects at most six pairs, so every
+// FP32 accumulator holds an integer below 2^22: the tensor-core sums are
+// exact.  Levels L = 2..7 are kept (21 digit pairs per contraction, 9
+// m16n8k16 + 3 m16n8k8 products per 16 x 8 output tile); the dropped levels
+// weigh less than 2^-48 of the element's scale.  The six level sums of an
+// output are combined in double-float (an unevaluated sum of two floats).
+//
+// Per element (one CTA of 4 warps; warp w owns the planes k = 2w, 2w+1 for
+// every pointwise step, in the layout of the m16n8 accumulator of the
+// r-direction tile):
+//   A  u (FP64) -> per-element scale -> 6 BF16 digit planes in shared memory;
+//   B  ur, us, ut on tensor cores (B operand: the digits of D^T, held in
+//      registers for the CTA's lifetime); ur stays in registers, us and ut
+//      go through two swizzled double-float buffers;
+//   C  y = G [ur us ut] in double-float with G split hi + lo by bit
+//      operations after a per-node power-of-two scale; per-element scale of
+//      y; 3 x 6 digit planes;
+//   D  w_r, w_s, w_t on tensor cores (B operand: the digits of D);
+//   E  w = (w_r + w_s + w_t) * 2^(scales) in FP64, stored.
+// The only FP64 instructions are the final add and scale of each node.
+// Inputs with Inf or NaN make their element's output NaN.
+#include <algorithm>
+#include <climits>
+
+#include "ax_f64x.cuh"
+
+namespace semax {
+namespace oz {
+
+using dfx::acc2;
+using dfx::df;
+
+constexpr int kThreads = 128;                // one element per CTA pass
+constexpr int kS = 6;                        // digits per operand
+constexpr int kPlane = 144;                  // bytes per 8 x 8 BF16 plane, padded (ldmatrix along k)
+constexpr int kSlice = 8 * kPlane;           // one digit of an 8^3 operand
+constexpr int kDigBytes = 3 * kS * kSlice;   // digits of wr, ws, wt (u reuses the first six)
+constexpr size_t kSmem = kDigBytes + 2 * 512 * sizeof(float2) + 16 * sizeof(int);
+constexpr int kBadExp = 1 << 20;             // marks a non-finite input in the exponent reductions
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm4(uint32_t a, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
+}
+__device__ __forceinline__ void ldsm4t(uint32_t a, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
+}
+__device__ __forceinline__ void mma16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                      uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma8(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a0), "r"(a1), "r"(b0));
+}
+
+__device__ __forceinline__ double2 ld_stream2(const double *p) {
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ int bexp(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+
+// Two integer-valued floats (|v| <= 256) as a BF16 pair, a in the low half;
+// exact because such a float has no bits below its top 16.
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+
+// The integer v (|v| < 2^22) as a float, by the 1.5 * 2^23 bias.
+__device__ __forceinline__ float int_to_float(int v) { return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f); }
+
+// Balanced base-256 digits of x * 2^-(E - 1022), E >= the biased exponent of
+// x (at least 1): M = round(x * 2^(48 - (E - 1022))) = sum_q d[q] 2^(8 (5 - q)),
+// |M| <= 2^48, d[1..5] in [-128, 127], |d[0]| <= 256.  Integer arithmetic only.
+__device__ __forceinline__ void digits_fp64(double x, int E, float (&d)[kS]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int eb = (int)((b >> 52) & 0x7ffu);
+    const unsigned long long m = (b & 0xfffffffffffffull) | (eb ? (1ull << 52) : 0ull);
+    const int s = min(E + 5 - max(eb, 1), 63);   // >= 5
+    long long M = (long long)((m + (1ull << (s - 1))) >> s);
+    if (b >> 63) M = -M;
+    int lo = (int)(M & 0xffffff);   // M = hi 2^24 + lo, lo in [0, 2^24)
+    int hi = (int)(M >> 24);
+    int q[kS];
+#pragma unroll
+    for (int i = kS - 1; i >= 3; --i) {
+        q[i] = ((lo + 128) & 255) - 128;
+        lo = (lo - q[i]) >> 8;
+    }
+    hi += lo;                       // carry (0 or 1)
+#pragma unroll
+    for (int i = 2; i >= 1; --i) {
+        q[i] = ((hi + 128) & 255) - 128;
+        hi = (hi - q[i]) >> 8;
+    }
+    q[0] = hi;
+#pragma unroll
+    for (int i = 0; i < kS; ++i) d[i] = int_to_float(q[i]);
+}
+
+// Balanced base-256 digits of the double-float value (hi + lo) * m, m a
+// power of two with |(hi + lo) * m| < 256 (1 + 2^-20) and |lo| a few units
+// in the last place of hi at most: (hi + lo) m = sum_q d[q] 2^(-8q) + (error
+// <= 2^-41).  Each digit is the sum of the digit of hi and that of lo, so
+// |d[0]| <= 256 and |d[q]| <= 256 for q >= 1.
+// Every step is exact: t * 256 is a scaling, adding and subtracting
+// 1.5 * 2^23 rounds to an integer, and the remainder is representable.
+__device__ __forceinline__ void digits_df(float hi, float lo, float m, float (&d)[kS]) {
+    constexpr float C = 12582912.0f;
+    const float t = __fmul_rn(hi, m);
+    float q = __fsub_rn(__fadd_rn(t, C), C);
+    float r = __fsub_rn(t, q);
+    d[0] = q;
+#pragma unroll
+    for (int i = 1; i < kS; ++i) {
+        q = __fsub_rn(__fmaf_rn(r, 256.0f, C), C);
+        r = __fmaf_rn(r, 256.0f, -q);
+        d[i] = q;
+    }
+    // |lo * m| < 1/2: the digit 0 of lo is zero
+    float rl = __fmul_rn(lo, m);
+#pragma unroll
+    for (int i = 1; i < kS; ++i) {
+        q = __fsub_rn(__fmaf_rn(rl, 256.0f, C), C);
+        rl = __fmaf_rn(rl, 256.0f, -q);
+        d[i] = __fadd_rn(d[i], q);
+    }
+}
+
+// 2^k as a float for k in [-126, 127]; 0 below
+__device__ __forceinline__ float pow2f_or_zero(int k) {
+    return k < -126 ? 0.0f : __uint_as_float((unsigned)(min(k, 127) + 127) << 23);
+}
+
+// V = x2 + x3 2^-8 + x4 2^-16 + x5 2^-24 + x6 2^-32 + x7 2^-40 (x_L the exact
+// level sums) as an unevaluated sum hi + lo; the two leading additions are
+// error-free, the rest err by < 2^-47 of |V|'s bound.
+__device__ __forceinline__ df combine_levels(const float (&x)[6][4], int e) {
+    const df a = dfx::two_sum(x[0][e], __fmul_rn(x[1][e], 0x1p-8f));
+    const df b = dfx::two_sum(a.hi, __fmul_rn(x[2][e], 0x1p-16f));
+    const float r = __fmaf_rn(x[3][e], 0x1p-24f, __fmaf_rn(x[4][e], 0x1p-32f, __fmul_rn(x[5][e], 0x1p-40f)));
+    return {b.hi, __fadd_rn(__fadd_rn(a.lo, b.lo), r)};
+}
+
+// One 16 x 8 output tile of a contraction along direction DIR (0: r / i,
+// 1: s / j, 2: t / k) for warp w, all 21 digit pairs of levels 2..7.
+// base: shared address of digit 0 of the operand; Bf[p]: the B fragment of
+// digit p of D^T (gradient) or D (transposed).  Accumulator rows:
+//   DIR 0: (k, j) = (2w + m / 8, m % 8), columns i;
+//   DIR 1: (k, i) = (2w + m / 8, m % 8), columns j;
+//   DIR 2: (j, i) = (2w + m / 8, m % 8), columns k.
+template <int DIR>
+__device__ __forceinline__ void contract(uint32_t base, int warp, int lane, const uint32_t (&Bf)[kS],
+                                         float (&acc)[6][4]) {
+    const int mi = lane >> 3, rr = lane & 7;
+    const int blk = 2 * warp + (mi & 1);
+    const uint32_t addr = base + (mi >> 1) * kSlice + (DIR == 2 ? rr * kPlane + blk * 16 : blk * kPlane + rr * 16);
+    uint32_t a[kS][2];
+#pragma unroll
+    for (int q = 0; q < kS; q += 2) {
+        if (DIR == 0)
+            ldsm4(addr + q * kSlice, a[q][0], a[q][1], a[q + 1][0], a[q + 1][1]);
+        else
+            ldsm4t(addr + q * kSlice, a[q][0], a[q][1], a[q + 1][0], a[q + 1][1]);
+    }
+#pragma unroll
+    for (int l = 0; l < 6; ++l) acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = 0.0f;
+    // level index L - 2 = p + q for D digit p and operand digit q (0-based)
+#define OZ_K8(L, p, q) mma8(acc[L], a[q][0], a[q][1], Bf[p])
+#define OZ_K16(L, p1, q1, p2, q2) mma16(acc[L], a[q1][0], a[q1][1], a[q2][0], a[q2][1], Bf[p1], Bf[p2])
+    OZ_K8(0, 0, 0);
+    OZ_K16(1, 0, 1, 1, 0);
+    OZ_K16(2, 0, 2, 1, 1);
+    OZ_K8(2, 2, 0);
+    OZ_K16(3, 0, 3, 1, 2);
+    OZ_K16(3, 2, 1, 3, 0);
+    OZ_K16(4, 0, 4, 1, 3);
+    OZ_K16(4, 2, 2, 3, 1);
+    OZ_K8(4, 4, 0);
+    OZ_K16(5, 0, 5, 1, 4);
+    OZ_K16(5, 2, 3, 3, 2);
+    OZ_K16(5, 4, 1, 5, 0);
+#undef OZ_K8
+#undef OZ_K16
+}
+
+// Double-float buffers of the s- and t-direction results (one float2 per
+// node), XOR-swizzled so that the accumulator-layout writes and the
+// pointwise reads are both free of bank conflicts:
+//   s: [k][i][j], t: [j][k][i], bits 2-3 of the flat index flipped by a key
+//   that does not depend on them.
+__device__ __forceinline__ int sidx(int k, int j, int i) { return (64 * k + 8 * i + j) ^ (((i >> 1) & 3) << 2); }
+__device__ __forceinline__ int tidx(int k, int j, int i) {
+    return (64 * j + 8 * k + i) ^ ((((k >> 1) & 3) ^ ((j & 1) << 1)) << 2);
+}
+
+// Write the s- or t-direction tile of warp w (levels combined) to its buffer.
+template <int DIR>
+__device__ __forceinline__ void store_tile(float2 *buf, const float (&acc)[6][4], int warp, int g, int t) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const df v0 = combine_levels(acc, 2 * h), v1 = combine_levels(acc, 2 * h + 1);
+        if (DIR == 1) {   // rows (k = 2w + h, i = g), columns j = 2t, 2t + 1: adjacent in [k][i][j]
+            *reinterpret_cast<float4 *>(buf + sidx(2 * warp + h, 2 * t, g)) = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+        } else {          // rows (j = 2w + h, i = g), columns k = 2t, 2t + 1
+            buf[tidx(2 * t, 2 * warp + h, g)] = make_float2(v0.hi, v0.lo);
+            buf[tidx(2 * t + 1, 2 * warp + h, g)] = make_float2(v1.hi, v1.lo);
+        }
+    }
+}
+
+// y = sum_b Gh[b] V[b] (double-float products, Dot2-style accumulation)
+__device__ __forceinline__ acc2 dot3(df g0, df g1, df g2, df v0, df v1, df v2) {
+    const float m = __fmul_rn(g0.hi, v0.hi);
+    float r = __fmaf_rn(g0.hi, v0.hi, -m);
+    r = __fmaf_rn(g0.hi, v0.lo, r);
+    r = __fmaf_rn(g0.lo, v0.hi, r);
+    acc2 a{m, r};
+    dfx::dot2_step(a, g1, v1);
+    dfx::dot2_step(a, g2, v2);
+    return a;
+}
+
+// x * 2^s for a double x, exact unless the result leaves the double range
+__device__ __forceinline__ double scale2(double x, int s) {
+    const int s1 = max(min(s / 2, 1023), -1022), s2 = max(min(s - s1, 1023), -1022);
+    return x * __longlong_as_double((long long)(s1 + 1023) << 52) * __longlong_as_double((long long)(s2 + 1023) << 52);
+}
+
+__device__ __forceinline__ int max4(const int *p) { return max(max(p[0], p[1]), max(p[2], p[3])); }
+
+__global__ void __launch_bounds__(kThreads, 4)
+ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
+                const double *__restrict__ D, double *__restrict__ w) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *dig = smem;
+    float2 *bs = reinterpret_cast<float2 *>(smem + kDigBytes);   // s-direction results
+    float2 *bt = bs + 512;                                         // t-direction results
+    int *sred = reinterpret_cast<int *>(bt + 512);                 // [0, 4) u, [4, 8) y exponents
+    const uint32_t dig_s = smem_u32(dig);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+
+    // D digits, once per CTA: B fragments of D^T (gradient) and D (transposed)
+    int eD = 1;
+    for (int q = lane; q < 64; q += 32) eD = max(eD, max(bexp(D[q]), 1));
+    eD = __reduce_max_sync(0xffffffffu, eD);
+    uint32_t fg[kS], ft[kS];
+    {
+        float x0[kS], x1[kS];
+        digits_fp64(D[g * 8 + 2 * t], eD, x0);
+        digits_fp64(D[g * 8 + 2 * t + 1], eD, x1);
+#pragma unroll
+        for (int p = 0; p < kS; ++p) fg[p] = pack_bf16(x0[p], x1[p]);
+        digits_fp64(D[(2 * t) * 8 + g], eD, x0);
+        digits_fp64(D[(2 * t + 1) * 8 + g], eD, x1);
+#pragma unroll
+        for (int p = 0; p < kS; ++p) ft[p] = pack_bf16(x0[p], x1[p]);
+    }
+
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const double *ue = u + e * 512;
+        const double *Ge = G + e * 3072;
+        double *we = w + e * 512;
+
+        // ---- A: u -> digits (thread's nodes: k = 2w + h, j = g, i = 2t + c)
+        double2 uv[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) uv[h] = ld_stream2(ue + (2 * warp + h) * 64 + g * 8 + 2 * t);
+        int ex = 1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) ex = max(ex, max(bexp(uv[h].x), bexp(uv[h].y)));
+        ex = __reduce_max_sync(0xffffffffu, ex);
+        if (lane == 0) sred[warp] = ex;
+        __syncthreads();
+        const int eU = max4(sred);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float d0[kS], d1[kS];
+            digits_fp64(uv[h].x, eU, d0);
+            digits_fp64(uv[h].y, eU, d1);
+            unsigned char *p = dig + (2 * warp + h) * kPlane + g * 16 + 4 * t;
+#pragma unroll
+            for (int q = 0; q < kS; ++q) *reinterpret_cast<uint32_t *>(p + q * kSlice) = pack_bf16(d0[q], d1[q]);
+        }
+        __syncthreads();
+
+        // ---- B: gradient on tensor cores
+        df vr[4];
+        {
+            float acc[6][4];
+            contract<0>(dig_s, warp, lane, fg, acc);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) vr[q] = combine_levels(acc, q);
+        }
+        {
+            float acc[6][4];
+            contract<1>(dig_s, warp, lane, fg, acc);
+            store_tile<1>(bs, acc, warp, g, t);
+        }
+        {
+            float acc[6][4];
+            contract<2>(dig_s, warp, lane, fg, acc);
+            store_tile<2>(bt, acc, warp, g, t);
+        }
+        __syncthreads();
+
+        // ---- C: y = G grad in double-float; per-element scale; digits
+        acc2 y[4][3];
+        int shn[4];
+        int tmax = INT_MIN;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * warp + h, nb = k * 64 + g * 8 + 2 * t;
+            double2 gv[6];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) gv[a] = ld_stream2(Ge + a * 512 + nb);
+            const float4 tv = *reinterpret_cast<const float4 *>(bt + tidx(k, g, 2 * t));
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int q = 2 * h + c;
+                const float2 sv = bs[sidx(k, g, 2 * t + c)];
+                const df Vs{sv.x, sv.y};
+                const df Vt = c ? df{tv.z, tv.w} : df{tv.x, tv.y};
+                double Gc[6];
+                int eg = 0;
+#pragma unroll
+                for (int a = 0; a < 6; ++a) {
+                    Gc[a] = c ? gv[a].y : gv[a].x;
+                    eg = max(eg, bexp(Gc[a]));
+                }
+                const int sh = max(eg, 1) - 1023;   // G * 2^-sh has magnitude < 2
+                df Gh[6];
+#pragma unroll
+                for (int a = 0; a < 6; ++a) Gh[a] = dfx::split_double(Gc[a], sh);
+                y[q][0] = dot3(Gh[0], Gh[1], Gh[2], vr[q], Vs, Vt);
+                y[q][1] = dot3(Gh[1], Gh[3], Gh[4], vr[q], Vs, Vt);
+                y[q][2] = dot3(Gh[2], Gh[4], Gh[5], vr[q], Vs, Vt);
+                // renormalise: when the leading level sums of a gradient cancel
+                // exactly, its value sits in the low part, and so can y's
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const df n2 = dfx::two_sum(y[q][a].s, y[q][a].c);
+                    y[q][a] = acc2{n2.hi, n2.lo};
+                }
+                shn[q] = sh;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int ev = (int)((__float_as_uint(y[q][a].s) >> 23) & 0xffu);
+                    if (ev) tmax = max(tmax, ev + sh);
+                }
+                if (eg == 0x7ff) tmax = kBadExp;
+            }
+        }
+        tmax = __reduce_max_sync(0xffffffffu, tmax);
+        if (lane == 0) sred[4 + warp] = tmax;
+        __syncthreads();
+        const int eWraw = max4(sred + 4);
+        const bool bad = eU == 0x7ff || eD == 0x7ff || eWraw >= kBadExp;
+        const int eW = eWraw == INT_MIN ? 0 : min(eWraw, kBadExp);   // y == 0 everywhere: any scale
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            unsigned char *p = dig + (2 * warp + h) * kPlane + g * 16 + 4 * t;
+            const float m0 = pow2f_or_zero(shn[2 * h] - eW + 134);       // |y 2^(sh - eW + 126)| < 1
+            const float m1 = pow2f_or_zero(shn[2 * h + 1] - eW + 134);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float d0[kS], d1[kS];
+                digits_df(y[2 * h][a].s, y[2 * h][a].c, m0, d0);
+                digits_df(y[2 * h + 1][a].s, y[2 * h + 1][a].c, m1, d1);
+#pragma unroll
+                for (int q = 0; q < kS; ++q)
+                    *reinterpret_cast<uint32_t *>(p + (a * kS + q) * kSlice) = pack_bf16(d0[q], d1[q]);
+            }
+        }
+        __syncthreads();
+
+        // ---- D: transposed contractions on tensor cores
+        df vo[4];
+        {
+            float acc[6][4];
+            contract<0>(dig_s, warp, lane, ft, acc);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) vo[q] = combine_levels(acc, q);
+        }
+        {
+            float acc[6][4];
+            contract<1>(dig_s + kS * kSlice, warp, lane, ft, acc);
+            store_tile<1>(bs, acc, warp, g, t);
+        }
+        {
+            float acc[6][4];
+            contract<2>(dig_s + 2 * kS * kSlice, warp, lane, ft, acc);
+            store_tile<2>(bt, acc, warp, g, t);
+        }
+        __syncthreads();
+
+        // ---- E: sum, undo the scales, store
+        // w = 2^((eU - 1022) + 2 (eD - 1022) + (eW - 126) - 32) V_out
+        const int SH = (eU - 1022) + 2 * (eD - 1022) + (eW - 126) - 32;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * warp + h, nb = k * 64 + g * 8 + 2 * t;
+            const float4 tv = *reinterpret_cast<const float4 *>(bt + tidx(k, g, 2 * t));
+            double o[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float2 sv = bs[sidx(k, g, 2 * t + c)];
+                const float th = c ? tv.z : tv.x, tl = c ? tv.w : tv.y;
+                const df a = dfx::two_sum(vo[2 * h + c].hi, sv.x);
+                const df b = dfx::two_sum(a.hi, th);
+                const float lo = __fadd_rn(__fadd_rn(__fadd_rn(vo[2 * h + c].lo, sv.y), tl), __fadd_rn(a.lo, b.lo));
+                o[c] = bad ? __longlong_as_double(0x7ff8000000000000ll)
+                           : scale2(dfx::f2d(b.hi) + dfx::f2d(lo), SH);
+            }
+            *reinterpret_cast<double2 *>(we + nb) = make_double2(o[0], o[1]);
+        }
+    }
+}
+
+static int launch(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s) {
+    auto kern = ax_f64tc_kernel;
+    int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
+    if (st != SEMAX_OK) return st;
+    st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
+    if (st != SEMAX_OK) return st;
+    int per_sm = 0;
+    st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kSmem));
+    if (st != SEMAX_OK) return st;
+    const int64_t grid = std::min<int64_t>(E, (int64_t)device_sm_count() * std::max(per_sm, 1));
+    kern<<<(unsigned)grid, kThreads, kSmem, s>>>(E, u, G, D, w);
+    return launch_status();
+}
+
+}  // namespace oz
+}  // namespace semax
+
+using namespace semax;
+
+extern "C" int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const double *D, double *w,
+                            void *stream) {
+    int st = check_args(E, N, u, G, D, w);
+    if (st != SEMAX_OK || E == 0) return st;
+    if (N != 7) return sem_ax_f64x(E, N, u, G, D, w, stream);   // other orders: the double-float tile
+    return oz::launch(E, u, G, D, w, (cudaStream_t)stream);
+}

@@ -1,0 +1,147 @@
+"""GPU parity of the tensor-core FP64-accurate form (exact digit slicing on
+BF16 tensor cores, sem_ax_f64tc) against the FP64 CPU oracle, through the C
+ABI.
+
+Error measure: ||w - w_ref||_inf / ||w_ref||_inf over the whole output.
+
+Tolerance.  Each operand keeps 6 base-256 digits (truncation 2^-49 of its
+element's scale), the tensor-core level sums are exact, the level sums and
+the geometric-factor multiply run in double-float (~2^-47 per operation,
+G split to 47 bits), and the dropped digit levels weigh < 2^-48.  About ten
+such terms pass through two contractions with 8-term sums (the gradient's
+worst case is 8 max|D| max|u|), so the bound is of order
+10 * 8 * 2^-47 ~ 6e-13 of the element's scale, and typically 1e-14.  The test
+holds it to TOL_TC = 1e-12, the FP64 requirement; the typical error is
+checked to stay below 2e-13.
+"""
+import numpy as np
+import pytest
+import torch
+
+import sem_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+TOL_TC = 1e-12
+TYPICAL_TC = 2e-13
+
+
+@pytest.fixture(scope="module")
+def semax():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1503_07659_gb300 as m
+    return m
+
+
+def rel_err(w, ref):
+    w = w.detach().cpu().double().numpy() if hasattr(w, "detach") else w
+    return float(np.max(np.abs(w - ref)) / np.max(np.abs(ref)))
+
+
+def run(semax, u, G, D):
+    w = semax.sem_ax_f64tc(u.cuda(), G.cuda(), D.cuda())
+    torch.cuda.synchronize()
+    return w
+
+
+@pytest.mark.parametrize("E", [1, 3, 77, 300])
+def test_f64tc_ragged_against_oracle(semax, oracle_mod, E):
+    m = si.make_mesh(np.random.default_rng(700 + E), E, 7)
+    ref = oracle_mod.sem_ax(m.u, m.G, m.D)
+    err = rel_err(run(semax, m.u, m.G, m.D), ref)
+    assert err <= TOL_TC
+    assert err <= TYPICAL_TC
+
+
+def test_f64tc_integer_inputs_are_exact(semax, oracle_mod):
+    """With small-integer u, G and D every digit product, level sum and
+    double-float step is exact, so the result equals the exact (integer)
+    FP64 value bit for bit.  This pins the exactness of the FP32
+    accumulation inside the tensor-core products, on which the method rests."""
+    rng = np.random.default_rng(71)
+    E = 40
+    u = torch.from_numpy(rng.integers(-100, 101, size=(E, 8, 8, 8)).astype(np.float64))
+    G = torch.from_numpy(rng.integers(0, 17, size=(E, 6, 8, 8, 8)).astype(np.float64))
+    D = torch.from_numpy(rng.integers(-8, 9, size=(8, 8)).astype(np.float64))
+    ref = oracle_mod.sem_ax(u, G, D)
+    w = run(semax, u, G, D).cpu().numpy()
+    assert np.array_equal(w, ref)
+
+
+def test_f64tc_full_size_sampled(semax, oracle_mod):
+    m = si.make_workload(1, device="cuda")[0]
+    w = semax.sem_ax_f64tc(m.u, m.G, m.D)
+    w64 = semax.sem_ax(m.u, m.G, m.D)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(24).choice(m.E, size=m.E // 50, replace=False))
+    it = torch.from_numpy(idx).cuda()
+    ref = oracle_mod.sem_ax(m.u[it].cpu(), m.G[it].cpu(), m.D.cpu())
+    assert rel_err(w[it], ref) <= TYPICAL_TC
+    r = semax.reduce(w, w64).cpu().numpy()
+    assert r[0] / r[1] <= TYPICAL_TC                   # whole output against the FP64 kernel
+
+
+@pytest.mark.parametrize("us,gs", [(1e-300, 1.0), (1e30, 1e-30), (1.0, 1e250), (2.0 ** -1000, 2.0 ** 900)])
+def test_f64tc_is_scale_invariant(semax, oracle_mod, us, gs):
+    """u and G far outside the float range: the per-element scale of u and
+    the per-node scale of G keep the result accurate."""
+    m = si.make_mesh(np.random.default_rng(72), 9, 7)
+    u, G = m.u * us, m.G * gs
+    ref = oracle_mod.sem_ax(u, G, m.D)
+    assert rel_err(run(semax, u, G, m.D), ref) <= TYPICAL_TC
+
+
+def test_f64tc_general_D(semax, oracle_mod):
+    """Any D works (no even/odd symmetry is used)."""
+    m = si.make_mesh(np.random.default_rng(73), 11, 7)
+    D = m.D.clone()
+    D[2, 3] += 0.25
+    D[5] *= 3.0
+    ref = oracle_mod.sem_ax(m.u, m.G, D)
+    assert rel_err(run(semax, m.u, m.G, D), ref) <= TYPICAL_TC
+
+
+def test_f64tc_zero_and_constant_fields(semax):
+    m = si.make_mesh(np.random.default_rng(74), 5, 7)
+    w0 = run(semax, torch.zeros_like(m.u), m.G, m.D)
+    assert torch.count_nonzero(w0).item() == 0
+    w1 = run(semax, torch.full_like(m.u, 3.25), m.G, m.D)
+    wr = run(semax, m.u, m.G, m.D)
+    # A 1 = 0 up to the rounding of D's row sums
+    assert w1.abs().max().item() <= 1e-12 * wr.abs().max().item()
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+@pytest.mark.parametrize("where", ["u", "G"])
+def test_f64tc_nonfinite_input_poisons_only_its_element(semax, oracle_mod, bad, where):
+    m = si.make_mesh(np.random.default_rng(75), 6, 7)
+    u, G = m.u.clone(), m.G.clone()
+    if where == "u":
+        u[3, 2, 5, 1] = bad
+    else:
+        G[3, 4, 1, 1, 6] = bad
+    ref = oracle_mod.sem_ax(np.delete(u.numpy(), 3, 0), np.delete(G.numpy(), 3, 0), m.D)
+    w = run(semax, u, G, m.D).cpu().numpy()
+    assert np.isnan(w[3]).all()
+    assert rel_err(np.delete(w, 3, 0), ref) <= TYPICAL_TC
+
+
+@pytest.mark.parametrize("N,E", [(3, 20), (15, 4), (4, 9)])
+def test_f64tc_other_orders_use_the_double_float_form(semax, oracle_mod, N, E):
+    m = si.make_mesh(np.random.default_rng(760 + N), E, N)
+    ref = oracle_mod.sem_ax(m.u, m.G, m.D)
+    assert rel_err(run(semax, m.u, m.G, m.D), ref) <= TOL_TC
+
+
+def test_f64tc_preserves_inputs_and_honours_stream(semax, oracle_mod):
+    m = si.make_mesh(np.random.default_rng(77), 50, 7)
+    u, G, D = m.u.cuda(), m.G.cuda(), m.D.cuda()
+    u0, G0 = u.clone(), G.clone()
+    s = torch.cuda.Stream()
+    w = torch.empty_like(u)
+    with torch.cuda.stream(s):
+        semax.sem_ax_f64tc(u, G, D, w, stream=s)
+    s.synchronize()
+    assert torch.equal(u, u0) and torch.equal(G, G0)
+    assert rel_err(w, oracle_mod.sem_ax(m.u, m.G, m.D)) <= TYPICAL_TC
