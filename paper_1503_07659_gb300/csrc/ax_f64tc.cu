@@ -18,7 +18,8 @@
 //
 // Per element (one CTA of 4 warps; warp w owns the planes k = 2w, 2w+1 for
 // every pointwise step, in the layout of the m16n8 accumulator of the
-// r-direction tile):
+// r-direction tile; u and G of the CTA's next element are fetched with
+// cp.async into shared memory while the current one finishes):
 //   A  u (FP64) -> per-element scale -> 6 BF16 digit planes in shared memory;
 //   B  ur, us, ut on tensor cores (B operand: the digits of D^T, held in
 //      registers for the CTA's lifetime); ur stays in registers, us and ut
@@ -43,10 +44,18 @@ using dfx::df;
 
 constexpr int kThreads = 128;                // one element per CTA pass
 constexpr int kS = 6;                        // digits per operand
-constexpr int kPlane = 144;                  // bytes per 8 x 8 BF16 plane, padded (ldmatrix along k)
+constexpr int kPlane = 128;                  // bytes per 8 x 8 BF16 plane (rows XOR-swizzled)
 constexpr int kSlice = 8 * kPlane;           // one digit of an 8^3 operand
 constexpr int kDigBytes = 3 * kS * kSlice;   // digits of wr, ws, wt (u reuses the first six)
-constexpr size_t kSmem = kDigBytes + 2 * 512 * sizeof(float2) + 16 * sizeof(int);
+constexpr int kBufBytes = 512 * 8;           // one double-float per node
+constexpr int kGBytes = 6 * 512 * 8;         // one element's G (FP64), staged
+constexpr int kUBytes = 512 * 8;             // one element's u (FP64), staged
+constexpr size_t kSmem = kDigBytes + 2 * kBufBytes + kGBytes + kUBytes + 16 * sizeof(int);
+
+// Byte offset of row j of plane p inside a digit slice: the 16-byte rows of
+// a plane are permuted by p, so that ldmatrix over the 8 rows of a plane
+// and over the 8 planes of a row both touch 8 distinct bank groups.
+__device__ __forceinline__ int prow(int p, int j) { return p * kPlane + ((j ^ p) << 4); }
 constexpr int kBadExp = 1 << 20;             // marks a non-finite input in the exponent reductions
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -73,10 +82,8 @@ __device__ __forceinline__ void mma8(float (&c)[4], uint32_t a0, uint32_t a1, ui
                  : "r"(a0), "r"(a1), "r"(b0));
 }
 
-__device__ __forceinline__ double2 ld_stream2(const double *p) {
-    double2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
-    return v;
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
 __device__ __forceinline__ int bexp(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
@@ -119,32 +126,32 @@ __device__ __forceinline__ void digits_fp64(double x, int E, float (&d)[kS]) {
     for (int i = 0; i < kS; ++i) d[i] = int_to_float(q[i]);
 }
 
-// Balanced base-256 digits of the double-float value (hi + lo) * m, m a
-// power of two with |(hi + lo) * m| < 256 (1 + 2^-20) and |lo| a few units
-// in the last place of hi at most: (hi + lo) m = sum_q d[q] 2^(-8q) + (error
-// <= 2^-41).  Each digit is the sum of the digit of hi and that of lo, so
-// |d[0]| <= 256 and |d[q]| <= 256 for q >= 1.
-// Every step is exact: t * 256 is a scaling, adding and subtracting
-// 1.5 * 2^23 rounds to an integer, and the remainder is representable.
-__device__ __forceinline__ void digits_df(float hi, float lo, float m, float (&d)[kS]) {
+// Balanced base-256 digits of the double-float value (hi + lo) m, m a power
+// of two, |hi m| < 256 (1 + 2^-20) and |lo| <= ulp(hi) / 2 (normalised):
+// (hi + lo) m = sum_q d[q] 2^(-8q) + (error <= 2^-40), |d[q]| <= 256.
+// Digits 0-2 come from hi alone, every step exact (t 256 is a scaling;
+// adding and subtracting 1.5 2^23 rounds to an integer; the remainder is
+// representable).  Then lo m, at most ulp(t) / 2 <= 2^-17, joins the
+// remainder (|r| <= 1/2 in units of 2^-16): one rounding of at most 2^-24
+// there, 2^-40 of t's unit, and |r + lo m 2^16| <= 1 keeps digit 3 within 256.
+__device__ __forceinline__ void digits_df(float hi, float lo, float m, float m16, float (&d)[kS]) {
     constexpr float C = 12582912.0f;
     const float t = __fmul_rn(hi, m);
     float q = __fsub_rn(__fadd_rn(t, C), C);
     float r = __fsub_rn(t, q);
     d[0] = q;
 #pragma unroll
-    for (int i = 1; i < kS; ++i) {
+    for (int i = 1; i < 3; ++i) {
         q = __fsub_rn(__fmaf_rn(r, 256.0f, C), C);
         r = __fmaf_rn(r, 256.0f, -q);
         d[i] = q;
     }
-    // |lo * m| < 1/2: the digit 0 of lo is zero
-    float rl = __fmul_rn(lo, m);
+    r = __fmaf_rn(lo, m16, r);   // m16 = m 2^16
 #pragma unroll
-    for (int i = 1; i < kS; ++i) {
-        q = __fsub_rn(__fmaf_rn(rl, 256.0f, C), C);
-        rl = __fmaf_rn(rl, 256.0f, -q);
-        d[i] = __fadd_rn(d[i], q);
+    for (int i = 3; i < kS; ++i) {
+        q = __fsub_rn(__fmaf_rn(r, 256.0f, C), C);
+        r = __fmaf_rn(r, 256.0f, -q);
+        d[i] = q;
     }
 }
 
@@ -154,11 +161,14 @@ __device__ __forceinline__ float pow2f_or_zero(int k) {
 }
 
 // V = x2 + x3 2^-8 + x4 2^-16 + x5 2^-24 + x6 2^-32 + x7 2^-40 (x_L the exact
-// level sums) as an unevaluated sum hi + lo; the two leading additions are
-// error-free, the rest err by < 2^-47 of |V|'s bound.
+// level sums, |x_L| < 2^22) as an unevaluated sum hi + lo.  The two leading
+// additions are error-free with the fast two-sum: either the larger
+// magnitude comes first, or the sum is exact (x2 + x3 2^-8 needs at most 23
+// bits when |x2| < |x3| 2^-8, likewise for the next); the rest err by
+// < 2^-47 of |V|'s bound.
 __device__ __forceinline__ df combine_levels(const float (&x)[6][4], int e) {
-    const df a = dfx::two_sum(x[0][e], __fmul_rn(x[1][e], 0x1p-8f));
-    const df b = dfx::two_sum(a.hi, __fmul_rn(x[2][e], 0x1p-16f));
+    const df a = dfx::fast_two_sum(x[0][e], __fmul_rn(x[1][e], 0x1p-8f));
+    const df b = dfx::fast_two_sum(a.hi, __fmul_rn(x[2][e], 0x1p-16f));
     const float r = __fmaf_rn(x[3][e], 0x1p-24f, __fmaf_rn(x[4][e], 0x1p-32f, __fmul_rn(x[5][e], 0x1p-40f)));
     return {b.hi, __fadd_rn(__fadd_rn(a.lo, b.lo), r)};
 }
@@ -175,7 +185,7 @@ __device__ __forceinline__ void contract(uint32_t base, int warp, int lane, cons
                                          float (&acc)[6][4]) {
     const int mi = lane >> 3, rr = lane & 7;
     const int blk = 2 * warp + (mi & 1);
-    const uint32_t addr = base + (mi >> 1) * kSlice + (DIR == 2 ? rr * kPlane + blk * 16 : blk * kPlane + rr * 16);
+    const uint32_t addr = base + (mi >> 1) * kSlice + (DIR == 2 ? prow(rr, blk) : prow(blk, rr));
     uint32_t a[kS][2];
 #pragma unroll
     for (int q = 0; q < kS; q += 2) {
@@ -230,6 +240,22 @@ __device__ __forceinline__ void store_tile(float2 *buf, const float (&acc)[6][4]
     }
 }
 
+// x 2^-sh as hi + lo by bit operations: hi = the top 24 bits of x's
+// significand, lo = the next 23.  K = (896 + sh) << 23 turns the double's
+// exponent field (its low 9 bits, shifted into place with the significand)
+// into the float's; entries with eb <= 896 + sh (below 2^-126 of the node's
+// largest) become zero.  lo = r23 2^-46 2^(ef - 127), formed as a product so
+// that small exponents underflow gracefully.
+__device__ __forceinline__ df split_g(double x, int eb, unsigned K, int ebmin) {
+    const unsigned h32 = (unsigned)__double2hiint(x), l32 = (unsigned)__double2loint(x);
+    const unsigned f = __funnelshift_l(l32, h32, 3);
+    const unsigned hb = (f - K) | (h32 & 0x80000000u);
+    const float r = __fsub_rn(__uint_as_float(0x4B000000u | ((l32 >> 6) & 0x7fffffu)), 8388608.0f);
+    const float sc = __fmul_rn(__uint_as_float(hb & 0x7f800000u), 0x1p-46f);
+    const float lo = __uint_as_float(__float_as_uint(__fmul_rn(r, sc)) | (h32 & 0x80000000u));
+    return eb >= ebmin ? df{__uint_as_float(hb), lo} : df{0.0f, 0.0f};
+}
+
 // y = sum_b Gh[b] V[b] (double-float products, Dot2-style accumulation)
 __device__ __forceinline__ acc2 dot3(df g0, df g1, df g2, df v0, df v1, df v2) {
     const float m = __fmul_rn(g0.hi, v0.hi);
@@ -257,10 +283,29 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
     unsigned char *dig = smem;
     float2 *bs = reinterpret_cast<float2 *>(smem + kDigBytes);   // s-direction results
     float2 *bt = bs + 512;                                         // t-direction results
-    int *sred = reinterpret_cast<int *>(bt + 512);                 // [0, 4) u, [4, 8) y exponents
-    const uint32_t dig_s = smem_u32(dig);
+    const double2 *gst = reinterpret_cast<const double2 *>(bt + 512);   // staged G [6][256 node pairs]
+    const double2 *ust = gst + 6 * 256;                            // staged u [256 node pairs]
+    int *sred = reinterpret_cast<int *>(smem + kDigBytes + 2 * kBufBytes + kGBytes + kUBytes);   // [0, 4) u, [4, 8) y exponents
+    const uint32_t dig_s = smem_u32(dig), gst_s = smem_u32(gst), ust_s = smem_u32(ust);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+
+    // Every thread stages, and later reads back, only its own 16-byte chunks
+    // of u and G (its node pairs (k = 2w + h, j = g, i = 2t, 2t + 1)), so the
+    // staging buffers need no barrier: element e + gridDim.x is fetched while
+    // element e finishes.
+    auto prefetch = [&](int64_t ep) {
+        const double *ue = u + ep * 512, *Ge = G + ep * 3072;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int pr = (2 * warp + h) * 32 + g * 4 + t;   // node pair
+            cp_async16(ust_s + 16 * pr, ue + 2 * pr);
+#pragma unroll
+            for (int a = 0; a < 6; ++a) cp_async16(gst_s + 16 * (a * 256 + pr), Ge + a * 512 + 2 * pr);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (blockIdx.x < E) prefetch(blockIdx.x);
 
     // D digits, once per CTA: B fragments of D^T (gradient) and D (transposed)
     int eD = 1;
@@ -280,14 +325,13 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
     }
 
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
-        const double *ue = u + e * 512;
-        const double *Ge = G + e * 3072;
         double *we = w + e * 512;
 
         // ---- A: u -> digits (thread's nodes: k = 2w + h, j = g, i = 2t + c)
+        asm volatile("cp.async.wait_all;" ::: "memory");
         double2 uv[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) uv[h] = ld_stream2(ue + (2 * warp + h) * 64 + g * 8 + 2 * t);
+        for (int h = 0; h < 2; ++h) uv[h] = ust[(2 * warp + h) * 32 + g * 4 + t];
         int ex = 1;
 #pragma unroll
         for (int h = 0; h < 2; ++h) ex = max(ex, max(bexp(uv[h].x), bexp(uv[h].y)));
@@ -300,7 +344,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
             float d0[kS], d1[kS];
             digits_fp64(uv[h].x, eU, d0);
             digits_fp64(uv[h].y, eU, d1);
-            unsigned char *p = dig + (2 * warp + h) * kPlane + g * 16 + 4 * t;
+            unsigned char *p = dig + prow(2 * warp + h, g) + 4 * t;
 #pragma unroll
             for (int q = 0; q < kS; ++q) *reinterpret_cast<uint32_t *>(p + q * kSlice) = pack_bf16(d0[q], d1[q]);
         }
@@ -335,7 +379,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
             const int k = 2 * warp + h, nb = k * 64 + g * 8 + 2 * t;
             double2 gv[6];
 #pragma unroll
-            for (int a = 0; a < 6; ++a) gv[a] = ld_stream2(Ge + a * 512 + nb);
+            for (int a = 0; a < 6; ++a) gv[a] = gst[a * 256 + (nb >> 1)];
             const float4 tv = *reinterpret_cast<const float4 *>(bt + tidx(k, g, 2 * t));
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
@@ -344,16 +388,18 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 const df Vs{sv.x, sv.y};
                 const df Vt = c ? df{tv.z, tv.w} : df{tv.x, tv.y};
                 double Gc[6];
-                int eg = 0;
+                int ebs[6], eg = 0;
 #pragma unroll
                 for (int a = 0; a < 6; ++a) {
                     Gc[a] = c ? gv[a].y : gv[a].x;
-                    eg = max(eg, bexp(Gc[a]));
+                    ebs[a] = bexp(Gc[a]);
+                    eg = max(eg, ebs[a]);
                 }
                 const int sh = max(eg, 1) - 1023;   // G * 2^-sh has magnitude < 2
+                const unsigned K = (unsigned)(896 + sh) << 23;
                 df Gh[6];
 #pragma unroll
-                for (int a = 0; a < 6; ++a) Gh[a] = dfx::split_double(Gc[a], sh);
+                for (int a = 0; a < 6; ++a) Gh[a] = split_g(Gc[a], ebs[a], K, 897 + sh);
                 y[q][0] = dot3(Gh[0], Gh[1], Gh[2], vr[q], Vs, Vt);
                 y[q][1] = dot3(Gh[1], Gh[3], Gh[4], vr[q], Vs, Vt);
                 y[q][2] = dot3(Gh[2], Gh[4], Gh[5], vr[q], Vs, Vt);
@@ -373,6 +419,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 if (eg == 0x7ff) tmax = kBadExp;
             }
         }
+        if (e + gridDim.x < E) prefetch(e + gridDim.x);   // this thread's staged u and G are consumed
         tmax = __reduce_max_sync(0xffffffffu, tmax);
         if (lane == 0) sred[4 + warp] = tmax;
         __syncthreads();
@@ -381,14 +428,16 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         const int eW = eWraw == INT_MIN ? 0 : min(eWraw, kBadExp);   // y == 0 everywhere: any scale
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            unsigned char *p = dig + (2 * warp + h) * kPlane + g * 16 + 4 * t;
+            unsigned char *p = dig + prow(2 * warp + h, g) + 4 * t;
             const float m0 = pow2f_or_zero(shn[2 * h] - eW + 134);       // |y 2^(sh - eW + 126)| < 1
             const float m1 = pow2f_or_zero(shn[2 * h + 1] - eW + 134);
+            const float m0s = pow2f_or_zero(shn[2 * h] - eW + 150);      // m 2^16, finite when m is clamped
+            const float m1s = pow2f_or_zero(shn[2 * h + 1] - eW + 150);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 float d0[kS], d1[kS];
-                digits_df(y[2 * h][a].s, y[2 * h][a].c, m0, d0);
-                digits_df(y[2 * h + 1][a].s, y[2 * h + 1][a].c, m1, d1);
+                digits_df(y[2 * h][a].s, y[2 * h][a].c, m0, m0s, d0);
+                digits_df(y[2 * h + 1][a].s, y[2 * h + 1][a].c, m1, m1s, d1);
 #pragma unroll
                 for (int q = 0; q < kS; ++q)
                     *reinterpret_cast<uint32_t *>(p + (a * kS + q) * kSlice) = pack_bf16(d0[q], d1[q]);
@@ -431,8 +480,12 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 const df a = dfx::two_sum(vo[2 * h + c].hi, sv.x);
                 const df b = dfx::two_sum(a.hi, th);
                 const float lo = __fadd_rn(__fadd_rn(__fadd_rn(vo[2 * h + c].lo, sv.y), tl), __fadd_rn(a.lo, b.lo));
-                o[c] = bad ? __longlong_as_double(0x7ff8000000000000ll)
-                           : scale2(dfx::f2d(b.hi) + dfx::f2d(lo), SH);
+                double oh, ol;
+                if (dfx::f2d_scaled(b.hi, SH, oh) && dfx::f2d_scaled(lo, SH, ol))
+                    o[c] = oh + ol;
+                else
+                    o[c] = scale2(dfx::f2d(b.hi) + dfx::f2d(lo), SH);
+                if (bad) o[c] = __longlong_as_double(0x7ff8000000000000ll);
             }
             *reinterpret_cast<double2 *>(we + nb) = make_double2(o[0], o[1]);
         }
