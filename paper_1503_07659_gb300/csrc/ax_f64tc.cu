@@ -243,8 +243,8 @@ __device__ __forceinline__ void store_tile(float2 *buf, const float (&acc)[6][4]
 // x 2^-sh as hi + lo by bit operations: hi = the top 24 bits of x's
 // significand, lo = the next 23.  K = (896 + sh) << 23 turns the double's
 // exponent field (its low 9 bits, shifted into place with the significand)
-// into the float's; entries with eb <= 896 + sh (below 2^-126 of the node's
-// largest) become zero.  lo = r23 2^-46 2^(ef - 127), formed as a product so
+// into the float's; entries with eb < ebmin = max(897 + sh, 1) (zeros,
+// subnormals, and values below 2^-126 of the scale) become zero.  lo = r23 2^-46 2^(ef - 127), formed as a product so
 // that small exponents underflow gracefully.
 __device__ __forceinline__ df split_g(double x, int eb, unsigned K, int ebmin) {
     const unsigned h32 = (unsigned)__double2hiint(x), l32 = (unsigned)__double2loint(x);
@@ -339,11 +339,17 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         if (lane == 0) sred[warp] = ex;
         __syncthreads();
         const int eU = max4(sred);
+        // u 2^-(eU - 1023) in (-2, 2) split hi + lo (47 bits), normalised; its
+        // digits at t = 128 u 2^-(eU - 1023) = 256 u 2^-(eU - 1022)
+        const unsigned Ku = (unsigned)(eU - 127) << 23;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             float d0[kS], d1[kS];
-            digits_fp64(uv[h].x, eU, d0);
-            digits_fp64(uv[h].y, eU, d1);
+            const df a0 = split_g(uv[h].x, bexp(uv[h].x), Ku, max(eU - 126, 1));
+            const df a1 = split_g(uv[h].y, bexp(uv[h].y), Ku, max(eU - 126, 1));
+            const df n0 = dfx::fast_two_sum(a0.hi, a0.lo), n1 = dfx::fast_two_sum(a1.hi, a1.lo);
+            digits_df(n0.hi, n0.lo, 128.0f, 8388608.0f, d0);
+            digits_df(n1.hi, n1.lo, 128.0f, 8388608.0f, d1);
             unsigned char *p = dig + prow(2 * warp + h, g) + 4 * t;
 #pragma unroll
             for (int q = 0; q < kS; ++q) *reinterpret_cast<uint32_t *>(p + q * kSlice) = pack_bf16(d0[q], d1[q]);
@@ -399,7 +405,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 const unsigned K = (unsigned)(896 + sh) << 23;
                 df Gh[6];
 #pragma unroll
-                for (int a = 0; a < 6; ++a) Gh[a] = split_g(Gc[a], ebs[a], K, 897 + sh);
+                for (int a = 0; a < 6; ++a) Gh[a] = split_g(Gc[a], ebs[a], K, max(897 + sh, 1));
                 y[q][0] = dot3(Gh[0], Gh[1], Gh[2], vr[q], Vs, Vt);
                 y[q][1] = dot3(Gh[1], Gh[3], Gh[4], vr[q], Vs, Vt);
                 y[q][2] = dot3(Gh[2], Gh[4], Gh[5], vr[q], Vs, Vt);

@@ -112,6 +112,20 @@ def test_f64tc_zero_and_constant_fields(semax):
     assert w1.abs().max().item() <= 1e-12 * wr.abs().max().item()
 
 
+def test_f64tc_zero_geometric_factor_nodes(semax, oracle_mod):
+    """Nodes whose six G entries are all zero, and an element with G = 0:
+    zero entries are split into zero, not into a value of the node's scale."""
+    m = si.make_mesh(np.random.default_rng(78), 7, 7)
+    G = m.G.clone()
+    G[2, :, 3, 4, 5] = 0.0
+    G[2, :, 0, 0, 0] = 0.0
+    G[5] = 0.0
+    ref = oracle_mod.sem_ax(m.u, G, m.D)
+    w = run(semax, m.u, G, m.D)
+    assert rel_err(w, ref) <= TYPICAL_TC
+    assert torch.count_nonzero(w[5]).item() == 0
+
+
 @pytest.mark.parametrize("bad", [float("nan"), float("inf")])
 @pytest.mark.parametrize("where", ["u", "G"])
 def test_f64tc_nonfinite_input_poisons_only_its_element(semax, oracle_mod, bad, where):
