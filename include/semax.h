@@ -226,14 +226,16 @@ int sem_ax_diag(int64_t E, int N, const double *G, const double *D, double *diag
  * doubles, equal copies at shared nodes); b must already be summed (gs) and
  * masked.  Create allocates the work vectors and computes the preconditioner;
  * G, D and gs stay bound to the solver; flags = 0 applies A with the FP64
- * kernel of sem_ax, SEMAX_PCG_F64X with that of sem_ax_f64x.  Solve starts from x (in/out) and
+ * kernel of sem_ax, SEMAX_PCG_F64X with that of sem_ax_f64x, SEMAX_PCG_F64TC
+ * with that of sem_ax_f64tc (at most one of the two flags).  Solve starts from x (in/out) and
  * stops when ||r|| <= rtol ||r_0|| (norms weighted by 1/multiplicity) or after
  * max_iter iterations, checked every 10 iterations: a block of 10 iterations
  * is one CUDA-graph launch with all scalars in device memory.  Solve blocks
  * the host until it returns; it is ordered after earlier work on `stream` and
  * later work on `stream` is ordered after it. */
 typedef struct semax_pcg semax_pcg;
-enum { SEMAX_PCG_F64X = 1 };   /* apply A with sem_ax_f64x (double-float, FP64-accurate) */
+enum { SEMAX_PCG_F64X = 1,     /* apply A with sem_ax_f64x (double-float, FP64-accurate) */
+       SEMAX_PCG_F64TC = 2 };   /* apply A with sem_ax_f64tc (tensor-core digit slicing, FP64-accurate) */
 int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G, const double *D, const semax_gs *gs,
                    int flags);
 int sem_pcg_solve(semax_pcg *pcg, const double *b, double *x, int max_iter, double rtol, int *iters,

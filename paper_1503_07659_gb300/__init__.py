@@ -237,11 +237,13 @@ def sem_ax_diag(G: torch.Tensor, D: torch.Tensor, out: torch.Tensor | None = Non
 class PCG:
     """Jacobi-PCG on Q A_L Q^T (sem_pcg_*); G, D and the gather-scatter stay bound."""
 
-    def __init__(self, G: torch.Tensor, D: torch.Tensor, gs: GatherScatter, f64x: bool = False):
+    def __init__(self, G: torch.Tensor, D: torch.Tensor, gs: GatherScatter, f64x: bool = False,
+                 f64tc: bool = False):
         self._keep = (G, D, gs)
         self._handle = ctypes.c_void_p()
+        flags = (1 if f64x else 0) | (2 if f64tc else 0)
         check(_lib.lib().sem_pcg_create(ctypes.byref(self._handle), G.shape[0], D.shape[0] - 1, _ptr(G), _ptr(D),
-                                        gs._handle, 1 if f64x else 0), "sem_pcg_create")
+                                        gs._handle, flags), "sem_pcg_create")
 
     def solve(self, b: torch.Tensor, x: torch.Tensor, max_iter: int = 1000, rtol: float = 1e-10,
               stream=None) -> tuple[int, float]:

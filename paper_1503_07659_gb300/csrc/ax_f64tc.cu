@@ -417,11 +417,9 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                     y[q][a] = acc2{n2.hi, n2.lo};
                 }
                 shn[q] = sh;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const int ev = (int)((__float_as_uint(y[q][a].s) >> 23) & 0xffu);
-                    if (ev) tmax = max(tmax, ev + sh);
-                }
+                const float ym = fmaxf(fabsf(y[q][0].s), fmaxf(fabsf(y[q][1].s), fabsf(y[q][2].s)));
+                const int ev = (int)(__float_as_uint(ym) >> 23);
+                if (ev) tmax = max(tmax, ev + sh);
                 if (eg == 0x7ff) tmax = kBadExp;
             }
         }
@@ -474,6 +472,8 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         // ---- E: sum, undo the scales, store
         // w = 2^((eU - 1022) + 2 (eD - 1022) + (eW - 126) - 32) V_out
         const int SH = (eU - 1022) + 2 * (eD - 1022) + (eW - 126) - 32;
+        const bool SHok = SH >= -1022 && SH <= 1023;
+        const double scl = __longlong_as_double((long long)(min(max(SH, -1022), 1023) + 1023) << 52);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = 2 * warp + h, nb = k * 64 + g * 8 + 2 * t;
@@ -486,12 +486,8 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 const df a = dfx::two_sum(vo[2 * h + c].hi, sv.x);
                 const df b = dfx::two_sum(a.hi, th);
                 const float lo = __fadd_rn(__fadd_rn(__fadd_rn(vo[2 * h + c].lo, sv.y), tl), __fadd_rn(a.lo, b.lo));
-                double oh, ol;
-                if (dfx::f2d_scaled(b.hi, SH, oh) && dfx::f2d_scaled(lo, SH, ol))
-                    o[c] = oh + ol;
-                else
-                    o[c] = scale2(dfx::f2d(b.hi) + dfx::f2d(lo), SH);
-                if (bad) o[c] = __longlong_as_double(0x7ff8000000000000ll);
+                const double v = (double)b.hi + (double)lo;
+                o[c] = bad ? __longlong_as_double(0x7ff8000000000000ll) : (SHok ? v * scl : scale2(v, SH));
             }
             *reinterpret_cast<double2 *>(we + nb) = make_double2(o[0], o[1]);
         }

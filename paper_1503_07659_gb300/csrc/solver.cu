@@ -312,12 +312,11 @@ struct semax_pcg {
     unsigned magic = 0x9c9u;
 };
 
-extern "C" int sem_ax_f64x(int64_t E, int N, const double *u, const double *G, const double *D, double *w,
-                           void *stream);
 
 // w = A_L v with the operator the solver was created with
 static int pcg_apply_a(semax_pcg *s, const double *v, double *w, cudaStream_t cs) {
     if (s->flags & SEMAX_PCG_F64X) return sem_ax_f64x(s->E, s->N, v, s->G, s->D, w, cs);
+    if (s->flags & SEMAX_PCG_F64TC) return sem_ax_f64tc(s->E, s->N, v, s->G, s->D, w, cs);
     return launch_plain<double>(s->E, s->N, default_tile<double>(s->N + 1), v, s->G, s->D, w, nullptr,
                                 Helm<double>{nullptr, 1.0, 0.0}, cs);
 }
@@ -359,7 +358,9 @@ extern "C" int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G
                               const semax_gs *gs, int flags) {
     if (!pcg) return SEMAX_EINVAL;
     *pcg = nullptr;
-    if (E <= 0 || !G || !D || !gs || gs->magic != 0x95u || (flags & ~SEMAX_PCG_F64X)) return SEMAX_EINVAL;
+    if (E <= 0 || !G || !D || !gs || gs->magic != 0x95u || (flags & ~(SEMAX_PCG_F64X | SEMAX_PCG_F64TC)) ||
+        flags == (SEMAX_PCG_F64X | SEMAX_PCG_F64TC))
+        return SEMAX_EINVAL;
     if (N < 1 || N > kMaxN) return SEMAX_EUNSUPPORTED_N;
     const int64_t count = E * (N + 1) * (N + 1) * (N + 1);
     if (gs->nlocal != count) return SEMAX_EINVAL;

@@ -107,14 +107,17 @@ def test_pcg_with_double_float_operator_matches(semax, solver_oracle):
     gs = semax.GatherScatter(m.l2g, m.nglobal, m.boundary)
     bd = torch.from_numpy(b).cuda()
     sols = []
-    for f64x in (False, True):
-        pcg = semax.PCG(G.cuda(), D.cuda(), gs, f64x=f64x)
+    for kw in ({}, {"f64x": True}, {"f64tc": True}):
+        pcg = semax.PCG(G.cuda(), D.cuda(), gs, **kw)
         x = torch.zeros_like(bd)
         it, rel = pcg.solve(bd, x, max_iter=1000, rtol=1e-12)
         assert rel <= 1e-12
         sols.append(x.cpu().numpy())
         pcg.close()
-    assert np.max(np.abs(sols[0] - sols[1])) <= 1e-10 * np.max(np.abs(sols[0]))
+    for s in sols[1:]:
+        assert np.max(np.abs(sols[0] - s)) <= 1e-10 * np.max(np.abs(sols[0]))
+    with pytest.raises(semax.SemaxError):
+        semax.PCG(G.cuda(), D.cuda(), gs, f64x=True, f64tc=True)
     gs.close()
 
 
