@@ -136,9 +136,8 @@ __device__ __forceinline__ void digits_fp64(double x, int E, float (&d)[kS]) {
 // there, 2^-40 of t's unit, and |r + lo m 2^16| <= 1 keeps digit 3 within 256.
 __device__ __forceinline__ void digits_df(float hi, float lo, float m, float m16, float (&d)[kS]) {
     constexpr float C = 12582912.0f;
-    const float t = __fmul_rn(hi, m);
-    float q = __fsub_rn(__fadd_rn(t, C), C);
-    float r = __fsub_rn(t, q);
+    float q = __fsub_rn(__fmaf_rn(hi, m, C), C);   // t = hi m is exact, so is t - q
+    float r = __fmaf_rn(hi, m, -q);
     d[0] = q;
 #pragma unroll
     for (int i = 1; i < 3; ++i) {
@@ -167,10 +166,13 @@ __device__ __forceinline__ float pow2f_or_zero(int k) {
 // bits when |x2| < |x3| 2^-8, likewise for the next); the rest err by
 // < 2^-47 of |V|'s bound.
 __device__ __forceinline__ df combine_levels(const float (&x)[6][4], int e) {
-    const df a = dfx::fast_two_sum(x[0][e], __fmul_rn(x[1][e], 0x1p-8f));
-    const df b = dfx::fast_two_sum(a.hi, __fmul_rn(x[2][e], 0x1p-16f));
-    const float r = __fmaf_rn(x[3][e], 0x1p-24f, __fmaf_rn(x[4][e], 0x1p-32f, __fmul_rn(x[5][e], 0x1p-40f)));
-    return {b.hi, __fadd_rn(__fadd_rn(a.lo, b.lo), r)};
+    // fast two-sums with the scaled operand formed inside the FMAs (x 2^-8k is exact)
+    const float s1 = __fmaf_rn(x[1][e], 0x1p-8f, x[0][e]);
+    const float e1 = __fmaf_rn(x[1][e], 0x1p-8f, -__fsub_rn(s1, x[0][e]));
+    const float s2 = __fmaf_rn(x[2][e], 0x1p-16f, s1);
+    const float e2 = __fmaf_rn(x[2][e], 0x1p-16f, -__fsub_rn(s2, s1));
+    const float r = __fmaf_rn(x[3][e], 0x1p-24f, __fmaf_rn(x[4][e], 0x1p-32f, __fmaf_rn(x[5][e], 0x1p-40f, e1)));
+    return {s2, __fadd_rn(r, e2)};
 }
 
 // One 16 x 8 output tile of a contraction along direction DIR (0: r / i,
