@@ -397,7 +397,16 @@ def run_ours(args, rank, world):
     t_cp = time_region(lambda: semax.sem_ax_from_host(u_h, G_h, D_h, w_h, bufs), e2e_steps,
                        max(3, args.warmup // 10), world) / e2e_steps
     assert torch.equal(w_h, w.cpu()), "end-to-end result differs from the device-resident result"
+    # the host link's ceiling for this step: a plain pinned-to-device copy of
+    # the step's input bytes (copy engine; more streams or other chunk sizes
+    # measured the same ~210 GB/s on this machine)
+    t_h2d = time_region(lambda: (bufs["u"].copy_(u_h, non_blocking=True), bufs["G"].copy_(G_h, non_blocking=True)),
+                        5, 2, world) / 5
+    h2d_gbs = (u_h.numel() + G_h.numel()) * 8 / t_h2d / 1e9
+    in_bytes = (u_h.numel() + G_h.numel() + D_h.numel()) * 8
     e2e = {"value": world * dofs / t_zc / 1e9, "unit": "GDOF/s",
+           "h2d_copy_gbs": h2d_gbs, "input_gbs": in_bytes / t_zc / 1e9,
+           "frac_of_h2d_copy": in_bytes / t_zc / 1e9 / h2d_gbs,
            "h2d_bytes_per_step": u_h.numel() * 8 + G_h.numel() * 8 + D_h.numel() * 8,
            "d2h_bytes_per_step": w_h.numel() * 8, "steps": e2e_steps,
            "path": "sem_ax on pinned host arrays: the kernel streams u, G, D from and w to host memory "
@@ -420,6 +429,8 @@ def run_ours(args, rank, world):
                       world) / args.steps
     f64tc = {"gdofs": world * dofs / t_t / 1e9, "hbm_gbs": world * dofs * bytes_per_node(8) / t_t / 1e9,
              "us_per_call": t_t * 1e6, "rel_err_vs_f64": rel_err_gpu(semax, wt, w),
+             "hbm_frac_of_measured": world * dofs * bytes_per_node(8) / t_t / 1e9 / load_peaks().get("hbm_gbs", 6786.6),
+             "bound": "instruction issue (tensor pipe ~17 % busy; digit extraction and double-float work on the CUDA cores)",
              "arith": "contractions on BF16 tensor cores by exact base-256 digit slicing (levels 2..7), "
                       "double-float level sums and geometric factor; FP64 in/out"}
     del wt

@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "mma_sync.cuh"
 
 namespace semax {
 namespace tc {
@@ -49,29 +50,12 @@ __device__ __forceinline__ uint32_t swz(int k, int j, int i) {
 
 __device__ __forceinline__ int widx(int k, int j, int i) { return k * kWPlane + j * kWRow + i; }
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t a, uint32_t (&r)[4]) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t a, uint32_t (&r)[4]) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
-}
-__device__ __forceinline__ uint32_t movm_t(uint32_t x) {
-    uint32_t y;
-    asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;\n" : "=r"(y) : "r"(x));
-    return y;
-}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return mma::smem_u32(p); }
+__device__ __forceinline__ void ldsm_x4(uint32_t a, uint32_t (&r)[4]) { mma::ldsm_x4(a, r[0], r[1], r[2], r[3]); }
+__device__ __forceinline__ void ldsm_x4_t(uint32_t a, uint32_t (&r)[4]) { mma::ldsm_x4_t(a, r[0], r[1], r[2], r[3]); }
+using mma::movm_t;
 __device__ __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    mma::bf16_16816(c, a[0], a[1], a[2], a[3], b0, b1);
 }
 
 __device__ __forceinline__ uint32_t pack(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t *>(&h); }

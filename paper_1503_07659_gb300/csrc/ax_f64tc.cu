@@ -35,6 +35,7 @@
 #include <climits>
 
 #include "ax_f64x.cuh"
+#include "mma_sync.cuh"
 
 namespace semax {
 namespace oz {
@@ -58,29 +59,7 @@ constexpr size_t kSmem = kDigBytes + 2 * kBufBytes + kGBytes + kUBytes + 16 * si
 __device__ __forceinline__ int prow(int p, int j) { return p * kPlane + ((j ^ p) << 4); }
 constexpr int kBadExp = 1 << 20;             // marks a non-finite input in the exponent reductions
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void ldsm4(uint32_t a, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
-}
-__device__ __forceinline__ void ldsm4t(uint32_t a, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
-}
-__device__ __forceinline__ void mma16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                      uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ void mma8(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a0), "r"(a1), "r"(b0));
-}
+using mma::smem_u32;
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -192,15 +171,15 @@ __device__ __forceinline__ void contract(uint32_t base, int warp, int lane, cons
 #pragma unroll
     for (int q = 0; q < kS; q += 2) {
         if (DIR == 0)
-            ldsm4(addr + q * kSlice, a[q][0], a[q][1], a[q + 1][0], a[q + 1][1]);
+            mma::ldsm_x4(addr + q * kSlice, a[q][0], a[q][1], a[q + 1][0], a[q + 1][1]);
         else
-            ldsm4t(addr + q * kSlice, a[q][0], a[q][1], a[q + 1][0], a[q + 1][1]);
+            mma::ldsm_x4_t(addr + q * kSlice, a[q][0], a[q][1], a[q + 1][0], a[q + 1][1]);
     }
 #pragma unroll
     for (int l = 0; l < 6; ++l) acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = 0.0f;
     // level index L - 2 = p + q for D digit p and operand digit q (0-based)
-#define OZ_K8(L, p, q) mma8(acc[L], a[q][0], a[q][1], Bf[p])
-#define OZ_K16(L, p1, q1, p2, q2) mma16(acc[L], a[q1][0], a[q1][1], a[q2][0], a[q2][1], Bf[p1], Bf[p2])
+#define OZ_K8(L, p, q) mma::bf16_1688(acc[L], a[q][0], a[q][1], Bf[p])
+#define OZ_K16(L, p1, q1, p2, q2) mma::bf16_16816(acc[L], a[q1][0], a[q1][1], a[q2][0], a[q2][1], Bf[p1], Bf[p2])
     OZ_K8(0, 0, 0);
     OZ_K16(1, 0, 1, 1, 0);
     OZ_K16(2, 0, 2, 1, 1);
