@@ -89,13 +89,13 @@ __device__ __forceinline__ df acc_sub(acc2 a, acc2 b) { return acc_add(a, acc2{-
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(k + 127) << 23); }
 
 // x * 2^-sh split into hi + lo by bit operations (no FP64 instruction).
-// Values whose scaled magnitude is below the float range flush to zero;
-// Inf and NaN pass through (as hi) so that they propagate like in FP64.
+// Values whose scaled magnitude is below the float range flush to zero.
+// Inf and NaN are not representable here (they come out finite): the tile
+// recognises their element by its exponent maximum (0x7ff) and writes NaN.
 __device__ __forceinline__ df split_double(double x, int sh) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
     const int eb = (int)((hi32 >> 20) & 0x7ffu);
-    if (eb == 0x7ff) return {__double2float_rn(x), 0.f};    // Inf and NaN propagate
     const int ef = eb - sh - 1023 + 127;             // biased float exponent of hi
     if (eb == 0 || ef < 1) return {0.f, 0.f};
     const unsigned sign = hi32 & 0x80000000u;
@@ -265,7 +265,7 @@ __device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__rest
     int ok = 1;
     for (int q = threadIdx.x; q < n2; q += blockDim.x) {
         const int i = q / n, l = q - (q / n) * n;
-        if (sD[q] != -sD[(n - 1 - i) * n + (n - 1 - l)]) ok = 0;
+        if (sD[q] != -sD[(n - 1 - i) * n + (n - 1 - l)] || biased_exponent(sD[q]) == 0x7ff) ok = 0;
     }
     if (!__syncthreads_and(ok)) {
         // D is not centro-antisymmetric: the FP64 node phases on a dense copy
@@ -358,6 +358,10 @@ __device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__rest
         const int e = f / n3, r = f - e * n3;
         const int k = r / n2, j = (r / n) % n, i = r % n;
         const int s = e * EP + k * PP + j * RP + i;
+        if (sexp[e] == 0x7ff || sexp[epb + e] == 0x7ff) {   // Inf or NaN in u or in G: the element is NaN
+            we[f] = __longlong_as_double(0x7ff8000000000000ll);
+            continue;
+        }
         const df acc = add(add(sr[s], ss[s]), su[s]);
         const int su_e = sexp[e] > 0 ? sexp[e] : 1, sw_e = sexp[epb + e] > 0 ? sexp[epb + e] : 1;
         double dh, dl;
