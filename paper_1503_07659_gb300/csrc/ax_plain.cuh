@@ -34,9 +34,11 @@ inline TileConfig default_tile(int n) {
 }
 
 // Registers are capped for three resident CTAs per SM wherever three tiles
-// fit in shared memory: FP64 up to n = 8, FP32 up to n = 16.
+// fit in shared memory: FP64 up to n = 8, FP32 at n > 12.  FP32 up to n = 12
+// takes 64 registers (four CTAs of 256 threads, or more of 64), measured 6-8 %
+// faster than 80; at n = 16 three CTAs with 80 registers are faster.
 template <typename T, int n, int MAP, bool HELM>
-__global__ void __launch_bounds__(256, (n <= 8 || sizeof(T) == 4 ? 3 : 1))
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (n <= 12 ? 4 : 3) : (n <= 8 ? 3 : 1)))
 ax_plain_kernel(int64_t E, int epb, const T *__restrict__ u, const T *__restrict__ G,
                 const T *__restrict__ D, T *__restrict__ w, const T *__restrict__ scale, Helm<T> helm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
