@@ -18,8 +18,8 @@
 //
 // Per element (one CTA of 4 warps; warp w owns the planes k = 2w, 2w+1 for
 // every pointwise step, in the layout of the m16n8 accumulator of the
-// r-direction tile; u and G of the CTA's next element are fetched with
-// cp.async into shared memory while the current one finishes):
+// r-direction tile; u and G of the CTA's next element are fetched by TMA
+// bulk copies into shared memory while the current one finishes):
 //   A  u (FP64) -> per-element scale -> 6 BF16 digit planes in shared memory;
 //   B  ur, us, ut on tensor cores (B operand: the digits of D^T, held in
 //      registers for the CTA's lifetime); ur stays in registers, us and ut
@@ -51,7 +51,7 @@ constexpr int kDigBytes = 3 * kS * kSlice;   // digits of wr, ws, wt (u reuses t
 constexpr int kBufBytes = 512 * 8;           // one double-float per node
 constexpr int kGBytes = 6 * 512 * 8;         // one element's G (FP64), staged
 constexpr int kUBytes = 512 * 8;             // one element's u (FP64), staged
-constexpr size_t kSmem = kDigBytes + 2 * kBufBytes + kGBytes + kUBytes + 16 * sizeof(int);
+constexpr size_t kSmem = kDigBytes + 2 * kBufBytes + kGBytes + kUBytes + 16 * sizeof(int);   // + mbarrier in the last 8 of them
 
 // Byte offset of row j of plane p inside a digit slice: the 16-byte rows of
 // a plane are permuted by p, so that ldmatrix over the 8 rows of a plane
@@ -61,8 +61,30 @@ constexpr int kBadExp = 1 << 20;             // marks a non-finite input in the 
 
 using mma::smem_u32;
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+// TMA bulk copy global -> shared, completing on an mbarrier transaction
+// count; the CTA is its own cluster, so its shared::cta address is valid.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, unsigned bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Wait for phase `parity` of the mbarrier, giving up after a bounded number
+// of polls (each try_wait may itself suspend briefly): false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
 __device__ __forceinline__ int bexp(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
@@ -267,26 +289,24 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
     const double2 *gst = reinterpret_cast<const double2 *>(bt + 512);   // staged G [6][256 node pairs]
     const double2 *ust = gst + 6 * 256;                            // staged u [256 node pairs]
     int *sred = reinterpret_cast<int *>(smem + kDigBytes + 2 * kBufBytes + kGBytes + kUBytes);   // [0, 4) u, [4, 8) y exponents
+    const uint32_t bar = smem_u32(sred + 8);                      // mbarrier of the staged u and G (8-byte aligned)
     const uint32_t dig_s = smem_u32(dig), gst_s = smem_u32(gst), ust_s = smem_u32(ust);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
 
-    // Every thread stages, and later reads back, only its own 16-byte chunks
-    // of u and G (its node pairs (k = 2w + h, j = g, i = 2t, 2t + 1)), so the
-    // staging buffers need no barrier: element e + gridDim.x is fetched while
-    // element e finishes.
+    // u_e and G_e are contiguous (4 KB, 24 KB) and staged in their global
+    // layout by two TMA bulk copies, issued by one thread for element
+    // e + gridDim.x once every thread has read element e's G; each element
+    // completes one phase of the mbarrier.
     auto prefetch = [&](int64_t ep) {
-        const double *ue = u + ep * 512, *Ge = G + ep * 3072;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int pr = (2 * warp + h) * 32 + g * 4 + t;   // node pair
-            cp_async16(ust_s + 16 * pr, ue + 2 * pr);
-#pragma unroll
-            for (int a = 0; a < 6; ++a) cp_async16(gst_s + 16 * (a * 256 + pr), Ge + a * 512 + 2 * pr);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads before async writes
+        mbar_expect_tx(bar, kUBytes + kGBytes);
+        bulk_g2s(ust_s, u + ep * 512, kUBytes, bar);
+        bulk_g2s(gst_s, G + ep * 3072, kGBytes, bar);
     };
-    if (blockIdx.x < E) prefetch(blockIdx.x);
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (tid == 0) prefetch(blockIdx.x);
 
     // D digits, once per CTA: B fragments of D^T (gradient) and D (transposed)
     int eD = 1;
@@ -305,11 +325,12 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         for (int p = 0; p < kS; ++p) ft[p] = pack_bf16(x0[p], x1[p]);
     }
 
-    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    unsigned parity = 0;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x, parity ^= 1u) {
         double *we = w + e * 512;
 
         // ---- A: u -> digits (thread's nodes: k = 2w + h, j = g, i = 2t + c)
-        asm volatile("cp.async.wait_all;" ::: "memory");
+        const bool timed_out = !mbar_wait(bar, parity);
         double2 uv[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) uv[h] = ust[(2 * warp + h) * 32 + g * 4 + t];
@@ -318,7 +339,14 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         for (int h = 0; h < 2; ++h) ex = max(ex, max(bexp(uv[h].x), bexp(uv[h].y)));
         ex = __reduce_max_sync(0xffffffffu, ex);
         if (lane == 0) sred[warp] = ex;
-        __syncthreads();
+        if (__syncthreads_or(timed_out)) {
+            // the staged data never arrived: mark this CTA's remaining outputs
+            // NaN and leave (the decision is the same in every thread)
+            for (int64_t r = e; r < E; r += gridDim.x)
+                for (int q = tid; q < 512; q += kThreads) w[r * 512 + q] = __longlong_as_double(0x7ff8000000000000ll);
+            mbar_wait(bar, parity);   // one more bounded wait for the copies in flight
+            return;
+        }
         const int eU = max4(sred);
         // u 2^-(eU - 1023) in (-2, 2) split hi + lo (47 bits), normalised; its
         // digits at t = 128 u 2^-(eU - 1023) = 256 u 2^-(eU - 1022)
@@ -404,10 +432,10 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 if (eg == 0x7ff) tmax = kBadExp;
             }
         }
-        if (e + gridDim.x < E) prefetch(e + gridDim.x);   // this thread's staged u and G are consumed
         tmax = __reduce_max_sync(0xffffffffu, tmax);
         if (lane == 0) sred[4 + warp] = tmax;
         __syncthreads();
+        if (tid == 0 && e + gridDim.x < E) prefetch(e + gridDim.x);   // every thread has read this element's G
         const int eWraw = max4(sred + 4);
         const bool bad = eU == 0x7ff || eD == 0x7ff || eWraw >= kBadExp;
         const int eW = eWraw == INT_MIN ? 0 : min(eWraw, kBadExp);   // y == 0 everywhere: any scale
