@@ -1,0 +1,117 @@
+"""CPU check of the exact digit-slicing method behind the tensor-core
+FP64-accurate form, independent of the GPU and of its arithmetic order.
+
+The method, in exact arithmetic: each operand of a contraction (u, D, and
+the intermediate [wr ws wt] = G grad u) is rounded to six balanced base-256
+digits against one power-of-two scale per element (D: one for the matrix),
+the digit products of levels p + q <= 7 are summed exactly, and the levels
+are combined.  This test evaluates that model in float64 (rounding each
+operand at 2^-48 of its scale and dropping the levels above 7, which is
+what the digits represent) and compares it with the FP64 oracle: the
+model's error is the method's own error floor, which the GPU parity tests'
+bound (2e-13 of ||w||_inf) must exceed.  Five digits per operand must miss
+the FP64 requirement, so the sixth is needed.
+"""
+import numpy as np
+import pytest
+
+import sem_inputs as si
+
+
+def _scale(x, axis=None):
+    """Smallest power of two strictly above max |x| (over axis)."""
+    m = np.max(np.abs(x), axis=axis, keepdims=axis is not None)
+    m = np.where(m > 0, m, 1.0)
+    return 2.0 ** (np.floor(np.log2(m)) + 1)
+
+
+def _expand(x, s, ndig):
+    """The ndig balanced base-256 digits of x / s as integer-valued arrays."""
+    M = np.round(x / s * 2.0 ** (8 * ndig)).astype(np.int64)
+    d = []
+    for _ in range(ndig - 1):
+        lo = ((M + 128) & 255) - 128
+        d.append(lo)
+        M = (M - lo) >> 8
+    d.append(M)
+    return d[::-1]   # most significant first
+
+
+def _contract(Dd, sD, ud, su, ndig, path):
+    """sum_l D[.,l] u[..l..] from digit expansions with levels p + q <= ndig + 1."""
+    out = 0.0
+    for p in range(ndig):
+        for q in range(ndig):
+            if p + q > ndig - 1:
+                continue
+            out = out + np.einsum(path, Dd[p].astype(np.float64), ud[q].astype(np.float64)) * 2.0 ** (-8 * (p + q + 2))
+    return out * sD * su
+
+
+def _slice_ax(u, G, D, ndig):
+    E = u.shape[0]
+    sD = float(_scale(D))
+    Dd = _expand(D, sD, ndig)
+    su = _scale(u.reshape(E, -1), axis=1).reshape(E, 1, 1, 1)
+    ud = _expand(u, su, ndig)
+    ur = _contract(Dd, sD, ud, su, ndig, "il,ekjl->ekji")
+    us = _contract(Dd, sD, ud, su, ndig, "jl,ekli->ekji")
+    ut = _contract(Dd, sD, ud, su, ndig, "kl,elji->ekji")
+    g = [G[:, a] for a in range(6)]
+    wr = g[0] * ur + g[1] * us + g[2] * ut
+    ws = g[1] * ur + g[3] * us + g[4] * ut
+    wt = g[2] * ur + g[4] * us + g[5] * ut
+    sw = np.maximum(np.maximum(_scale(wr.reshape(E, -1), axis=1), _scale(ws.reshape(E, -1), axis=1)),
+                    _scale(wt.reshape(E, -1), axis=1)).reshape(E, 1, 1, 1)
+    xr, xs, xt = (_expand(a, sw, ndig) for a in (wr, ws, wt))
+    return (_contract(Dd, sD, xr, sw, ndig, "li,ekjl->ekji") + _contract(Dd, sD, xs, sw, ndig, "lj,ekli->ekji")
+            + _contract(Dd, sD, xt, sw, ndig, "lk,elji->ekji"))
+
+
+def _rel(w, ref):
+    return float(np.max(np.abs(w - ref)) / np.max(np.abs(ref)))
+
+
+@pytest.fixture(scope="module")
+def mesh():
+    return si.make_mesh(np.random.default_rng(90), 12, 7)
+
+
+def test_digit_expansion_is_balanced_and_exact(mesh):
+    u = mesh.u.numpy()
+    s = _scale(u)
+    d = _expand(u, s, 6)
+    assert np.abs(d[0]).max() <= 256
+    assert all(np.abs(x).max() <= 128 for x in d[1:])
+    val = sum(x.astype(np.float64) * 2.0 ** (-8 * (k + 1)) for k, x in enumerate(d)) * s
+    assert np.max(np.abs(val - u)) <= 2.0 ** -49 * s
+
+
+def test_level_sums_fit_the_fp32_significand(mesh):
+    """Every level of a K = 8 contraction sums at most six digit pairs of
+    magnitude <= 256 x 256: below 2^22, so FP32 accumulation is exact."""
+    D = mesh.D.numpy()
+    u = mesh.u.numpy()
+    Dd, ud = _expand(D, float(_scale(D)), 6), _expand(u, _scale(u), 6)
+    for L in range(6):
+        acc = 0
+        for p in range(L + 1):
+            acc = acc + np.abs(np.einsum("il,ekjl->ekji", np.abs(Dd[p]), np.abs(ud[L - p])))
+        assert acc.max() < 2 ** 22
+
+
+def test_six_digits_meet_the_fp64_bound_and_five_do_not(oracle_mod, mesh):
+    u, G, D = mesh.u.numpy(), mesh.G.numpy(), mesh.D.numpy()
+    ref = oracle_mod.sem_ax(u, G, D)
+    e6 = _rel(_slice_ax(u, G, D, 6), ref)
+    e5 = _rel(_slice_ax(u, G, D, 5), ref)
+    assert e6 <= 2e-13          # the GPU tests' typical bound sits above the method's floor
+    assert e5 > 1e-12           # one digit fewer misses the FP64 requirement
+
+
+def test_constant_field_floor(oracle_mod, mesh):
+    """A 1 = 0 up to the six-digit truncation of D's rows (~1e-13 of ||A u||)."""
+    u1 = np.full(mesh.u.shape, 3.25)
+    w1 = _slice_ax(u1, mesh.G.numpy(), mesh.D.numpy(), 6)
+    wr = oracle_mod.sem_ax(mesh.u.numpy(), mesh.G.numpy(), mesh.D.numpy())
+    assert np.max(np.abs(w1)) <= 1e-12 * np.max(np.abs(wr))
