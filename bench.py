@@ -326,7 +326,9 @@ def variants(semax, reps: int) -> dict:
     b = (B * 3 * torch.pi ** 2 * ue).contiguous()
     gs(b, mask=True)
     for name, kw in (("pcg_jacobi_N7_16x16x16", {}), ("pcg_jacobi_f64x_N7_16x16x16", {"f64x": True}),
-                     ("pcg_jacobi_f64tc_N7_16x16x16", {"f64tc": True})):
+                     ("pcg_jacobi_f64tc_N7_16x16x16", {"f64tc": True}),
+                     ("pcg_jacobi_mixed_N7_16x16x16", {"mixed": True}),
+                     ("pcg_jacobi_mixed_f64tc_N7_16x16x16", {"mixed": True, "f64tc": True})):
         pcg = semax.PCG(G, D, gs, **kw)
         x = torch.zeros_like(b)
         pcg.solve(b, x, max_iter=20, rtol=0.0)              # warm-up (captures the graph)

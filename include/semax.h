@@ -227,7 +227,16 @@ int sem_ax_diag(int64_t E, int N, const double *G, const double *D, double *diag
  * masked.  Create allocates the work vectors and computes the preconditioner;
  * G, D and gs stay bound to the solver; flags = 0 applies A with the FP64
  * kernel of sem_ax, SEMAX_PCG_F64X with that of sem_ax_f64x, SEMAX_PCG_F64TC
- * with that of sem_ax_f64tc (at most one of the two flags).  Solve starts from x (in/out) and
+ * with that of sem_ax_f64tc (at most one of the two flags).  SEMAX_PCG_MIXED
+ * (combinable with either) is mixed-precision iterative refinement: each
+ * outer step computes the true residual r = b - A x with the FP64-accurate
+ * operator, solves A d = r from d = 0 by PCG whose recurrences are FP64 but
+ * whose A is the FP32 kernel (FP32 copies of G and D made at create; the
+ * search direction converted to FP32 and the product back), to a relative
+ * reduction max(1e-5, rtol / 2 / current residual), and adds d to x.  The
+ * reported residual is the true one; the solve also stops when an outer
+ * step fails to halve it (the FP64-accurate operator's own floor); iters
+ * counts the inner iterations.  Solve starts from x (in/out) and
  * stops when ||r|| <= rtol ||r_0|| (norms weighted by 1/multiplicity) or after
  * max_iter iterations, checked every 10 iterations: a block of 10 iterations
  * is one CUDA-graph launch with all scalars in device memory.  Solve blocks
@@ -235,7 +244,8 @@ int sem_ax_diag(int64_t E, int N, const double *G, const double *D, double *diag
  * later work on `stream` is ordered after it. */
 typedef struct semax_pcg semax_pcg;
 enum { SEMAX_PCG_F64X = 1,     /* apply A with sem_ax_f64x (double-float, FP64-accurate) */
-       SEMAX_PCG_F64TC = 2 };   /* apply A with sem_ax_f64tc (tensor-core digit slicing, FP64-accurate) */
+       SEMAX_PCG_F64TC = 2,     /* apply A with sem_ax_f64tc (tensor-core digit slicing, FP64-accurate) */
+       SEMAX_PCG_MIXED = 4 };   /* FP32 operator inside, FP64 residuals outside (iterative refinement) */
 int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G, const double *D, const semax_gs *gs,
                    int flags);
 int sem_pcg_solve(semax_pcg *pcg, const double *b, double *x, int max_iter, double rtol, int *iters,

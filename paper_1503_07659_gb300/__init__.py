@@ -238,10 +238,10 @@ class PCG:
     """Jacobi-PCG on Q A_L Q^T (sem_pcg_*); G, D and the gather-scatter stay bound."""
 
     def __init__(self, G: torch.Tensor, D: torch.Tensor, gs: GatherScatter, f64x: bool = False,
-                 f64tc: bool = False):
+                 f64tc: bool = False, mixed: bool = False):
         self._keep = (G, D, gs)
         self._handle = ctypes.c_void_p()
-        flags = (1 if f64x else 0) | (2 if f64tc else 0)
+        flags = (1 if f64x else 0) | (2 if f64tc else 0) | (4 if mixed else 0)
         check(_lib.lib().sem_pcg_create(ctypes.byref(self._handle), G.shape[0], D.shape[0] - 1, _ptr(G), _ptr(D),
                                         gs._handle, flags), "sem_pcg_create")
 

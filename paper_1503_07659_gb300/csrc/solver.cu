@@ -108,7 +108,7 @@ dot_kernel(int64_t count, const double *__restrict__ a, const double *__restrict
 }
 
 // What to do with the two sums of the partials.
-enum { FIN_PAP = 0, FIN_RZ_RR = 1, FIN_INIT = 2 };
+enum { FIN_PAP = 0, FIN_RZ_RR = 1, FIN_INIT = 2, FIN_REPLACE = 3 };
 
 __global__ void __launch_bounds__(kSolverThreads)
 final_kernel(int nparts, const double *__restrict__ part, double *__restrict__ scal, int mode) {
@@ -126,6 +126,9 @@ final_kernel(int nparts, const double *__restrict__ part, double *__restrict__ s
             scal[S_ALPHA] = a != 0.0 ? scal[S_RZ] / a : 0.0;
         } else if (mode == FIN_RZ_RR) {
             scal[S_BETA] = scal[S_RZ] != 0.0 ? a / scal[S_RZ] : 0.0;
+            scal[S_RZ] = a;
+            scal[S_RR] = b;
+        } else if (mode == FIN_REPLACE) {   // residual replacement: r.z and r.r of the true residual
             scal[S_RZ] = a;
             scal[S_RR] = b;
         } else {
@@ -176,6 +179,25 @@ residual_kernel(int64_t count, const double *__restrict__ b, const double *__res
         r[q] = rq;
         z[q] = invdiag[q] * rq;
     }
+}
+
+// precision conversions of the mixed-precision operator
+__global__ void __launch_bounds__(kSolverThreads)
+to_f32_kernel(int64_t count, const double *__restrict__ a, float *__restrict__ b) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride) b[q] = (float)a[q];
+}
+__global__ void __launch_bounds__(kSolverThreads)
+to_f64_kernel(int64_t count, const float *__restrict__ a, double *__restrict__ b) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride) b[q] = (double)a[q];
+}
+
+// x += d
+__global__ void __launch_bounds__(kSolverThreads)
+axpy1_kernel(int64_t count, double *__restrict__ x, const double *__restrict__ d) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride) x[q] += d[q];
 }
 
 // invdiag = free ? 1 / d : 0 (d already summed; Dirichlet nodes were zeroed)
@@ -304,6 +326,8 @@ struct semax_pcg {
     const semax_gs *gs = nullptr;
     double *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *invdiag = nullptr;
     double *part = nullptr, *scal = nullptr;
+    float *G32 = nullptr, *D32 = nullptr, *p32 = nullptr, *w32 = nullptr;   // SEMAX_PCG_MIXED
+    double *d = nullptr;                                                   // its correction vector
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -313,12 +337,27 @@ struct semax_pcg {
 };
 
 
-// w = A_L v with the operator the solver was created with
-static int pcg_apply_a(semax_pcg *s, const double *v, double *w, cudaStream_t cs) {
+// w = A_L v, FP64-accurate, with the operator the solver was created with
+static int pcg_apply_a64(semax_pcg *s, const double *v, double *w, cudaStream_t cs) {
     if (s->flags & SEMAX_PCG_F64X) return sem_ax_f64x(s->E, s->N, v, s->G, s->D, w, cs);
     if (s->flags & SEMAX_PCG_F64TC) return sem_ax_f64tc(s->E, s->N, v, s->G, s->D, w, cs);
     return launch_plain<double>(s->E, s->N, default_tile<double>(s->N + 1), v, s->G, s->D, w, nullptr,
                                 Helm<double>{nullptr, 1.0, 0.0}, cs);
+}
+
+// w = A_L v for the iterations: the FP64-accurate operator, or with
+// SEMAX_PCG_MIXED the FP32 kernel on FP32 copies of v, G and D
+static int pcg_apply_a(semax_pcg *s, const double *v, double *w, cudaStream_t cs) {
+    if (!(s->flags & SEMAX_PCG_MIXED)) return pcg_apply_a64(s, v, w, cs);
+    const int blocks = solver_blocks(s->count);
+    to_f32_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, v, s->p32);
+    int st = launch_status();
+    if (st == SEMAX_OK)
+        st = launch_plain<float>(s->E, s->N, default_tile<float>(s->N + 1), s->p32, s->G32, s->D32, s->w32,
+                                 nullptr, Helm<float>{nullptr, 1.0f, 0.0f}, cs);
+    if (st != SEMAX_OK) return st;
+    to_f64_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->w32, w);
+    return launch_status();
 }
 
 static const int kItersPerGraph = 10;
@@ -335,6 +374,11 @@ static void pcg_free(semax_pcg *s) {
     cudaFree(s->invdiag);
     cudaFree(s->part);
     cudaFree(s->scal);
+    cudaFree(s->G32);
+    cudaFree(s->D32);
+    cudaFree(s->p32);
+    cudaFree(s->w32);
+    cudaFree(s->d);
     s->magic = 0;
     delete s;
 }
@@ -358,8 +402,9 @@ extern "C" int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G
                               const semax_gs *gs, int flags) {
     if (!pcg) return SEMAX_EINVAL;
     *pcg = nullptr;
-    if (E <= 0 || !G || !D || !gs || gs->magic != 0x95u || (flags & ~(SEMAX_PCG_F64X | SEMAX_PCG_F64TC)) ||
-        flags == (SEMAX_PCG_F64X | SEMAX_PCG_F64TC))
+    if (E <= 0 || !G || !D || !gs || gs->magic != 0x95u ||
+        (flags & ~(SEMAX_PCG_F64X | SEMAX_PCG_F64TC | SEMAX_PCG_MIXED)) ||
+        (flags & (SEMAX_PCG_F64X | SEMAX_PCG_F64TC)) == (SEMAX_PCG_F64X | SEMAX_PCG_F64TC))
         return SEMAX_EINVAL;
     if (N < 1 || N > kMaxN) return SEMAX_EUNSUPPORTED_N;
     const int64_t count = E * (N + 1) * (N + 1) * (N + 1);
@@ -379,6 +424,19 @@ extern "C" int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G
     if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->part, sizeof(double) * 2 * kSolverMaxBlocks));
     if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->scal, sizeof(double) * S_COUNT));
     if (st == SEMAX_OK) st = cuda_status(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
+    if (st == SEMAX_OK && (flags & SEMAX_PCG_MIXED)) {
+        const int64_t nn = (int64_t)(N + 1) * (N + 1);
+        for (float **v : {&s->p32, &s->w32})
+            if (st == SEMAX_OK) st = cuda_status(cudaMalloc(v, sizeof(float) * (size_t)count));
+        if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->G32, sizeof(float) * 6 * (size_t)count));
+        if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->D32, sizeof(float) * (size_t)nn));
+        if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->d, sizeof(double) * (size_t)count));
+        if (st == SEMAX_OK) {
+            to_f32_kernel<<<solver_blocks(6 * count), kSolverThreads, 0, s->cs>>>(6 * count, G, s->G32);
+            to_f32_kernel<<<1, kSolverThreads, 0, s->cs>>>(nn, D, s->D32);
+            st = launch_status();
+        }
+    }
     // Jacobi: invdiag = 1 / (Q Q^T diag(A_L)) at free nodes, 0 at Dirichlet nodes
     if (st == SEMAX_OK) st = launch_diag_N(E, N, G, D, s->invdiag, s->cs);
     if (st == SEMAX_OK) st = gs_enqueue(gs, s->invdiag, 1, s->cs);
@@ -408,19 +466,24 @@ extern "C" int sem_pcg_solve(semax_pcg *s, const double *b, double *x, int max_i
     if (st != SEMAX_OK) return st;
     st = cuda_status(cudaEventRecord(ev, us));
     if (st == SEMAX_OK) st = cuda_status(cudaStreamWaitEvent(cs, ev, 0));
-    // initial residual
     const int blocks = solver_blocks(s->count);
-    if (st == SEMAX_OK) st = pcg_apply_a(s, x, s->w, cs);
-    if (st == SEMAX_OK) st = gs_enqueue(s->gs, s->w, 1, cs);
-    if (st == SEMAX_OK) {
-        residual_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, b, s->w, s->invdiag, s->r, s->z);
-        dot_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->r, s->z, s->r, s->gs->inv_mult, s->part);
-        final_kernel<<<1, kSolverThreads, 0, cs>>>(blocks, s->part, s->scal, FIN_INIT);
-        pupdate_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->z, s->scal, 0);
-        st = launch_status();
-    }
-    // (re)capture a block of iterations bound to this x
-    if (st == SEMAX_OK && s->x_bound != x) {
+    const bool mixed = (s->flags & SEMAX_PCG_MIXED) != 0;
+    double *xi = mixed ? s->d : x;   // the vector the iterations update (the graph is bound to it)
+    // r = b - A v (FP64-accurate operator), z = M r, p = z, and the scalars of a fresh start
+    auto restart = [&](const double *v) {
+        int rs = pcg_apply_a64(s, v, s->w, cs);
+        if (rs == SEMAX_OK) rs = gs_enqueue(s->gs, s->w, 1, cs);
+        if (rs == SEMAX_OK) {
+            residual_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, b, s->w, s->invdiag, s->r, s->z);
+            dot_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->r, s->z, s->r, s->gs->inv_mult, s->part);
+            final_kernel<<<1, kSolverThreads, 0, cs>>>(blocks, s->part, s->scal, FIN_INIT);
+            pupdate_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->z, s->scal, 0);
+            rs = launch_status();
+        }
+        return rs;
+    };
+    // (re)capture a block of iterations bound to xi
+    if (st == SEMAX_OK && s->x_bound != xi) {
         if (s->exec) { cudaGraphExecDestroy(s->exec); s->exec = nullptr; }
         if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
         cudaStream_t cap = nullptr;
@@ -428,32 +491,76 @@ extern "C" int sem_pcg_solve(semax_pcg *s, const double *b, double *x, int max_i
         if (st == SEMAX_OK) st = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
         if (st == SEMAX_OK) {
             int lst = SEMAX_OK;
-            for (int it = 0; it < kItersPerGraph && lst == SEMAX_OK; ++it) lst = pcg_iteration(s, x, cap);
+            for (int it = 0; it < kItersPerGraph && lst == SEMAX_OK; ++it) lst = pcg_iteration(s, xi, cap);
             int est = cuda_status(cudaStreamEndCapture(cap, &s->graph));
             st = lst != SEMAX_OK ? lst : est;
         }
         if (st == SEMAX_OK) st = cuda_status(cudaGraphInstantiate(&s->exec, s->graph, 0));
         if (cap) cudaStreamDestroy(cap);
-        s->x_bound = st == SEMAX_OK ? x : nullptr;
+        s->x_bound = st == SEMAX_OK ? xi : nullptr;
     }
     double h[S_COUNT] = {0};
-    if (st == SEMAX_OK) st = cuda_status(cudaMemcpyAsync(h, s->scal, sizeof h, cudaMemcpyDeviceToHost, cs));
-    if (st == SEMAX_OK) st = cuda_status(cudaStreamSynchronize(cs));
-    const double rr0 = h[S_RR0];
+    auto read_scalars = [&]() {
+        int rs = cuda_status(cudaMemcpyAsync(h, s->scal, sizeof h, cudaMemcpyDeviceToHost, cs));
+        return rs == SEMAX_OK ? cuda_status(cudaStreamSynchronize(cs)) : rs;
+    };
+    // iterate on xi until its recurrence residual falls to `target` of its start
     int done = 0;
-    double rel = rr0 > 0.0 ? 1.0 : 0.0;
-    while (st == SEMAX_OK && done < max_iter && rel > rtol) {
-        const int left = max_iter - done;
-        if (left >= kItersPerGraph) {
-            st = cuda_status(cudaGraphLaunch(s->exec, cs));
-            done += kItersPerGraph;
-        } else {
-            for (int it = 0; it < left && st == SEMAX_OK; ++it) st = pcg_iteration(s, x, cs);
-            done += left;
+    bool broke_down = false;   // the recurrence produced NaN
+    auto iterate = [&](double target) {
+        int rs = SEMAX_OK;
+        double r = 1.0;
+        while (rs == SEMAX_OK && done < max_iter && r > target) {
+            const int left = max_iter - done;
+            if (left >= kItersPerGraph) {
+                rs = cuda_status(cudaGraphLaunch(s->exec, cs));
+                done += kItersPerGraph;
+            } else {
+                for (int it = 0; it < left && rs == SEMAX_OK; ++it) rs = pcg_iteration(s, xi, cs);
+                done += left;
+            }
+            if (rs == SEMAX_OK) rs = read_scalars();
+            r = h[S_RR0] > 0.0 ? std::sqrt(std::max(h[S_RR], 0.0) / h[S_RR0]) : 0.0;
+            if (!(r == r)) {   // NaN: stop
+                broke_down = true;
+                break;
+            }
         }
-        if (st == SEMAX_OK) st = cuda_status(cudaMemcpyAsync(h, s->scal, sizeof h, cudaMemcpyDeviceToHost, cs));
-        if (st == SEMAX_OK) st = cuda_status(cudaStreamSynchronize(cs));
-        rel = rr0 > 0.0 ? std::sqrt(std::max(h[S_RR], 0.0) / rr0) : 0.0;
+        return rs;
+    };
+    double rel = 1.0;
+    if (st == SEMAX_OK) st = restart(x);
+    if (st == SEMAX_OK) st = read_scalars();
+    const double rr0 = h[S_RR0];
+    if (!mixed) {
+        rel = rr0 > 0.0 ? 1.0 : 0.0;
+        if (st == SEMAX_OK && rel > rtol) st = iterate(rtol);
+        if (rel > 0.0) rel = std::sqrt(std::max(h[S_RR], 0.0) / rr0);
+    } else {
+        // Mixed-precision iterative refinement: each outer step takes the true
+        // residual with the FP64-accurate operator, solves A d = r from d = 0
+        // with the FP32 operator inside the FP64 iteration to a relative
+        // reduction eta, and adds d to x.  Restarting keeps the FP32
+        // operator's error relative to the current residual.
+        // Stops when an outer step fails to halve the true residual: the
+        // FP64-accurate operator's own error then sets the floor.
+        const int64_t vbytes = (int64_t)sizeof(double) * s->count;
+        double prev = 2.0;
+        for (;;) {
+            rel = rr0 > 0.0 ? std::sqrt(std::max(h[S_RR0], 0.0) / rr0) : 0.0;
+            if (st != SEMAX_OK || !(rel > rtol) || done >= max_iter || rel > 0.5 * prev) break;
+            prev = rel;
+            const double eta = std::min(0.5, std::max(1e-5, 0.5 * rtol / rel));
+            st = cuda_status(cudaMemsetAsync(s->d, 0, (size_t)vbytes, cs));
+            if (st == SEMAX_OK) st = iterate(eta);
+            if (broke_down) break;   // x keeps the last refined iterate
+            if (st == SEMAX_OK) {
+                axpy1_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, x, s->d);
+                st = launch_status();
+            }
+            if (st == SEMAX_OK) st = restart(x);
+            if (st == SEMAX_OK) st = read_scalars();
+        }
     }
     // the caller's stream continues after the solve
     if (st == SEMAX_OK) st = cuda_status(cudaEventRecord(ev, cs));

@@ -132,3 +132,43 @@ def test_pcg_manufactured_solution_spectral_accuracy(semax, solver_oracle):
     assert np.max(np.abs(x.cpu().numpy() - ue)) < 1e-7
     pcg.close()
     gs.close()
+
+
+def test_pcg_mixed_precision_iterative_refinement(semax, solver_oracle):
+    """FP32 operator inside the FP64 iteration, refined with true FP64
+    residuals: the reported residual is the true one and the solution is the
+    FP64 solver's to 1e-10; with the tensor-core outer operator the solve
+    reaches 1e-10 and stops on its own at that operator's residual floor."""
+    m, G, B, D, ue, mask = _setup((3, 3, 3), 7, 6)
+    b = mask * solver_oracle.gather_scatter(B.numpy() * 3 * np.pi ** 2 * ue, m.l2g, m.nglobal)
+    gs = semax.GatherScatter(m.l2g, m.nglobal, m.boundary)
+    bd = torch.from_numpy(b).cuda()
+    Gd, Dd = G.cuda(), D.cuda()
+    inv_mult = 1.0 / solver_oracle.multiplicity(m.l2g, m.nglobal).reshape(ue.shape)
+
+    def solve(rtol, **kw):
+        pcg = semax.PCG(Gd, Dd, gs, **kw)
+        x = torch.zeros_like(bd)
+        it, rel = pcg.solve(bd, x, max_iter=3000, rtol=rtol)
+        pcg.close()
+        return x, it, rel
+
+    def true_rel(x):   # with the FP64 operator; x0 = 0, so r0 = b
+        w = semax.sem_ax(x, Gd, Dd)
+        gs(w, mask=True)
+        r = b - w.cpu().numpy()
+        return float(np.sqrt(np.sum(r * r * inv_mult) / np.sum(b * b * inv_mult)))
+
+    x64, _, rel64 = solve(1e-12)
+    assert rel64 <= 1e-12
+    xm, itm, relm = solve(1e-12, mixed=True)
+    assert relm <= 1e-12 and itm < 3000
+    tr = true_rel(xm)
+    assert tr <= 1.1e-12 and abs(tr - relm) <= 0.05 * relm + 1e-15
+    assert np.max(np.abs(xm.cpu().numpy() - x64.cpu().numpy())) <= 1e-10 * np.max(np.abs(x64.cpu().numpy()))
+
+    xt, itt, relt = solve(1e-10, mixed=True, f64tc=True)
+    assert relt <= 1e-10 and true_rel(xt) <= 1.5e-10
+    xs, its, rels = solve(1e-15, mixed=True, f64tc=True)   # below that operator's floor
+    assert its < 3000 and rels > 1e-15                       # stops on stagnation, not at max_iter
+    gs.close()
