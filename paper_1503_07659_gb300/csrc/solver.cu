@@ -110,17 +110,8 @@ dot_kernel(int64_t count, const double *__restrict__ a, const double *__restrict
 // What to do with the two sums of the partials.
 enum { FIN_PAP = 0, FIN_RZ_RR = 1, FIN_INIT = 2, FIN_REPLACE = 3 };
 
-__global__ void __launch_bounds__(kSolverThreads)
-final_kernel(int nparts, const double *__restrict__ part, double *__restrict__ scal, int mode) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int q = threadIdx.x; q < nparts; q += blockDim.x) {
-        s0 += part[2 * q];
-        s1 += part[2 * q + 1];
-    }
-    __shared__ double out[2];
-    block_sum2(s0, s1, out);
-    if (threadIdx.x == 0) {
-        const double a = out[0], b = out[1];
+// The scalars that a mode derives from the two global sums a, b.
+__device__ __forceinline__ void apply_final(double *scal, int mode, double a, double b) {
         if (mode == FIN_PAP) {
             scal[S_PAP] = a;
             scal[S_ALPHA] = a != 0.0 ? scal[S_RZ] / a : 0.0;
@@ -135,7 +126,44 @@ final_kernel(int nparts, const double *__restrict__ part, double *__restrict__ s
             scal[S_RZ] = a;
             scal[S_RR] = b;
             scal[S_RR0] = b;
+            scal[S_BETA] = 0.0;
         }
+}
+
+__global__ void __launch_bounds__(kSolverThreads)
+final_kernel(int nparts, const double *__restrict__ part, double *__restrict__ scal, int mode) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += blockDim.x) {
+        s0 += part[2 * q];
+        s1 += part[2 * q + 1];
+    }
+    __shared__ double out[2];
+    block_sum2(s0, s1, out);
+    if (threadIdx.x == 0) apply_final(scal, mode, out[0], out[1]);
+}
+
+// The last block of a grid to finish (counted on `counter`) sums every
+// block's partials, in index order like final_kernel, applies `mode` and
+// resets the counter; each block must have written its partials before.
+__device__ __forceinline__ void finish_in_last_block(const double *part, double *scal, int mode,
+                                                     unsigned *counter) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s0 = 0.0, s1 = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+        s0 += __ldcg(part + 2 * q);
+        s1 += __ldcg(part + 2 * q + 1);
+    }
+    __shared__ double out[2];
+    block_sum2(s0, s1, out);
+    if (threadIdx.x == 0) {
+        apply_final(scal, mode, out[0], out[1]);
+        *counter = 0;
     }
 }
 
@@ -143,7 +171,8 @@ final_kernel(int nparts, const double *__restrict__ part, double *__restrict__ s
 __global__ void __launch_bounds__(kSolverThreads)
 update_kernel(int64_t count, double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
               const double *__restrict__ p, const double *__restrict__ w, const double *__restrict__ invdiag,
-              const double *__restrict__ wt, const double *__restrict__ scal, double *__restrict__ part) {
+              const double *__restrict__ wt, double *__restrict__ scal, double *__restrict__ part,
+              unsigned *__restrict__ counter) {
     const double alpha = scal[S_ALPHA];
     double s0 = 0.0, s1 = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -157,6 +186,7 @@ update_kernel(int64_t count, double *__restrict__ x, double *__restrict__ r, dou
         s1 = __fma_rn(rq * rq, wt[q], s1);
     }
     block_sum2(s0, s1, part + 2 * blockIdx.x);
+    finish_in_last_block(part, scal, FIN_RZ_RR, counter);
 }
 
 // p = z + beta p  (use_beta = 0: p = z)
@@ -178,6 +208,41 @@ residual_kernel(int64_t count, const double *__restrict__ b, const double *__res
         const double rq = b[q] - w[q];
         r[q] = rq;
         z[q] = invdiag[q] * rq;
+    }
+}
+
+// Gather-scatter of w fused with the partials of (p, w): p and w are
+// continuous after the sum (equal copies), so the weighted local sum
+// sum_l p_l w_l / mult_l is the sum over global nodes of p_g w_g.
+__global__ void __launch_bounds__(kSolverThreads)
+gs_dot_kernel(int64_t nglobal, const int64_t *__restrict__ offsets, const int64_t *__restrict__ locals,
+              const unsigned char *__restrict__ dirichlet, double *__restrict__ w, const double *__restrict__ p,
+              double *__restrict__ part, double *__restrict__ scal, unsigned *__restrict__ counter) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double acc = 0.0, unused = 0.0;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nglobal; g += stride) {
+        const int64_t q0 = offsets[g], q1 = offsets[g + 1];
+        double sum = 0.0;
+        for (int64_t q = q0; q < q1; ++q) sum += w[locals[q]];
+        if (dirichlet && dirichlet[g]) sum = 0.0;
+        for (int64_t q = q0; q < q1; ++q) w[locals[q]] = sum;
+        if (q1 > q0) acc = __fma_rn(p[locals[q0]], sum, acc);
+    }
+    block_sum2(acc, unused, part + 2 * blockIdx.x);
+    finish_in_last_block(part, scal, FIN_PAP, counter);
+}
+
+// p = z + beta p (beta from the previous iteration, 0 after a restart) and
+// its FP32 copy, for the mixed-precision operator
+__global__ void __launch_bounds__(kSolverThreads)
+pupdate_f32_kernel(int64_t count, double *__restrict__ p, const double *__restrict__ z, float *__restrict__ p32,
+                   const double *__restrict__ scal) {
+    const double beta = scal[S_BETA];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride) {
+        const double v = __fma_rn(beta, p[q], z[q]);
+        p[q] = v;
+        p32[q] = (float)v;
     }
 }
 
@@ -328,6 +393,7 @@ struct semax_pcg {
     double *part = nullptr, *scal = nullptr;
     float *G32 = nullptr, *D32 = nullptr, *p32 = nullptr, *w32 = nullptr;   // SEMAX_PCG_MIXED
     double *d = nullptr;                                                   // its correction vector
+    unsigned *counters = nullptr;                                          // last-block reductions (2)
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -343,21 +409,6 @@ static int pcg_apply_a64(semax_pcg *s, const double *v, double *w, cudaStream_t 
     if (s->flags & SEMAX_PCG_F64TC) return sem_ax_f64tc(s->E, s->N, v, s->G, s->D, w, cs);
     return launch_plain<double>(s->E, s->N, default_tile<double>(s->N + 1), v, s->G, s->D, w, nullptr,
                                 Helm<double>{nullptr, 1.0, 0.0}, cs);
-}
-
-// w = A_L v for the iterations: the FP64-accurate operator, or with
-// SEMAX_PCG_MIXED the FP32 kernel on FP32 copies of v, G and D
-static int pcg_apply_a(semax_pcg *s, const double *v, double *w, cudaStream_t cs) {
-    if (!(s->flags & SEMAX_PCG_MIXED)) return pcg_apply_a64(s, v, w, cs);
-    const int blocks = solver_blocks(s->count);
-    to_f32_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, v, s->p32);
-    int st = launch_status();
-    if (st == SEMAX_OK)
-        st = launch_plain<float>(s->E, s->N, default_tile<float>(s->N + 1), s->p32, s->G32, s->D32, s->w32,
-                                 nullptr, Helm<float>{nullptr, 1.0f, 0.0f}, cs);
-    if (st != SEMAX_OK) return st;
-    to_f64_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->w32, w);
-    return launch_status();
 }
 
 static const int kItersPerGraph = 10;
@@ -379,22 +430,39 @@ static void pcg_free(semax_pcg *s) {
     cudaFree(s->p32);
     cudaFree(s->w32);
     cudaFree(s->d);
+    cudaFree(s->counters);
     s->magic = 0;
     delete s;
 }
 
 // One PCG iteration on stream cs (x is the caller's solution vector).
+// With SEMAX_PCG_MIXED the direction update p = z + beta p is deferred to
+// the start of the next iteration, fused with its FP32 conversion.
 static int pcg_iteration(semax_pcg *s, double *x, cudaStream_t cs) {
     const int blocks = solver_blocks(s->count);
-    int st = pcg_apply_a(s, s->p, s->w, cs);
-    if (st == SEMAX_OK) st = gs_enqueue(s->gs, s->w, 1, cs);
+    const bool mixed = (s->flags & SEMAX_PCG_MIXED) != 0;
+    int st = SEMAX_OK;
+    if (mixed) {
+        pupdate_f32_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->z, s->p32, s->scal);
+        st = launch_status();
+        if (st == SEMAX_OK)
+            st = launch_plain<float>(s->E, s->N, default_tile<float>(s->N + 1), s->p32, s->G32, s->D32, s->w32,
+                                     nullptr, Helm<float>{nullptr, 1.0f, 0.0f}, cs);
+        if (st == SEMAX_OK) {
+            to_f64_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->w32, s->w);
+            st = launch_status();
+        }
+    } else {
+        st = pcg_apply_a64(s, s->p, s->w, cs);
+    }
     if (st != SEMAX_OK) return st;
-    dot_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->w, nullptr, s->gs->inv_mult, s->part);
-    final_kernel<<<1, kSolverThreads, 0, cs>>>(blocks, s->part, s->scal, FIN_PAP);
+    const semax_gs *gs = s->gs;
+    gs_dot_kernel<<<solver_blocks(gs->nglobal), kSolverThreads, 0, cs>>>(gs->nglobal, gs->offsets, gs->locals,
+                                                                          gs->dirichlet, s->w, s->p, s->part,
+                                                                          s->scal, s->counters);
     update_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, x, s->r, s->z, s->p, s->w, s->invdiag,
-                                                     s->gs->inv_mult, s->scal, s->part);
-    final_kernel<<<1, kSolverThreads, 0, cs>>>(blocks, s->part, s->scal, FIN_RZ_RR);
-    pupdate_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->z, s->scal, 1);
+                                                     s->gs->inv_mult, s->scal, s->part, s->counters + 1);
+    if (!mixed) pupdate_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->z, s->scal, 1);
     return launch_status();
 }
 
@@ -423,6 +491,8 @@ extern "C" int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G
         if (st == SEMAX_OK) st = cuda_status(cudaMalloc(v, vb));
     if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->part, sizeof(double) * 2 * kSolverMaxBlocks));
     if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->scal, sizeof(double) * S_COUNT));
+    if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->counters, 2 * sizeof(unsigned)));
+    if (st == SEMAX_OK) st = cuda_status(cudaMemset(s->counters, 0, 2 * sizeof(unsigned)));
     if (st == SEMAX_OK) st = cuda_status(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
     if (st == SEMAX_OK && (flags & SEMAX_PCG_MIXED)) {
         const int64_t nn = (int64_t)(N + 1) * (N + 1);
