@@ -159,3 +159,24 @@ def test_f64tc_preserves_inputs_and_honours_stream(semax, oracle_mod):
     s.synchronize()
     assert torch.equal(u, u0) and torch.equal(G, G0)
     assert rel_err(w, oracle_mod.sem_ax(m.u, m.G, m.D)) <= TYPICAL_TC
+
+
+def test_f64tc_max_size_offsets_past_2_31(semax, oracle_mod):
+    """E = 720000 elements of order 7 (369M nodes, 23 GB): G's element offsets
+    pass 2^31 values from e = 699051 on (e * 6 * 512).  Built by tiling a
+    64-element seeded mesh; checked against the oracle on elements on both
+    sides of that point and at the end, and against the FP64 kernel whole."""
+    base = si.make_mesh(np.random.default_rng(79), 64, 7, device="cuda")
+    E = 720000
+    G = base.G.repeat((E + 63) // 64, 1, 1, 1, 1)[:E].contiguous()
+    gen = torch.Generator(device="cuda").manual_seed(80)
+    u = torch.rand((E, 8, 8, 8), generator=gen, dtype=torch.float64, device="cuda") * 2 - 1
+    w = semax.sem_ax_f64tc(u, G, base.D)
+    torch.cuda.synchronize()
+    idx = np.array([0, 699050, 699051, 710000, E - 2, E - 1])
+    it = torch.from_numpy(idx).cuda()
+    ref = oracle_mod.sem_ax(u[it].cpu(), base.G[it.remainder(64)].cpu(), base.D.cpu())
+    assert rel_err(w[it], ref) <= TYPICAL_TC
+    w64 = semax.sem_ax(u, G, base.D)
+    r = semax.reduce(w, w64).cpu().numpy()
+    assert r[0] / r[1] <= TYPICAL_TC
