@@ -41,12 +41,13 @@ def test_strerror_covers_every_status(lib):
 A = 1 << 40
 
 
-@pytest.mark.parametrize("fn", ["sem_ax", "sem_ax_f64x", "sem_ax_f32", "sem_ax_bf16x3"])
+@pytest.mark.parametrize("fn", ["sem_ax", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f32", "sem_ax_bf16x3"])
 def test_argument_validation(lib, fn):
     f = getattr(lib, fn)
 
     def call(E, N, u=A, G=A + (1 << 32), D=A + (2 << 32), w=A + (3 << 32)):
-        extra = {"sem_ax": (), "sem_ax_f64x": (), "sem_ax_f32": (None,), "sem_ax_bf16x3": (None, 3)}[fn]
+        extra = {"sem_ax": (), "sem_ax_f64x": (), "sem_ax_f64tc": (), "sem_ax_f32": (None,),
+                 "sem_ax_bf16x3": (None, 3)}[fn]
         return f(E, N, u, G, D, w, *extra, None)
 
     assert call(0, 7) == 0                      # empty: no-op, nothing inspected
