@@ -175,6 +175,14 @@ def rel_err_gpu(semax, w, ref) -> float:
     return float(r[0] / r[1]) if r[1] > 0 else float(r[0])
 
 
+def energy_rel_gpu(semax, u, w, ref) -> float:
+    """|u.w - u.ref| / |u.ref|: the energy u^T A u of a form against the FP64
+    kernel's, both dot products in FP64 on the GPU."""
+    e = float(semax.reduce(u.reshape(-1), w.reshape(-1)).cpu().numpy()[2])
+    e0 = float(semax.reduce(u.reshape(-1), ref.reshape(-1)).cpu().numpy()[2])
+    return abs(e - e0) / abs(e0)
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -274,6 +282,7 @@ def variants(semax, reps: int) -> dict:
     dofs = m.dofs
     ref = semax.sem_ax(m.u, m.G, m.D)
     u, G, D = m.u.float(), m.G.float(), m.D.float()
+    u64 = m.u
     X = torch.from_numpy(m.X).float().cuda().contiguous()
     xq = torch.cat([torch.from_numpy(si.gll_nodes(m.N)), torch.from_numpy(si.gll_weights(m.N))]).float().cuda()
     del m
@@ -283,13 +292,15 @@ def variants(semax, reps: int) -> dict:
                      ("bf16x6", lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=6))]:
         r = rate(fn, dofs, dofs * bytes_per_node(4))
         r["rel_err_vs_f64"] = rel_err_gpu(semax, w, ref)
+        r["energy_rel_err"] = energy_rel_gpu(semax, u64, w, ref)
         out[f"{name}_N15_E8192"] = r
     # geometric factor recomputed from the vertices: 8 B/node + 96 B/element
     for name, terms in (("bf16x3_geo", 3), ("bf16x6_geo", 6)):
         r = rate(lambda: semax.sem_ax_bf16x3_geo(u, X, xq, D, w, terms=terms), dofs, dofs * 8 + 96 * (dofs // 4096))
         r["rel_err_vs_f64"] = rel_err_gpu(semax, w, ref)
+        r["energy_rel_err"] = energy_rel_gpu(semax, u64, w, ref)
         out[f"{name}_N15_E8192"] = r
-    del u, G, D, w, ref, X, xq
+    del u, u64, G, D, w, ref, X, xq
     torch.cuda.empty_cache()
 
     # uneven orders, one persistent graph-captured launch vs per-order launches
@@ -361,6 +372,7 @@ def variants(semax, reps: int) -> dict:
     w32 = torch.empty_like(u)
     r = rate(lambda: semax.sem_ax_f32(u, G, D, w32), dofs, dofs * bytes_per_node(4), 10)
     r["rel_err_vs_f64"] = rel_err_gpu(semax, w32, w64)
+    r["energy_rel_err"] = energy_rel_gpu(semax, u, w32, w64)
     out["f32_N7_E262144"] = r
     del u, G, D, w32, w64
     torch.cuda.empty_cache()
@@ -423,6 +435,7 @@ def run_ours(args, rank, world):
                       world) / args.steps
     f64x = {"gdofs": world * dofs / t_x / 1e9, "hbm_gbs": world * dofs * bytes_per_node(8) / t_x / 1e9,
             "us_per_call": t_x * 1e6, "rel_err_vs_f64": rel_err_gpu(semax, wx, w),
+            "energy_rel_err": energy_rel_gpu(semax, mesh.u, wx, w),
             "arith": "double-float contractions on the FP32 pipe, FP64 geometric factor; FP64 in/out"}
     del wx
     # FP64-accurate tensor-core form (exact digit slicing) on the same workload
@@ -431,6 +444,7 @@ def run_ours(args, rank, world):
                       world) / args.steps
     f64tc = {"gdofs": world * dofs / t_t / 1e9, "hbm_gbs": world * dofs * bytes_per_node(8) / t_t / 1e9,
              "us_per_call": t_t * 1e6, "rel_err_vs_f64": rel_err_gpu(semax, wt, w),
+             "energy_rel_err": energy_rel_gpu(semax, mesh.u, wt, w),
              "hbm_frac_of_measured": world * dofs * bytes_per_node(8) / t_t / 1e9 / load_peaks().get("hbm_gbs", 6786.6),
              "bound": "instruction issue (tensor pipe ~17 % busy; digit extraction and double-float work on the CUDA cores)",
              "arith": "contractions on BF16 tensor cores by exact base-256 digit slicing (levels 2..7), "

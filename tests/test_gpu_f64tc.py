@@ -180,3 +180,17 @@ def test_f64tc_max_size_offsets_past_2_31(semax, oracle_mod):
     w64 = semax.sem_ax(u, G, base.D)
     r = semax.reduce(w, w64).cpu().numpy()
     assert r[0] / r[1] <= TYPICAL_TC
+
+
+def test_energy_norm_on_the_gpu(semax, oracle_mod):
+    """u^T A u with the FP64 reduction on the GPU: equal to the oracle's energy
+    for the FP64 and both FP64-accurate forms, and positive for random u."""
+    m = si.make_mesh(np.random.default_rng(81), 40, 7)
+    ref = oracle_mod.sem_ax(m.u, m.G, m.D)
+    e_ref = float(np.sum(m.u.numpy() * ref))
+    assert e_ref > 0
+    u = m.u.cuda()
+    for fn in (semax.sem_ax, semax.sem_ax_f64x, semax.sem_ax_f64tc):
+        w = fn(u, m.G.cuda(), m.D.cuda())
+        e = float(semax.reduce(u.reshape(-1), w.reshape(-1)).cpu().numpy()[2])
+        assert abs(e - e_ref) <= 1e-12 * e_ref
