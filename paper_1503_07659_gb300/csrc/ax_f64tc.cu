@@ -252,11 +252,10 @@ __device__ __forceinline__ void store_tile(float2 *buf, const float (&acc)[6][4]
 __device__ __forceinline__ df split_g(double x, int eb, unsigned K, int ebmin) {
     const unsigned h32 = (unsigned)__double2hiint(x), l32 = (unsigned)__double2loint(x);
     const unsigned f = __funnelshift_l(l32, h32, 3);
-    const unsigned hb = (f - K) | (h32 & 0x80000000u);
+    const float hi = eb >= ebmin ? __uint_as_float((f - K) | (h32 & 0x80000000u)) : 0.0f;
     const float r = __fsub_rn(__uint_as_float(0x4B000000u | ((l32 >> 6) & 0x7fffffu)), 8388608.0f);
-    const float sc = __fmul_rn(__uint_as_float(hb & 0x7f800000u), 0x1p-46f);
-    const float lo = __uint_as_float(__float_as_uint(__fmul_rn(r, sc)) | (h32 & 0x80000000u));
-    return eb >= ebmin ? df{__uint_as_float(hb), lo} : df{0.0f, 0.0f};
+    const float sc = __fmul_rn(__uint_as_float(__float_as_uint(hi) & 0x7f800000u), 0x1p-46f);   // 0 with hi
+    return {hi, __uint_as_float(__float_as_uint(__fmul_rn(r, sc)) | (h32 & 0x80000000u))};
 }
 
 // y = sum_b Gh[b] V[b] (double-float products, Dot2-style accumulation)
@@ -501,6 +500,8 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
             *reinterpret_cast<double2 *>(we + nb) = make_double2(o[0], o[1]);
         }
     }
+    __syncthreads();   // no thread polls the mbarrier any more, and no copy is in flight
+    if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 static int launch(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s) {
