@@ -88,6 +88,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity) {
 }
 
 __device__ __forceinline__ int bexp(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+// |x|'s high word: the biased exponent in bits 20-30 above the top significand
+// bits, so the largest such word of a group carries the group's largest
+// exponent, and word >= (e << 20) tests exponent >= e
+__device__ __forceinline__ unsigned habs(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
 
 // Two integer-valued floats (|v| <= 256) as a BF16 pair, a in the low half;
 // exact because such a float has no bits below its top 16.
@@ -246,13 +250,14 @@ __device__ __forceinline__ void store_tile(float2 *buf, const float (&acc)[6][4]
 // x 2^-sh as hi + lo by bit operations: hi = the top 24 bits of x's
 // significand, lo = the next 23.  K = (896 + sh) << 23 turns the double's
 // exponent field (its low 9 bits, shifted into place with the significand)
-// into the float's; entries with eb < ebmin = max(897 + sh, 1) (zeros,
-// subnormals, and values below 2^-126 of the scale) become zero.  lo = r23 2^-46 2^(ef - 127), formed as a product so
-// that small exponents underflow gracefully.
-__device__ __forceinline__ df split_g(double x, int eb, unsigned K, int ebmin) {
+// into the float's.  hw = habs(x); entries whose biased exponent is below
+// max(897 + sh, 1) (min_word = that << 20: zeros, subnormals, and values below
+// 2^-126 of the scale) become zero.  lo = r23 2^-46 2^(ef - 127), formed as a
+// product so that small exponents underflow gracefully.
+__device__ __forceinline__ df split_g(double x, unsigned hw, unsigned K, unsigned min_word) {
     const unsigned h32 = (unsigned)__double2hiint(x), l32 = (unsigned)__double2loint(x);
     const unsigned f = __funnelshift_l(l32, h32, 3);
-    const float hi = eb >= ebmin ? __uint_as_float((f - K) | (h32 & 0x80000000u)) : 0.0f;
+    const float hi = hw >= min_word ? __uint_as_float((f - K) | (h32 & 0x80000000u)) : 0.0f;
     const float r = __fsub_rn(__uint_as_float(0x4B000000u | ((l32 >> 6) & 0x7fffffu)), 8388608.0f);
     const float sc = __fmul_rn(__uint_as_float(__float_as_uint(hi) & 0x7f800000u), 0x1p-46f);   // 0 with hi
     return {hi, __uint_as_float(__float_as_uint(__fmul_rn(r, sc)) | (h32 & 0x80000000u))};
@@ -335,7 +340,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         for (int h = 0; h < 2; ++h) uv[h] = ust[(2 * warp + h) * 32 + g * 4 + t];
         int ex = 1;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) ex = max(ex, max(bexp(uv[h].x), bexp(uv[h].y)));
+        for (int h = 0; h < 2; ++h) ex = max(ex, (int)(max(habs(uv[h].x), habs(uv[h].y)) >> 20));
         ex = __reduce_max_sync(0xffffffffu, ex);
         if (lane == 0) sred[warp] = ex;
         if (__syncthreads_or(timed_out)) {
@@ -353,8 +358,9 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             float d0[kS], d1[kS];
-            const df a0 = split_g(uv[h].x, bexp(uv[h].x), Ku, max(eU - 126, 1));
-            const df a1 = split_g(uv[h].y, bexp(uv[h].y), Ku, max(eU - 126, 1));
+            const unsigned mw = (unsigned)max(eU - 126, 1) << 20;
+            const df a0 = split_g(uv[h].x, habs(uv[h].x), Ku, mw);
+            const df a1 = split_g(uv[h].y, habs(uv[h].y), Ku, mw);
             const df n0 = dfx::fast_two_sum(a0.hi, a0.lo), n1 = dfx::fast_two_sum(a1.hi, a1.lo);
             digits_df(n0.hi, n0.lo, 128.0f, 8388608.0f, d0);
             digits_df(n1.hi, n1.lo, 128.0f, 8388608.0f, d1);
@@ -402,18 +408,19 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 const df Vs{sv.x, sv.y};
                 const df Vt = c ? df{tv.z, tv.w} : df{tv.x, tv.y};
                 double Gc[6];
-                int ebs[6], eg = 0;
+                unsigned hws[6], hmax = 0;
 #pragma unroll
                 for (int a = 0; a < 6; ++a) {
                     Gc[a] = c ? gv[a].y : gv[a].x;
-                    ebs[a] = bexp(Gc[a]);
-                    eg = max(eg, ebs[a]);
+                    hws[a] = habs(Gc[a]);
+                    hmax = max(hmax, hws[a]);
                 }
+                const int eg = (int)(hmax >> 20);   // largest biased exponent of the node's G
                 const int sh = max(eg, 1) - 1023;   // G * 2^-sh has magnitude < 2
                 const unsigned K = (unsigned)(896 + sh) << 23;
                 df Gh[6];
 #pragma unroll
-                for (int a = 0; a < 6; ++a) Gh[a] = split_g(Gc[a], ebs[a], K, max(897 + sh, 1));
+                for (int a = 0; a < 6; ++a) Gh[a] = split_g(Gc[a], hws[a], K, (unsigned)max(897 + sh, 1) << 20);
                 y[q][0] = dot3(Gh[0], Gh[1], Gh[2], vr[q], Vs, Vt);
                 y[q][1] = dot3(Gh[1], Gh[3], Gh[4], vr[q], Vs, Vt);
                 y[q][2] = dot3(Gh[2], Gh[4], Gh[5], vr[q], Vs, Vt);
