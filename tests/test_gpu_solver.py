@@ -172,3 +172,23 @@ def test_pcg_mixed_precision_iterative_refinement(semax, solver_oracle):
     xs, its, rels = solve(1e-15, mixed=True, f64tc=True)   # below that operator's floor
     assert its < 3000 and rels > 1e-15                       # stops on stagnation, not at max_iter
     gs.close()
+
+
+@pytest.mark.parametrize("N,shape", [(4, (3, 2, 2)), (3, (3, 3, 2))])
+def test_pcg_mixed_other_orders(semax, solver_oracle, N, shape):
+    """Mixed-precision refinement with the FP32 tile of other orders (odd n
+    uses the column map) reaches the FP64 solver's solution."""
+    m, G, B, D, ue, mask = _setup(shape, N, 40 + N)
+    b = mask * solver_oracle.gather_scatter(B.numpy() * 3 * np.pi ** 2 * ue, m.l2g, m.nglobal)
+    gs = semax.GatherScatter(m.l2g, m.nglobal, m.boundary)
+    bd = torch.from_numpy(b).cuda()
+    xs = []
+    for kw in ({}, {"mixed": True}):
+        pcg = semax.PCG(G.cuda(), D.cuda(), gs, **kw)
+        x = torch.zeros_like(bd)
+        it, rel = pcg.solve(bd, x, max_iter=4000, rtol=1e-11)
+        assert rel <= 1e-11, (kw, it, rel)
+        xs.append(x.cpu().numpy())
+        pcg.close()
+    assert np.max(np.abs(xs[0] - xs[1])) <= 1e-9 * np.max(np.abs(xs[0]))
+    gs.close()
