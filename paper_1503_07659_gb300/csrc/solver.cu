@@ -182,8 +182,9 @@ update_kernel(int64_t count, double *__restrict__ x, double *__restrict__ r, dou
         r[q] = rq;
         const double zq = invdiag[q] * rq;
         z[q] = zq;
-        s0 = __fma_rn(rq * zq, wt[q], s0);
-        s1 = __fma_rn(rq * rq, wt[q], s1);
+        const double tq = rq * wt[q];   // shared by both weighted partials
+        s0 = __fma_rn(tq, zq, s0);
+        s1 = __fma_rn(tq, rq, s1);
     }
     block_sum2(s0, s1, part + 2 * blockIdx.x);
     finish_in_last_block(part, scal, FIN_RZ_RR, counter);
