@@ -85,28 +85,23 @@ __device__ __forceinline__ df acc_add(acc2 a, acc2 b) {
 }
 __device__ __forceinline__ df acc_sub(acc2 a, acc2 b) { return acc_add(a, acc2{-b.s, -b.c}); }
 
-// 2^k as a float, k in [-126, 127]
-__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(k + 127) << 23); }
-
 // x * 2^-sh split into hi + lo by bit operations (no FP64 instruction).
 // Values whose scaled magnitude is below the float range flush to zero.
 // Inf and NaN are not representable here (they come out finite): the tile
 // recognises their element by its exponent maximum (0x7ff) and writes NaN.
 __device__ __forceinline__ df split_double(double x, int sh) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
-    const int eb = (int)((hi32 >> 20) & 0x7ffu);
-    const int ef = eb - sh - 1023 + 127;             // biased float exponent of hi
-    if (eb == 0 || ef < 1) return {0.f, 0.f};
-    const unsigned sign = hi32 & 0x80000000u;
-    const unsigned mh = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
-    const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | mh);
-    const unsigned r23 = (lo32 >> 6) & 0x7fffffu;
-    const float r = __fsub_rn(__uint_as_float(0x4B000000u | r23), 8388608.0f);   // = r23 exactly
-    const int k = ef - 127 - 46;                      // lo = r23 * 2^k
-    float lo = k >= -126 ? __fmul_rn(r, pow2f(k)) : __fmul_rn(__fmul_rn(r, pow2f(k + 64)), pow2f(-64));
-    if (sign) lo = -lo;
-    return {hi, lo};
+    // A funnel shift puts the double's exponent (its low 9 bits) next to the
+    // top 23 significand bits; subtracting (896 + sh) << 23 rebiases it to
+    // the float's.  Zeros, subnormals and entries below the float range
+    // (biased exponent < 897 + sh) give hi = 0, hence lo = 0 through sc.
+    const unsigned h32 = (unsigned)__double2hiint(x), l32 = (unsigned)__double2loint(x);
+    const unsigned sign = h32 & 0x80000000u;
+    const unsigned min_word = (unsigned)(897 + sh > 1 ? 897 + sh : 1) << 20;
+    const unsigned f = __funnelshift_l(l32, h32, 3);
+    const float hi = (h32 & 0x7fffffffu) >= min_word ? __uint_as_float((f - ((unsigned)(896 + sh) << 23)) | sign) : 0.f;
+    const float r = __fsub_rn(__uint_as_float(0x4B000000u | ((l32 >> 6) & 0x7fffffu)), 8388608.0f);   // r23
+    const float sc = __fmul_rn(__uint_as_float(__float_as_uint(hi) & 0x7f800000u), 0x1p-46f);   // 2^(ef-127-46)
+    return {hi, __uint_as_float(__float_as_uint(__fmul_rn(r, sc)) | sign)};
 }
 
 // a float (normal or zero) as a double, exactly, by bit operations
@@ -334,7 +329,8 @@ __device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__rest
             reinterpret_cast<double *>(sr)[s] = wr;
             reinterpret_cast<double *>(ss)[s] = ws;
             reinterpret_cast<double *>(su)[s] = wt;
-            mx = max(mx, max(biased_exponent(wr), max(biased_exponent(ws), biased_exponent(wt))));
+            mx = max(mx, (int)(max(__double2hiint(wr) & 0x7fffffff,
+                                   max(__double2hiint(ws) & 0x7fffffff, __double2hiint(wt) & 0x7fffffff)) >> 20));
         }
         exp_max(sexp + epb, e, mx);
     }
