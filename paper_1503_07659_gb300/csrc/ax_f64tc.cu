@@ -365,12 +365,17 @@ static int launch(int64_t E, const double *u, const double *G, const double *D, 
 }  // namespace oz
 }  // namespace semax
 
+namespace semax {
+int launch_f64tc16(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s);
+}
+
 using namespace semax;
 
 extern "C" int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const double *D, double *w,
                             void *stream) {
     int st = check_args(E, N, u, G, D, w);
     if (st != SEMAX_OK || E == 0) return st;
-    if (N != 7) return sem_ax_f64x(E, N, u, G, D, w, stream);   // other orders: the double-float tile
-    return oz::launch(E, u, G, D, w, (cudaStream_t)stream);
+    if (N == 7) return oz::launch(E, u, G, D, w, (cudaStream_t)stream);
+    if (N == 15) return launch_f64tc16(E, u, G, D, w, (cudaStream_t)stream);
+    return sem_ax_f64x(E, N, u, G, D, w, stream);   // other orders: the double-float tile
 }

@@ -1,0 +1,530 @@
+// FP64-accurate Ax for order N = 15 (n = 16) on BF16 tensor cores by exact
+// digit slicing, the method of the order-7 form (ax_f64tc.cuh): each operand
+// as six balanced base-256 digits against a power-of-two scale, the digit
+// pairs of levels 2..7 summed exactly in FP32 accumulators (one pair per
+// m16n8k16 product, K = 16 terms; a level gathers at most six pairs, so the
+// sums stay below 6 * 16 * 2^16 < 2^23), the level sums combined in
+// double-float.
+//
+// One CTA of 16 warps per element, persistent over elements.  Warp w owns
+// plane k = w for every pointwise step, in the accumulator layout of an
+// m16n8 tile pair (rows j, columns i = 0..7 and 8..15).  With n = 16 = M,
+// the r- and s-contractions of a plane both land in that layout:
+//   r: C[j][i] = sum_l U_k[j][l] D^T[l][i]   (A: u digits, B: D digits)
+//   s: C[j][i] = sum_l D[j][l] U_k[l][i]     (A: D digits, B: u digits)
+// so the gradient's r and s parts never leave their warp; the t-part is
+// formed per row j (warp w owns j = w there: C[k][i] = sum_l D[k][l] U_j[l][i])
+// and crosses through a shared double-float buffer.  The transposed side
+// mirrors this: the digits of y_r = (G grad)_r pack from the accumulator
+// layout straight into A fragments, those of y_s are transposed into B
+// fragments by movmatrix, and only y_t's digits go through shared memory.
+// y_r, y_s and y_t take separate per-element scales.
+//
+// G is staged in two halves by TMA bulk copies: (rr, rs, rt) while the
+// gradient runs (y_r complete, the r-parts of y_s and y_t formed), then
+// (ss, st, tt) while the transposed r-contraction runs.  The next element's
+// u is loaded into registers during the last phases.
+#include "ax_f64tc.cuh"
+
+namespace semax {
+namespace oz16 {
+
+using namespace oz;
+
+constexpr int kThreads = 512;
+constexpr int kN3 = 4096;
+constexpr int kPlaneB = 512;                 // one 16 x 16 BF16 plane
+constexpr int kDigitB = 16 * kPlaneB;        // one digit of a 16^3 operand
+constexpr int kUD = kS * kDigitB;            // digits of u, later of y_t (48 KB)
+constexpr int kDD = kS * kPlaneB;            // digits of D (3 KB)
+constexpr int kTB = kN3 * 8;                 // double-float per node: t-direction (32 KB)
+constexpr int kSB = kN3 * 8;                 // double-float per node: the s-gradient, parked (32 KB)
+constexpr int kGS = 3 * kN3 * 8;             // half of an element's G (96 KB)
+constexpr int kRed = 64 * 4;                 // reduction slots
+constexpr size_t kSmem = kUD + kDD + kTB + kSB + kGS + kRed + 16;   // + two mbarriers
+
+// Byte offset of (row r, 16-byte chunk c) of the 16 x 16 BF16 plane p: the
+// 32 chunks of a plane are permuted by p and by bit 2 of r, so that ldmatrix
+// over 8 rows of a plane (r = 0..7 or 8..15) and over 8 planes of a row both
+// touch 8 distinct bank groups.
+__device__ __forceinline__ int pch(int p, int r, int c) {
+    return p * kPlaneB + ((((2 * r + c) ^ ((p & 7) ^ ((r >> 2) & 1)))) << 4);
+}
+
+// Node-pair slot (16 bytes: two double-floats) of (k, j, i = 2 ip) in the
+// t-direction buffer; bit 2 flipped by (j ^ k) & 1, so that the row owners'
+// writes and the plane owners' reads are both conflict-free.
+__device__ __forceinline__ int tslot(int k, int j, int ip) { return (k * 128 + j * 8 + ip) ^ (((j ^ k) & 1) << 2); }
+
+// acc[L] += A_a B_b over the 21 digit pairs a + b = L <= 5
+__device__ __forceinline__ void pairs21(float (&acc)[6][4], const uint32_t (&A)[kS][4], const uint32_t (&B)[kS][2]) {
+#pragma unroll
+    for (int L = 0; L < 6; ++L) acc[L][0] = acc[L][1] = acc[L][2] = acc[L][3] = 0.0f;
+#pragma unroll
+    for (int L = 0; L < 6; ++L)
+#pragma unroll
+        for (int a = 0; a <= L; ++a)
+            mma::bf16_16816(acc[L], A[a][0], A[a][1], A[a][2], A[a][3], B[L - a][0], B[L - a][1]);
+}
+
+__device__ __forceinline__ int max16(const int *p) {
+    const int4 a = reinterpret_cast<const int4 *>(p)[0], b = reinterpret_cast<const int4 *>(p)[1];
+    const int4 c = reinterpret_cast<const int4 *>(p)[2], d = reinterpret_cast<const int4 *>(p)[3];
+    return max(max(max(max(a.x, a.y), max(a.z, a.w)), max(max(b.x, b.y), max(b.z, b.w))),
+               max(max(max(c.x, c.y), max(c.z, c.w)), max(max(d.x, d.y), max(d.z, d.w))));
+}
+
+// the double-float value d 2^k (k <= 0) in floats; 0 when below the range
+__device__ __forceinline__ df scale_df(df d, int k) {
+    const float f = pow2f_or_zero(k);
+    return {__fmul_rn(d.hi, f), __fmul_rn(d.lo, f)};
+}
+
+// (a.s + a.c) 2^ka + (b.s + b.c) 2^kb, ka, kb <= 0, as acc2
+__device__ __forceinline__ acc2 add_scaled(acc2 a, int ka, acc2 b, int kb) {
+    const df x = scale_df(df{a.s, a.c}, ka), y = scale_df(df{b.s, b.c}, kb);
+    const df t = dfx::two_sum(x.hi, y.hi);
+    return acc2{t.hi, __fadd_rn(__fadd_rn(x.lo, y.lo), t.lo)};
+}
+
+// a * x for double-floats a (geometric factor) and x, as acc2
+__device__ __forceinline__ acc2 prod(df a, df x) {
+    const float m = __fmul_rn(a.hi, x.hi);
+    float r = __fmaf_rn(a.hi, x.hi, -m);
+    r = __fmaf_rn(a.hi, x.lo, r);
+    r = __fmaf_rn(a.lo, x.hi, r);
+    return acc2{m, r};
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
+                  const double *__restrict__ D, double *__restrict__ w) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *ud = smem;
+    unsigned char *dd = ud + kUD;
+    float4 *tb = reinterpret_cast<float4 *>(dd + kDD);                 // [2048] node pairs
+    float2 *sb = reinterpret_cast<float2 *>(dd + kDD + kTB);           // [8][512] per-thread slots
+    const double2 *gs = reinterpret_cast<const double2 *>(dd + kDD + kTB + kSB);   // [3][2048]
+    int *sred = reinterpret_cast<int *>(dd + kDD + kTB + kSB + kGS);   // 4 x 16 slots
+    const uint32_t ud_s = smem_u32(ud), dd_s = smem_u32(dd), gs_s = smem_u32(gs);
+    const uint32_t barA = smem_u32(sred + 64), barB = barA + 8;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const int mi = lane >> 3, rr = lane & 7;
+    const int k = warp;   // the plane this warp owns in the pointwise phases (and the row j in the t-phases)
+
+    if (tid == 0) {
+        mbar_init(barA, 1);
+        mbar_init(barB, 1);
+    }
+    __syncthreads();
+    auto stage = [&](uint32_t bar, const double *src) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, kGS);
+        bulk_g2s(gs_s, src, kGS, bar);
+    };
+    if (tid == 0) stage(barA, G + (int64_t)blockIdx.x * 6 * kN3);
+
+    // ---- D digits, once per CTA: [p][16 x 16] in the plane layout
+    int eD = 1;
+    if (tid < 256) eD = max((int)(habs(D[tid]) >> 20), 1);
+    eD = __reduce_max_sync(0xffffffffu, eD);
+    if (lane == 0) sred[warp] = eD;
+    __syncthreads();
+    eD = max16(sred);
+    if (tid < 256) {
+        float d[kS];
+        digits_fp64(D[tid], eD, d);
+        const int a = tid >> 4, b = tid & 15;
+#pragma unroll
+        for (int p = 0; p < kS; ++p)
+            *reinterpret_cast<unsigned short *>(dd + p * kPlaneB + pch(0, a, b >> 3) + 2 * (b & 7)) =
+                (unsigned short)(__float_as_uint(d[p]) >> 16);
+    }
+    __syncthreads();
+
+    // lane addresses of the two ldmatrix x4 arrangements (row, 16-byte chunk)
+    const int r1 = rr + 8 * (mi & 1), c1 = mi >> 1;   // a0..a3 = (0-7,0) (8-15,0) (0-7,1) (8-15,1)
+    const int r2 = rr + 8 * (mi >> 1), c2 = mi & 1;   // (0-7,0) (0-7,1) (8-15,0) (8-15,1)
+    const int rx = rr + 8 * (mi & 1);                 // x2: rows 0-7, 8-15 of one chunk
+
+    // thread's nodes: q = 4 nt + e -> (j, i) = (g + 8 (e >> 1), 8 nt + 2 t + (e & 1)) in plane k
+    double2 uv[2][2];   // [nt][row half]
+    auto load_u = [&](int64_t ep) {
+        const double *ue = u + ep * kN3 + k * 256;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                double2 v;
+                asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];"
+                             : "=d"(v.x), "=d"(v.y) : "l"(ue + (g + 8 * h) * 16 + 8 * nt + 2 * t));
+                uv[nt][h] = v;
+            }
+    };
+    load_u(blockIdx.x);
+
+    unsigned pA = 0, pB = 0;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x, pA ^= 1u, pB ^= 1u) {
+        const double *Ge = G + e * 6 * kN3;
+        double *we = w + e * kN3;
+
+        // ---- A: u -> digits
+        const bool toA = !mbar_wait(barA, pA);   // G's first half (staged during the previous element)
+        int ex = 1;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) ex = max(ex, (int)(max(habs(uv[nt][h].x), habs(uv[nt][h].y)) >> 20));
+        ex = __reduce_max_sync(0xffffffffu, ex);
+        if (lane == 0) sred[warp] = ex;
+        if (__syncthreads_or(toA)) {
+            for (int64_t r = e; r < E; r += gridDim.x)
+                for (int q = tid; q < kN3; q += kThreads) w[r * kN3 + q] = __longlong_as_double(0x7ff8000000000000ll);
+            mbar_wait(barA, pA);
+            return;
+        }
+        const int eU = max16(sred);
+        {
+            const unsigned Ku = (unsigned)(eU - 127) << 23, mw = (unsigned)max(eU - 126, 1) << 20;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float d0[kS], d1[kS];
+                    const df a0 = split_g(uv[nt][h].x, habs(uv[nt][h].x), Ku, mw);
+                    const df a1 = split_g(uv[nt][h].y, habs(uv[nt][h].y), Ku, mw);
+                    const df n0 = dfx::fast_two_sum(a0.hi, a0.lo), n1 = dfx::fast_two_sum(a1.hi, a1.lo);
+                    digits_df(n0.hi, n0.lo, 128.0f, 8388608.0f, d0);
+                    digits_df(n1.hi, n1.lo, 128.0f, 8388608.0f, d1);
+                    unsigned char *p = ud + pch(k, g + 8 * h, nt) + 4 * t;
+#pragma unroll
+                    for (int q = 0; q < kS; ++q) *reinterpret_cast<uint32_t *>(p + q * kDigitB) = pack_bf16(d0[q], d1[q]);
+                }
+        }
+        __syncthreads();
+
+        // ---- B: gradient on tensor cores
+        df vr[8];   // r-gradient of the thread's nodes
+        {
+            uint32_t fa[kS][4];   // D as A (rows j or k, K = l)
+#pragma unroll
+            for (int p = 0; p < kS; ++p)
+                mma::ldsm_x4(dd_s + p * kPlaneB + pch(0, r1, c1), fa[p][0], fa[p][1], fa[p][2], fa[p][3]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                // s: B = U_k (rows l, columns i), transposed load
+                uint32_t bu[kS][2];
+#pragma unroll
+                for (int q = 0; q < kS; ++q) {
+                    uint32_t x2, x3;
+                    mma::ldsm_x4_t(ud_s + q * kDigitB + pch(k, rx, nt), bu[q][0], bu[q][1], x2, x3);
+                }
+                float acc[6][4];
+                pairs21(acc, fa, bu);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const df v = combine_levels(acc, c);
+                    sb[(4 * nt + c) * kThreads + tid] = make_float2(v.hi, v.lo);
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                // t (row j = k): B = U at row j (rows = planes l, columns i)
+                uint32_t bu[kS][2];
+#pragma unroll
+                for (int q = 0; q < kS; ++q) {
+                    uint32_t x2, x3;
+                    mma::ldsm_x4_t(ud_s + q * kDigitB + pch(rx, k, nt), bu[q][0], bu[q][1], x2, x3);
+                }
+                float acc[6][4];
+                pairs21(acc, fa, bu);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {   // rows kk = g + 8 h, columns i = 8 nt + 2 t, +1
+                    const df v0 = combine_levels(acc, 2 * h), v1 = combine_levels(acc, 2 * h + 1);
+                    tb[tslot(g + 8 * h, k, 4 * nt + t)] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+                }
+            }
+        }
+        {
+            // r: A = U_k (rows j, K = l), B = D^T from D stored (rows i, columns l)
+            uint32_t au[kS][4];
+#pragma unroll
+            for (int q = 0; q < kS; ++q)
+                mma::ldsm_x4(ud_s + q * kDigitB + pch(k, r1, c1), au[q][0], au[q][1], au[q][2], au[q][3]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                uint32_t bd[kS][2];
+#pragma unroll
+                for (int p = 0; p < kS; ++p) {
+                    uint32_t x2, x3;
+                    mma::ldsm_x4(dd_s + p * kPlaneB + pch(0, 8 * nt + rr, mi & 1), bd[p][0], bd[p][1], x2, x3);
+                }
+                float acc[6][4];
+                pairs21(acc, au, bd);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) vr[4 * nt + c] = combine_levels(acc, c);
+            }
+        }
+        __syncthreads();
+
+        // ---- C1: G's first half (rr, rs, rt): y_r, and the r-parts of y_s, y_t
+        acc2 yr[8], ysp[8], ytp[8];
+        int shA[8];
+        int tmax = INT_MIN;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = g + 8 * h, nd2 = (k * 256 + j * 16 + 8 * nt + 2 * t) >> 1;
+                const float4 tv = tb[tslot(k, j, 4 * nt + t)];
+                double2 gv[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) gv[a] = gs[a * 2048 + nd2];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int q = 4 * nt + 2 * h + c;
+                    const float2 s2 = sb[q * kThreads + tid];
+                    const df Vs{s2.x, s2.y}, Vt = c ? df{tv.z, tv.w} : df{tv.x, tv.y};
+                    double Gc[3];
+                    unsigned hw[3], hm = 0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Gc[a] = c ? gv[a].y : gv[a].x;
+                        hw[a] = habs(Gc[a]);
+                        hm = max(hm, hw[a]);
+                    }
+                    const int eg = (int)(hm >> 20), sh = max(eg, 1) - 1023;
+                    const unsigned K = (unsigned)(896 + sh) << 23, mw = (unsigned)max(897 + sh, 1) << 20;
+                    df Gh[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) Gh[a] = split_g(Gc[a], hw[a], K, mw);
+                    const acc2 y = dot3(Gh[0], Gh[1], Gh[2], vr[q], Vs, Vt);
+                    const df yn = dfx::two_sum(y.s, y.c);
+                    yr[q] = acc2{yn.hi, yn.lo};
+                    ysp[q] = prod(Gh[1], vr[q]);
+                    ytp[q] = prod(Gh[2], vr[q]);
+                    shA[q] = sh;
+                    const int ev = (int)(__float_as_uint(fabsf(yn.hi)) >> 23);
+                    if (ev) tmax = max(tmax, ev + sh);
+                    if (eg == 0x7ff) tmax = kBadExp;
+                }
+            }
+        tmax = __reduce_max_sync(0xffffffffu, tmax);
+        if (lane == 0) sred[16 + warp] = tmax;
+        __syncthreads();
+        if (tid == 0) stage(barB, Ge + 3 * kN3);   // every thread has read G's first half
+        const int eRraw = max16(sred + 16);
+        const int eR = eRraw == INT_MIN ? 0 : min(eRraw, kBadExp);
+
+        // y_r digits, packed from the accumulator layout into A fragments
+        uint32_t ya[kS][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q0 = 4 * nt + 2 * h;
+                float d0[kS], d1[kS];
+                digits_df(yr[q0].s, yr[q0].c, pow2f_or_zero(shA[q0] - eR + 134), pow2f_or_zero(shA[q0] - eR + 150), d0);
+                digits_df(yr[q0 + 1].s, yr[q0 + 1].c, pow2f_or_zero(shA[q0 + 1] - eR + 134),
+                          pow2f_or_zero(shA[q0 + 1] - eR + 150), d1);
+#pragma unroll
+                for (int d = 0; d < kS; ++d) ya[d][2 * nt + h] = pack_bf16(d0[d], d1[d]);
+            }
+
+        // ---- D_r: w_r = y_r D on tensor cores (B = D, rows l, columns i)
+        df wr_[8];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            uint32_t bd[kS][2];
+#pragma unroll
+            for (int p = 0; p < kS; ++p) {
+                uint32_t x2, x3;
+                mma::ldsm_x4_t(dd_s + p * kPlaneB + pch(0, rx, nt), bd[p][0], bd[p][1], x2, x3);
+            }
+            float acc[6][4];
+            pairs21(acc, ya, bd);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) wr_[4 * nt + c] = combine_levels(acc, c);
+        }
+
+        // ---- C2: G's second half (ss, st, tt): finish y_s, y_t
+        const bool toB = !mbar_wait(barB, pB);
+        acc2 ys[8], yt[8];
+        int shS[8];
+        int smax = INT_MIN, tmx = INT_MIN;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = g + 8 * h, nd2 = (k * 256 + j * 16 + 8 * nt + 2 * t) >> 1;
+                const float4 tv = tb[tslot(k, j, 4 * nt + t)];
+                double2 gv[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) gv[a] = gs[a * 2048 + nd2];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int q = 4 * nt + 2 * h + c;
+                    const float2 s2 = sb[q * kThreads + tid];
+                    const df Vs{s2.x, s2.y}, Vt = c ? df{tv.z, tv.w} : df{tv.x, tv.y};
+                    double Gc[3];
+                    unsigned hw[3], hm = 0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Gc[a] = c ? gv[a].y : gv[a].x;
+                        hw[a] = habs(Gc[a]);
+                        hm = max(hm, hw[a]);
+                    }
+                    const int eg = (int)(hm >> 20), sh = max(eg, 1) - 1023;
+                    const unsigned K = (unsigned)(896 + sh) << 23, mw = (unsigned)max(897 + sh, 1) << 20;
+                    df Gh[3];   // ss, st, tt
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) Gh[a] = split_g(Gc[a], hw[a], K, mw);
+                    // y_s = Grs r + Gss s + Gst t,  y_t = Grt r + Gst s + Gtt t
+                    acc2 bs = prod(Gh[0], Vs);
+                    dfx::dot2_step(bs, Gh[1], Vt);
+                    acc2 bt = prod(Gh[1], Vs);
+                    dfx::dot2_step(bt, Gh[2], Vt);
+                    const int sm = max(shA[q], sh);
+                    const acc2 s_ = add_scaled(ysp[q], shA[q] - sm, bs, sh - sm);
+                    const acc2 t_ = add_scaled(ytp[q], shA[q] - sm, bt, sh - sm);
+                    const df sn = dfx::two_sum(s_.s, s_.c), tn = dfx::two_sum(t_.s, t_.c);
+                    ys[q] = acc2{sn.hi, sn.lo};
+                    yt[q] = acc2{tn.hi, tn.lo};
+                    shS[q] = sm;
+                    const int es = (int)(__float_as_uint(fabsf(sn.hi)) >> 23);
+                    const int et = (int)(__float_as_uint(fabsf(tn.hi)) >> 23);
+                    if (es) smax = max(smax, es + sm);
+                    if (et) tmx = max(tmx, et + sm);
+                    if (eg == 0x7ff) smax = tmx = kBadExp;
+                }
+            }
+        smax = __reduce_max_sync(0xffffffffu, smax);
+        tmx = __reduce_max_sync(0xffffffffu, tmx);
+        if (lane == 0) {
+            sred[32 + warp] = smax;
+            sred[48 + warp] = tmx;
+        }
+        if (__syncthreads_or(toB)) {
+            for (int64_t r = e; r < E; r += gridDim.x)
+                for (int q = tid; q < kN3; q += kThreads) w[r * kN3 + q] = __longlong_as_double(0x7ff8000000000000ll);
+            mbar_wait(barB, pB);
+            return;
+        }
+        if (tid == 0 && e + gridDim.x < E) stage(barA, Ge + (int64_t)gridDim.x * 6 * kN3);   // next element's first half
+        const int eSraw = max16(sred + 32), eTraw = max16(sred + 48);
+        const int eS = eSraw == INT_MIN ? 0 : min(eSraw, kBadExp), eT = eTraw == INT_MIN ? 0 : min(eTraw, kBadExp);
+        const bool bad = eU == 0x7ff || eD == 0x7ff || eRraw >= kBadExp || eSraw >= kBadExp || eTraw >= kBadExp;
+
+        // y_s digits -> B fragments (movmatrix transposes each 8 x 8 block);
+        // y_t digits -> shared memory (plane k)
+        uint32_t yb[kS][4];   // [digit][b0(nt0), b1(nt0), b0(nt1), b1(nt1)]
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q0 = 4 * nt + 2 * h;
+                float d0[kS], d1[kS];
+                digits_df(ys[q0].s, ys[q0].c, pow2f_or_zero(shS[q0] - eS + 134), pow2f_or_zero(shS[q0] - eS + 150), d0);
+                digits_df(ys[q0 + 1].s, ys[q0 + 1].c, pow2f_or_zero(shS[q0 + 1] - eS + 134),
+                          pow2f_or_zero(shS[q0 + 1] - eS + 150), d1);
+                // block (rows j = 8h.., columns i = 8nt..) transposed: the B fragment of
+                // K rows l = 8h.. (b0 for h = 0, b1 for h = 1) of n-tile nt
+#pragma unroll
+                for (int d = 0; d < kS; ++d) yb[d][2 * nt + h] = mma::movm_t(pack_bf16(d0[d], d1[d]));
+                digits_df(yt[q0].s, yt[q0].c, pow2f_or_zero(shS[q0] - eT + 134), pow2f_or_zero(shS[q0] - eT + 150), d0);
+                digits_df(yt[q0 + 1].s, yt[q0 + 1].c, pow2f_or_zero(shS[q0 + 1] - eT + 134),
+                          pow2f_or_zero(shS[q0 + 1] - eT + 150), d1);
+                unsigned char *p = ud + pch(k, g + 8 * h, nt) + 4 * t;
+#pragma unroll
+                for (int d = 0; d < kS; ++d) *reinterpret_cast<uint32_t *>(p + d * kDigitB) = pack_bf16(d0[d], d1[d]);
+            }
+        __syncthreads();
+
+        // ---- D_s, D_t: A = D^T (from D stored rows l, columns j: transposed load)
+        df ws_[8];
+        {
+            uint32_t fat[kS][4];
+#pragma unroll
+            for (int p = 0; p < kS; ++p)
+                mma::ldsm_x4_t(dd_s + p * kPlaneB + pch(0, r2, c2), fat[p][0], fat[p][1], fat[p][2], fat[p][3]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                uint32_t bb[kS][2];
+#pragma unroll
+                for (int d = 0; d < kS; ++d) {
+                    bb[d][0] = yb[d][2 * nt];
+                    bb[d][1] = yb[d][2 * nt + 1];
+                }
+                float acc[6][4];
+                pairs21(acc, fat, bb);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) ws_[4 * nt + c] = combine_levels(acc, c);
+            }
+            if (e + gridDim.x < E) load_u(e + gridDim.x);   // next element's u, in flight through D_t and E
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                // row j = k: B = y_t digits at row j (rows = planes l, columns i)
+                uint32_t bt[kS][2];
+#pragma unroll
+                for (int q = 0; q < kS; ++q) {
+                    uint32_t x2, x3;
+                    mma::ldsm_x4_t(ud_s + q * kDigitB + pch(rx, k, nt), bt[q][0], bt[q][1], x2, x3);
+                }
+                float acc[6][4];
+                pairs21(acc, fat, bt);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const df v0 = combine_levels(acc, 2 * h), v1 = combine_levels(acc, 2 * h + 1);
+                    tb[tslot(g + 8 * h, k, 4 * nt + t)] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- E: w = 2^SH_r V_r + 2^SH_s V_s + 2^SH_t V_t, stored
+        const int base = (eU - 1022) + 2 * (eD - 1022) - 126 - 32;
+        const int SHr = base + eR, SHs = base + eS, SHt = base + eT;
+        const int SHm = max(SHr, max(SHs, SHt));
+        const bool SHok = SHm >= -1022 && SHm <= 1023;
+        const double scl = __longlong_as_double((long long)(min(max(SHm, -1022), 1023) + 1023) << 52);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = g + 8 * h;
+                const float4 tv = tb[tslot(k, j, 4 * nt + t)];
+                double o[2];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int q = 4 * nt + 2 * h + c;
+                    const df a = scale_df(wr_[q], SHr - SHm), b = scale_df(ws_[q], SHs - SHm);
+                    const df cc = scale_df(c ? df{tv.z, tv.w} : df{tv.x, tv.y}, SHt - SHm);
+                    const df s1 = dfx::two_sum(a.hi, b.hi);
+                    const df s2 = dfx::two_sum(s1.hi, cc.hi);
+                    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(a.lo, b.lo), cc.lo), __fadd_rn(s1.lo, s2.lo));
+                    const double v = (double)s2.hi + (double)lo;
+                    o[c] = bad ? __longlong_as_double(0x7ff8000000000000ll) : (SHok ? v * scl : scale2(v, SHm));
+                }
+                *reinterpret_cast<double2 *>(we + k * 256 + j * 16 + 8 * nt + 2 * t) = make_double2(o[0], o[1]);
+            }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(barA) : "memory");
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(barB) : "memory");
+    }
+}
+
+}  // namespace oz16
+
+int launch_f64tc16(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s) {
+    auto kern = oz16::ax_f64tc16_kernel;
+    int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz16::kSmem));
+    if (st != SEMAX_OK) return st;
+    const int64_t grid = std::min<int64_t>(E, (int64_t)device_sm_count());
+    kern<<<(unsigned)grid, oz16::kThreads, oz16::kSmem, s>>>(E, u, G, D, w);
+    return launch_status();
+}
+
+}  // namespace semax

@@ -141,7 +141,66 @@ def test_f64tc_nonfinite_input_poisons_only_its_element(semax, oracle_mod, bad, 
     assert rel_err(np.delete(w, 3, 0), ref) <= TYPICAL_TC
 
 
-@pytest.mark.parametrize("N,E", [(3, 20), (15, 4), (4, 9)])
+@pytest.mark.parametrize("E", [1, 3, 20])
+def test_f64tc_order15_against_oracle(semax, oracle_mod, E):
+    m = si.make_mesh(np.random.default_rng(900 + E), E, 15)
+    ref = oracle_mod.sem_ax(m.u, m.G, m.D)
+    err = rel_err(run(semax, m.u, m.G, m.D), ref)
+    assert err <= TYPICAL_TC
+
+
+def test_f64tc_order15_integer_inputs_are_exact(semax, oracle_mod):
+    rng = np.random.default_rng(91)
+    E = 6
+    u = torch.from_numpy(rng.integers(-100, 101, size=(E, 16, 16, 16)).astype(np.float64))
+    G = torch.from_numpy(rng.integers(0, 17, size=(E, 6, 16, 16, 16)).astype(np.float64))
+    D = torch.from_numpy(rng.integers(-8, 9, size=(16, 16)).astype(np.float64))
+    ref = oracle_mod.sem_ax(u, G, D)
+    w = run(semax, u, G, D).cpu().numpy()
+    assert np.array_equal(w, ref)
+
+
+def test_f64tc_order15_edge_inputs(semax, oracle_mod):
+    """Scaled inputs, a general D, zero G nodes and elements, zero and
+    constant fields, and a NaN that poisons only its element, at order 15."""
+    m = si.make_mesh(np.random.default_rng(92), 5, 15)
+    for us, gs in ((1e-300, 1.0), (1.0, 1e250), (2.0 ** -1000, 2.0 ** 900)):
+        u, G = m.u * us, m.G * gs
+        assert rel_err(run(semax, u, G, m.D), oracle_mod.sem_ax(u, G, m.D)) <= TYPICAL_TC
+    D = m.D.clone()
+    D[2, 3] += 0.25
+    assert rel_err(run(semax, m.u, m.G, D), oracle_mod.sem_ax(m.u, m.G, D)) <= TYPICAL_TC
+    G = m.G.clone()
+    G[1, :, 3, 4, 5] = 0.0
+    G[3] = 0.0
+    w = run(semax, m.u, G, m.D)
+    assert rel_err(w, oracle_mod.sem_ax(m.u, G, m.D)) <= TYPICAL_TC
+    assert torch.count_nonzero(w[3]).item() == 0
+    assert torch.count_nonzero(run(semax, torch.zeros_like(m.u), m.G, m.D)).item() == 0
+    w1 = run(semax, torch.full_like(m.u, 3.25), m.G, m.D)
+    assert w1.abs().max().item() <= 1e-12 * run(semax, m.u, m.G, m.D).abs().max().item()
+    u = m.u.clone()
+    u[2, 5, 1, 7] = float("nan")
+    w = run(semax, u, m.G, m.D).cpu().numpy()
+    assert np.isnan(w[2]).all()
+    ref = oracle_mod.sem_ax(np.delete(u.numpy(), 2, 0), np.delete(m.G.numpy(), 2, 0), m.D)
+    assert rel_err(np.delete(w, 2, 0), ref) <= TYPICAL_TC
+
+
+def test_f64tc_order15_full_size_sampled(semax, oracle_mod):
+    m = si.make_workload(2, device="cuda")[0]
+    w = semax.sem_ax_f64tc(m.u, m.G, m.D)
+    w64 = semax.sem_ax(m.u, m.G, m.D)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(93).choice(m.E, size=m.E // 256, replace=False))
+    it = torch.from_numpy(idx).cuda()
+    ref = oracle_mod.sem_ax(m.u[it].cpu(), m.G[it].cpu(), m.D.cpu())
+    assert rel_err(w[it], ref) <= TYPICAL_TC
+    r = semax.reduce(w, w64).cpu().numpy()
+    assert r[0] / r[1] <= TYPICAL_TC
+
+
+@pytest.mark.parametrize("N,E", [(3, 20), (4, 9), (11, 3)])
 def test_f64tc_other_orders_use_the_double_float_form(semax, oracle_mod, N, E):
     m = si.make_mesh(np.random.default_rng(760 + N), E, N)
     ref = oracle_mod.sem_ax(m.u, m.G, m.D)
