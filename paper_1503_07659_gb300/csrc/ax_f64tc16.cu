@@ -146,7 +146,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
     // lane addresses of the two ldmatrix x4 arrangements (row, 16-byte chunk)
     const int r1 = rr + 8 * (mi & 1), c1 = mi >> 1;   // a0..a3 = (0-7,0) (8-15,0) (0-7,1) (8-15,1)
     const int r2 = rr + 8 * (mi >> 1), c2 = mi & 1;   // (0-7,0) (0-7,1) (8-15,0) (8-15,1)
-    const int rx = rr + 8 * (mi & 1);                 // x2: rows 0-7, 8-15 of one chunk
+    const int rx = rr + 8 * (mi & 1);                 // x2: rows 0-7, 8-15 of one chunk (lanes 0-15)
 
     // thread's nodes: q = 4 nt + e -> (j, i) = (g + 8 (e >> 1), 8 nt + 2 t + (e & 1)) in plane k
     double2 uv[2][2];   // [nt][row half]
@@ -217,8 +217,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 uint32_t bu[kS][2];
 #pragma unroll
                 for (int q = 0; q < kS; ++q) {
-                    uint32_t x2, x3;
-                    mma::ldsm_x4_t(ud_s + q * kDigitB + pch(k, rx, nt), bu[q][0], bu[q][1], x2, x3);
+                    mma::ldsm_x2_t(ud_s + q * kDigitB + pch(k, rx, nt), bu[q][0], bu[q][1]);
                 }
                 float acc[6][4];
                 pairs21(acc, fa, bu);
@@ -234,8 +233,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 uint32_t bu[kS][2];
 #pragma unroll
                 for (int q = 0; q < kS; ++q) {
-                    uint32_t x2, x3;
-                    mma::ldsm_x4_t(ud_s + q * kDigitB + pch(rx, k, nt), bu[q][0], bu[q][1], x2, x3);
+                    mma::ldsm_x2_t(ud_s + q * kDigitB + pch(rx, k, nt), bu[q][0], bu[q][1]);
                 }
                 float acc[6][4];
                 pairs21(acc, fa, bu);
@@ -257,8 +255,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 uint32_t bd[kS][2];
 #pragma unroll
                 for (int p = 0; p < kS; ++p) {
-                    uint32_t x2, x3;
-                    mma::ldsm_x4(dd_s + p * kPlaneB + pch(0, 8 * nt + rr, mi & 1), bd[p][0], bd[p][1], x2, x3);
+                    mma::ldsm_x2(dd_s + p * kPlaneB + pch(0, 8 * nt + rr, mi & 1), bd[p][0], bd[p][1]);
                 }
                 float acc[6][4];
                 pairs21(acc, au, bd);
@@ -339,8 +336,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
             uint32_t bd[kS][2];
 #pragma unroll
             for (int p = 0; p < kS; ++p) {
-                uint32_t x2, x3;
-                mma::ldsm_x4_t(dd_s + p * kPlaneB + pch(0, rx, nt), bd[p][0], bd[p][1], x2, x3);
+                mma::ldsm_x2_t(dd_s + p * kPlaneB + pch(0, rx, nt), bd[p][0], bd[p][1]);
             }
             float acc[6][4];
             pairs21(acc, ya, bd);
@@ -468,8 +464,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 uint32_t bt[kS][2];
 #pragma unroll
                 for (int q = 0; q < kS; ++q) {
-                    uint32_t x2, x3;
-                    mma::ldsm_x4_t(ud_s + q * kDigitB + pch(rx, k, nt), bt[q][0], bt[q][1], x2, x3);
+                    mma::ldsm_x2_t(ud_s + q * kDigitB + pch(rx, k, nt), bt[q][0], bt[q][1]);
                 }
                 float acc[6][4];
                 pairs21(acc, fat, bt);
@@ -486,8 +481,6 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
         const int base = (eU - 1022) + 2 * (eD - 1022) - 126 - 32;
         const int SHr = base + eR, SHs = base + eS, SHt = base + eT;
         const int SHm = max(SHr, max(SHs, SHt));
-        const bool SHok = SHm >= -1022 && SHm <= 1023;
-        const double scl = __longlong_as_double((long long)(min(max(SHm, -1022), 1023) + 1023) << 52);
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
@@ -503,8 +496,14 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                     const df s1 = dfx::two_sum(a.hi, b.hi);
                     const df s2 = dfx::two_sum(s1.hi, cc.hi);
                     const float lo = __fadd_rn(__fadd_rn(__fadd_rn(a.lo, b.lo), cc.lo), __fadd_rn(s1.lo, s2.lo));
-                    const double v = (double)s2.hi + (double)lo;
-                    o[c] = bad ? __longlong_as_double(0x7ff8000000000000ll) : (SHok ? v * scl : scale2(v, SHm));
+                    // bit-level conversions and scaling: one FP64 add per node (the whole
+                    // CTA runs this phase at once, so FP64-pipe work here is not hidden)
+                    double dh, dl;
+                    if (dfx::f2d_scaled(s2.hi, SHm, dh) && dfx::f2d_scaled(lo, SHm, dl))
+                        o[c] = dh + dl;
+                    else
+                        o[c] = scale2(dfx::f2d(s2.hi) + dfx::f2d(lo), SHm);
+                    if (bad) o[c] = __longlong_as_double(0x7ff8000000000000ll);
                 }
                 *reinterpret_cast<double2 *>(we + k * 256 + j * 16 + 8 * nt + 2 * t) = make_double2(o[0], o[1]);
             }
