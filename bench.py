@@ -281,6 +281,15 @@ def variants(semax, reps: int) -> dict:
     m = si.make_workload(2, device="cuda")[0]
     dofs = m.dofs
     ref = semax.sem_ax(m.u, m.G, m.D)
+    # FP64 storage: the FP64 tile and the two FP64-accurate forms
+    w64 = torch.empty_like(m.u)
+    out["f64_N15_E8192"] = rate(lambda: semax.sem_ax(m.u, m.G, m.D, w64), dofs, dofs * bytes_per_node(8))
+    for name, fn in (("f64x", semax.sem_ax_f64x), ("f64tc", semax.sem_ax_f64tc)):
+        r = rate(lambda: fn(m.u, m.G, m.D, w64), dofs, dofs * bytes_per_node(8))
+        r["rel_err_vs_f64"] = rel_err_gpu(semax, w64, ref)
+        r["energy_rel_err"] = energy_rel_gpu(semax, m.u, w64, ref)
+        out[f"{name}_N15_E8192"] = r
+    del w64
     u, G, D = m.u.float(), m.G.float(), m.D.float()
     u64 = m.u
     X = torch.from_numpy(m.X).float().cuda().contiguous()

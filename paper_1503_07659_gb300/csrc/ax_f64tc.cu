@@ -323,8 +323,6 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         // ---- E: sum, undo the scales, store
         // w = 2^((eU - 1022) + 2 (eD - 1022) + (eW - 126) - 32) V_out
         const int SH = (eU - 1022) + 2 * (eD - 1022) + (eW - 126) - 32;
-        const bool SHok = SH >= -1022 && SH <= 1023;
-        const double scl = __longlong_as_double((long long)(min(max(SH, -1022), 1023) + 1023) << 52);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = 2 * warp + h, nb = k * 64 + g * 8 + 2 * t;
@@ -337,8 +335,13 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 const df a = dfx::two_sum(vo[2 * h + c].hi, sv.x);
                 const df b = dfx::two_sum(a.hi, th);
                 const float lo = __fadd_rn(__fadd_rn(__fadd_rn(vo[2 * h + c].lo, sv.y), tl), __fadd_rn(a.lo, b.lo));
-                const double v = (double)b.hi + (double)lo;
-                o[c] = bad ? __longlong_as_double(0x7ff8000000000000ll) : (SHok ? v * scl : scale2(v, SH));
+                // bit-level conversions with the scale in the exponent field: one FP64 add
+                double dh, dl;
+                if (dfx::f2d_scaled(b.hi, SH, dh) && dfx::f2d_scaled(lo, SH, dl))
+                    o[c] = dh + dl;
+                else
+                    o[c] = scale2(dfx::f2d(b.hi) + dfx::f2d(lo), SH);
+                if (bad) o[c] = __longlong_as_double(0x7ff8000000000000ll);
             }
             *reinterpret_cast<double2 *>(we + nb) = make_double2(o[0], o[1]);
         }

@@ -187,6 +187,23 @@ def test_f64tc_order15_edge_inputs(semax, oracle_mod):
     assert rel_err(np.delete(w, 2, 0), ref) <= TYPICAL_TC
 
 
+def test_f64tc_order15_unbalanced_geometric_factor(semax, oracle_mod):
+    """Nodes whose (ss, st, tt) and (rr, rs, rt) differ in scale by far more
+    than the common-scale path takes (2^80, 2^-70, one group zero), in whole
+    elements and in some nodes of an element: every element still matches
+    the oracle to its own scale."""
+    m = si.make_mesh(np.random.default_rng(94), 5, 15)
+    G = m.G.clone()
+    G[0, 3:] *= 2.0 ** 80                   # second half far above the first
+    G[1, :3, ::2] *= 2.0 ** -70             # first half far below, in every other plane
+    G[2, :3, :, 5] = 0.0                    # first half zero in one row of every plane
+    G[3, 3:, 7, :, 2:9] = 0.0               # second half zero in part of a plane
+    ref = oracle_mod.sem_ax(m.u, G, m.D)
+    w = run(semax, m.u, G, m.D).cpu().numpy()
+    for e in range(m.E):
+        assert rel_err(w[e], ref[e]) <= TYPICAL_TC, e
+
+
 def test_f64tc_order15_full_size_sampled(semax, oracle_mod):
     m = si.make_workload(2, device="cuda")[0]
     w = semax.sem_ax_f64tc(m.u, m.G, m.D)
