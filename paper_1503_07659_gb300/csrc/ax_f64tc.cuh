@@ -140,6 +140,93 @@ __device__ __forceinline__ df combine_levels(const float (&x)[6][4], int e) {
     return {s2, __fadd_rn(r, e2)};
 }
 
+// ---- base-1024 digits in FP16 (five per operand)
+//
+// Balanced base-1024 digits are integers of magnitude <= 528 here, exact in
+// FP16 (11 significant bits).  With K = 16 terms per product, the level sums
+// of levels 0..2 stay below 2^24 and are exact in FP32; levels 3 and 4 may
+// exceed it by a few per cent and round by a unit or two, at weights 2^-30
+// and 2^-40 of level 0, which is far below the 2^-48 the five digits keep.
+
+constexpr int kS10 = 5;
+
+// Two integer-valued floats (|v| <= 2048) as an FP16 pair, a in the low half
+// (exact: such a float has at most 11 significant bits).
+__device__ __forceinline__ uint32_t pack_f16(float a, float b) {
+    uint32_t d;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
+
+// Balanced base-1024 digits of x * 2^-(E - 1022), E >= the biased exponent
+// of x (at least 1): M = round(x * 2^(49 - (E - 1022))) = sum_q d[q]
+// 2^(10 (4 - q)), |M| <= 2^49, d[1..4] in [-512, 511], |d[0]| <= 512.
+// Integer arithmetic only.
+__device__ __forceinline__ void digits10_fp64(double x, int E, float (&d)[kS10]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int eb = (int)((b >> 52) & 0x7ffu);
+    const unsigned long long m = (b & 0xfffffffffffffull) | (eb ? (1ull << 52) : 0ull);
+    const int s = min(E + 4 - max(eb, 1), 63);   // >= 4
+    long long M = (long long)((m + (1ull << (s - 1))) >> s);
+    if (b >> 63) M = -M;
+    int lo = (int)(M & 0x3fffffff);   // M = hi 2^30 + lo, lo in [0, 2^30)
+    int hi = (int)(M >> 30);
+    int q[kS10];
+#pragma unroll
+    for (int i = kS10 - 1; i >= 2; --i) {
+        q[i] = ((lo + 512) & 1023) - 512;
+        lo = (lo - q[i]) >> 10;
+    }
+    hi += lo;                         // carry (0 or 1)
+    q[1] = ((hi + 512) & 1023) - 512;
+    q[0] = (hi - q[1]) >> 10;
+#pragma unroll
+    for (int i = 0; i < kS10; ++i) d[i] = int_to_float(q[i]);
+}
+
+// Balanced base-1024 digits of the double-float value (hi + lo) m, m a
+// power of two, |hi m| < 512 and |lo| <= ulp(hi) / 2 (normalised):
+// (hi + lo) m = sum_q d[q] 2^(-10q) + (error <= 2^-41 + 2^-45), |d[2]| <= 528,
+// the others <= 512.  Digits 0-2 come from hi alone, each step exact.  Then
+// lo joins the remainder r2 of digit 2 (units of 2^-20): S = r2 + lo m 2^20
+// (m20 = m 2^20) is exact when |lo m 2^20| >= 1/2, because hi then has no
+// bits below 2^-20 and r2 = 0, and rounds by at most 2^-25 otherwise; S's
+// integer part goes into digit 2 and its fraction, |f| <= 1/2 exactly, gives
+// digits 3 and 4.
+__device__ __forceinline__ void digits10_df(float hi, float lo, float m, float m20, float (&d)[kS10]) {
+    constexpr float C = 12582912.0f;
+    float q = __fsub_rn(__fmaf_rn(hi, m, C), C);
+    float r = __fmaf_rn(hi, m, -q);
+    d[0] = q;
+    q = __fsub_rn(__fmaf_rn(r, 1024.0f, C), C);
+    r = __fmaf_rn(r, 1024.0f, -q);
+    d[1] = q;
+    q = __fsub_rn(__fmaf_rn(r, 1024.0f, C), C);
+    r = __fmaf_rn(r, 1024.0f, -q);
+    const float S = __fmaf_rn(lo, m20, r);
+    const float li = __fsub_rn(__fadd_rn(S, C), C);
+    d[2] = __fadd_rn(q, li);
+    r = __fsub_rn(S, li);
+    q = __fsub_rn(__fmaf_rn(r, 1024.0f, C), C);
+    r = __fmaf_rn(r, 1024.0f, -q);
+    d[3] = q;
+    d[4] = __fsub_rn(__fmaf_rn(r, 1024.0f, C), C);
+}
+
+// V = x0 + x1 2^-10 + x2 2^-20 + x3 2^-30 + x4 2^-40 (x_L the level sums,
+// x0..x2 exact, |x_L| < 2^25) as an unevaluated sum hi + lo.  The first
+// addition is error-free with the fast two-sum (the larger magnitude comes
+// first, or the sum fits 24 bits since |x0| < 2^13 then); the second uses
+// the full two-sum; the rest err by < 2^-47 of |V|'s bound.
+__device__ __forceinline__ df combine5(const float (&x)[kS10][4], int e) {
+    const float s1 = __fmaf_rn(x[1][e], 0x1p-10f, x[0][e]);
+    const float e1 = __fmaf_rn(x[1][e], 0x1p-10f, -__fsub_rn(s1, x[0][e]));
+    const float b = __fmul_rn(x[2][e], 0x1p-20f);
+    const df s2 = dfx::two_sum(s1, b);
+    const float r = __fmaf_rn(x[3][e], 0x1p-30f, __fmaf_rn(x[4][e], 0x1p-40f, e1));
+    return {s2.hi, __fadd_rn(r, s2.lo)};
+}
+
 // x 2^-sh as hi + lo by bit operations: hi = the top 24 bits of x's
 // significand, lo = the next 23.  K = (896 + sh) << 23 turns the double's
 // exponent field (its low 9 bits, shifted into place with the significand)

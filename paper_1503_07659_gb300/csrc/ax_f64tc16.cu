@@ -1,10 +1,13 @@
-// FP64-accurate Ax for order N = 15 (n = 16) on BF16 tensor cores by exact
-// digit slicing, the method of the order-7 form (ax_f64tc.cuh): each operand
-// as six balanced base-256 digits against a power-of-two scale, the digit
-// pairs of levels 2..7 summed exactly in FP32 accumulators (one pair per
-// m16n8k16 product, K = 16 terms; a level gathers at most six pairs, so the
-// sums stay below 6 * 16 * 2^16 < 2^23), the level sums combined in
-// double-float.
+// FP64-accurate Ax for order N = 15 (n = 16) on FP16 tensor cores by exact
+// digit slicing (the Ozaki scheme, as in the order-7 form): each operand as
+// five balanced base-1024 digits (integers of magnitude <= 528, exact in
+// FP16) against a power-of-two scale, the 15 digit pairs of levels 0..4
+// summed in FP32 accumulators (one pair per m16n8k16 product, K = 16 terms;
+// levels 0..2 stay below 2^24 and are exact, levels 3 and 4 weigh 2^-30 and
+// 2^-40), the level sums combined in double-float.  Against six base-256
+// digits in BF16 (21 pairs) this takes 29 % fewer tensor-core products at
+// the same digit-extraction cost; at n = 16 the products are a third of the
+// kernel's time.
 //
 // One CTA of 16 warps per element, persistent over elements.  Warp w owns
 // plane k = w for every pointwise step, in the accumulator layout of an
@@ -35,8 +38,8 @@ constexpr int kThreads = 512;
 constexpr int kN3 = 4096;
 constexpr int kPlaneB = 512;                 // one 16 x 16 BF16 plane
 constexpr int kDigitB = 16 * kPlaneB;        // one digit of a 16^3 operand
-constexpr int kUD = kS * kDigitB;            // digits of u, later of y_t (48 KB)
-constexpr int kDD = kS * kPlaneB;            // digits of D (3 KB)
+constexpr int kUD = kS10 * kDigitB;            // digits of u, later of y_t (40 KB)
+constexpr int kDD = kS10 * kPlaneB;            // digits of D (2.5 KB)
 constexpr int kTB = kN3 * 8;                 // double-float per node: t-direction (32 KB)
 constexpr int kSB = kN3 * 8;                 // double-float per node: the s-gradient, parked (32 KB)
 constexpr int kGS = 3 * kN3 * 8;             // half of an element's G (96 KB)
@@ -56,15 +59,15 @@ __device__ __forceinline__ int pch(int p, int r, int c) {
 // writes and the plane owners' reads are both conflict-free.
 __device__ __forceinline__ int tslot(int k, int j, int ip) { return (k * 128 + j * 8 + ip) ^ (((j ^ k) & 1) << 2); }
 
-// acc[L] += A_a B_b over the 21 digit pairs a + b = L <= 5
-__device__ __forceinline__ void pairs21(float (&acc)[6][4], const uint32_t (&A)[kS][4], const uint32_t (&B)[kS][2]) {
+// acc[L] += A_a B_b over the 15 digit pairs a + b = L <= 4
+__device__ __forceinline__ void pairs15(float (&acc)[kS10][4], const uint32_t (&A)[kS10][4], const uint32_t (&B)[kS10][2]) {
 #pragma unroll
-    for (int L = 0; L < 6; ++L) acc[L][0] = acc[L][1] = acc[L][2] = acc[L][3] = 0.0f;
+    for (int L = 0; L < kS10; ++L) acc[L][0] = acc[L][1] = acc[L][2] = acc[L][3] = 0.0f;
 #pragma unroll
-    for (int L = 0; L < 6; ++L)
+    for (int L = 0; L < kS10; ++L)
 #pragma unroll
         for (int a = 0; a <= L; ++a)
-            mma::bf16_16816(acc[L], A[a][0], A[a][1], A[a][2], A[a][3], B[L - a][0], B[L - a][1]);
+            mma::f16_16816(acc[L], A[a][0], A[a][1], A[a][2], A[a][3], B[L - a][0], B[L - a][1]);
 }
 
 __device__ __forceinline__ int max16(const int *p) {
@@ -133,13 +136,13 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
     __syncthreads();
     eD = max16(sred);
     if (tid < 256) {
-        float d[kS];
-        digits_fp64(D[tid], eD, d);
+        float d[kS10];
+        digits10_fp64(D[tid], eD, d);
         const int a = tid >> 4, b = tid & 15;
 #pragma unroll
-        for (int p = 0; p < kS; ++p)
+        for (int p = 0; p < kS10; ++p)
             *reinterpret_cast<unsigned short *>(dd + p * kPlaneB + pch(0, a, b >> 3) + 2 * (b & 7)) =
-                (unsigned short)(__float_as_uint(d[p]) >> 16);
+                (unsigned short)(pack_f16(d[p], 0.0f) & 0xffffu);
     }
     __syncthreads();
 
@@ -191,15 +194,15 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
             for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    float d0[kS], d1[kS];
+                    float d0[kS10], d1[kS10];
                     const df a0 = split_g(uv[nt][h].x, habs(uv[nt][h].x), Ku, mw);
                     const df a1 = split_g(uv[nt][h].y, habs(uv[nt][h].y), Ku, mw);
                     const df n0 = dfx::fast_two_sum(a0.hi, a0.lo), n1 = dfx::fast_two_sum(a1.hi, a1.lo);
-                    digits_df(n0.hi, n0.lo, 128.0f, 8388608.0f, d0);
-                    digits_df(n1.hi, n1.lo, 128.0f, 8388608.0f, d1);
+                    digits10_df(n0.hi, n0.lo, 256.0f, 268435456.0f, d0);
+                    digits10_df(n1.hi, n1.lo, 256.0f, 268435456.0f, d1);
                     unsigned char *p = ud + pch(k, g + 8 * h, nt) + 4 * t;
 #pragma unroll
-                    for (int q = 0; q < kS; ++q) *reinterpret_cast<uint32_t *>(p + q * kDigitB) = pack_bf16(d0[q], d1[q]);
+                    for (int q = 0; q < kS10; ++q) *reinterpret_cast<uint32_t *>(p + q * kDigitB) = pack_f16(d0[q], d1[q]);
                 }
         }
         __syncthreads();
@@ -207,60 +210,60 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
         // ---- B: gradient on tensor cores
         df vr[8];   // r-gradient of the thread's nodes
         {
-            uint32_t fa[kS][4];   // D as A (rows j or k, K = l)
+            uint32_t fa[kS10][4];   // D as A (rows j or k, K = l)
 #pragma unroll
-            for (int p = 0; p < kS; ++p)
+            for (int p = 0; p < kS10; ++p)
                 mma::ldsm_x4(dd_s + p * kPlaneB + pch(0, r1, c1), fa[p][0], fa[p][1], fa[p][2], fa[p][3]);
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
                 // s: B = U_k (rows l, columns i), transposed load
-                uint32_t bu[kS][2];
+                uint32_t bu[kS10][2];
 #pragma unroll
-                for (int q = 0; q < kS; ++q) {
+                for (int q = 0; q < kS10; ++q) {
                     mma::ldsm_x2_t(ud_s + q * kDigitB + pch(k, rx, nt), bu[q][0], bu[q][1]);
                 }
-                float acc[6][4];
-                pairs21(acc, fa, bu);
+                float acc[kS10][4];
+                pairs15(acc, fa, bu);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const df v = combine_levels(acc, c);
+                    const df v = combine5(acc, c);
                     sb[(4 * nt + c) * kThreads + tid] = make_float2(v.hi, v.lo);
                 }
             }
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
                 // t (row j = k): B = U at row j (rows = planes l, columns i)
-                uint32_t bu[kS][2];
+                uint32_t bu[kS10][2];
 #pragma unroll
-                for (int q = 0; q < kS; ++q) {
+                for (int q = 0; q < kS10; ++q) {
                     mma::ldsm_x2_t(ud_s + q * kDigitB + pch(rx, k, nt), bu[q][0], bu[q][1]);
                 }
-                float acc[6][4];
-                pairs21(acc, fa, bu);
+                float acc[kS10][4];
+                pairs15(acc, fa, bu);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {   // rows kk = g + 8 h, columns i = 8 nt + 2 t, +1
-                    const df v0 = combine_levels(acc, 2 * h), v1 = combine_levels(acc, 2 * h + 1);
+                    const df v0 = combine5(acc, 2 * h), v1 = combine5(acc, 2 * h + 1);
                     tb[tslot(g + 8 * h, k, 4 * nt + t)] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
                 }
             }
         }
         {
             // r: A = U_k (rows j, K = l), B = D^T from D stored (rows i, columns l)
-            uint32_t au[kS][4];
+            uint32_t au[kS10][4];
 #pragma unroll
-            for (int q = 0; q < kS; ++q)
+            for (int q = 0; q < kS10; ++q)
                 mma::ldsm_x4(ud_s + q * kDigitB + pch(k, r1, c1), au[q][0], au[q][1], au[q][2], au[q][3]);
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
-                uint32_t bd[kS][2];
+                uint32_t bd[kS10][2];
 #pragma unroll
-                for (int p = 0; p < kS; ++p) {
+                for (int p = 0; p < kS10; ++p) {
                     mma::ldsm_x2(dd_s + p * kPlaneB + pch(0, 8 * nt + rr, mi & 1), bd[p][0], bd[p][1]);
                 }
-                float acc[6][4];
-                pairs21(acc, au, bd);
+                float acc[kS10][4];
+                pairs15(acc, au, bd);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) vr[4 * nt + c] = combine_levels(acc, c);
+                for (int c = 0; c < 4; ++c) vr[4 * nt + c] = combine5(acc, c);
             }
         }
         __syncthreads();
@@ -315,33 +318,33 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
         const int eR = eRraw == INT_MIN ? 0 : min(eRraw, kBadExp);
 
         // y_r digits, packed from the accumulator layout into A fragments
-        uint32_t ya[kS][4];
+        uint32_t ya[kS10][4];
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int q0 = 4 * nt + 2 * h;
-                float d0[kS], d1[kS];
-                digits_df(yr[q0].s, yr[q0].c, pow2f_or_zero(shA[q0] - eR + 134), pow2f_or_zero(shA[q0] - eR + 150), d0);
-                digits_df(yr[q0 + 1].s, yr[q0 + 1].c, pow2f_or_zero(shA[q0 + 1] - eR + 134),
-                          pow2f_or_zero(shA[q0 + 1] - eR + 150), d1);
+                float d0[kS10], d1[kS10];
+                digits10_df(yr[q0].s, yr[q0].c, pow2f_or_zero(shA[q0] - eR + 135), pow2f_or_zero(shA[q0] - eR + 155), d0);
+                digits10_df(yr[q0 + 1].s, yr[q0 + 1].c, pow2f_or_zero(shA[q0 + 1] - eR + 135),
+                          pow2f_or_zero(shA[q0 + 1] - eR + 155), d1);
 #pragma unroll
-                for (int d = 0; d < kS; ++d) ya[d][2 * nt + h] = pack_bf16(d0[d], d1[d]);
+                for (int d = 0; d < kS10; ++d) ya[d][2 * nt + h] = pack_f16(d0[d], d1[d]);
             }
 
         // ---- D_r: w_r = y_r D on tensor cores (B = D, rows l, columns i)
         df wr_[8];
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt) {
-            uint32_t bd[kS][2];
+            uint32_t bd[kS10][2];
 #pragma unroll
-            for (int p = 0; p < kS; ++p) {
+            for (int p = 0; p < kS10; ++p) {
                 mma::ldsm_x2_t(dd_s + p * kPlaneB + pch(0, rx, nt), bd[p][0], bd[p][1]);
             }
-            float acc[6][4];
-            pairs21(acc, ya, bd);
+            float acc[kS10][4];
+            pairs15(acc, ya, bd);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) wr_[4 * nt + c] = combine_levels(acc, c);
+            for (int c = 0; c < 4; ++c) wr_[4 * nt + c] = combine5(acc, c);
         }
 
         // ---- C2: G's second half (ss, st, tt): finish y_s, y_t
@@ -414,63 +417,63 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
 
         // y_s digits -> B fragments (movmatrix transposes each 8 x 8 block);
         // y_t digits -> shared memory (plane k)
-        uint32_t yb[kS][4];   // [digit][b0(nt0), b1(nt0), b0(nt1), b1(nt1)]
+        uint32_t yb[kS10][4];   // [digit][b0(nt0), b1(nt0), b0(nt1), b1(nt1)]
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int q0 = 4 * nt + 2 * h;
-                float d0[kS], d1[kS];
-                digits_df(ys[q0].s, ys[q0].c, pow2f_or_zero(shS[q0] - eS + 134), pow2f_or_zero(shS[q0] - eS + 150), d0);
-                digits_df(ys[q0 + 1].s, ys[q0 + 1].c, pow2f_or_zero(shS[q0 + 1] - eS + 134),
-                          pow2f_or_zero(shS[q0 + 1] - eS + 150), d1);
+                float d0[kS10], d1[kS10];
+                digits10_df(ys[q0].s, ys[q0].c, pow2f_or_zero(shS[q0] - eS + 135), pow2f_or_zero(shS[q0] - eS + 155), d0);
+                digits10_df(ys[q0 + 1].s, ys[q0 + 1].c, pow2f_or_zero(shS[q0 + 1] - eS + 135),
+                          pow2f_or_zero(shS[q0 + 1] - eS + 155), d1);
                 // block (rows j = 8h.., columns i = 8nt..) transposed: the B fragment of
                 // K rows l = 8h.. (b0 for h = 0, b1 for h = 1) of n-tile nt
 #pragma unroll
-                for (int d = 0; d < kS; ++d) yb[d][2 * nt + h] = mma::movm_t(pack_bf16(d0[d], d1[d]));
-                digits_df(yt[q0].s, yt[q0].c, pow2f_or_zero(shS[q0] - eT + 134), pow2f_or_zero(shS[q0] - eT + 150), d0);
-                digits_df(yt[q0 + 1].s, yt[q0 + 1].c, pow2f_or_zero(shS[q0 + 1] - eT + 134),
-                          pow2f_or_zero(shS[q0 + 1] - eT + 150), d1);
+                for (int d = 0; d < kS10; ++d) yb[d][2 * nt + h] = mma::movm_t(pack_f16(d0[d], d1[d]));
+                digits10_df(yt[q0].s, yt[q0].c, pow2f_or_zero(shS[q0] - eT + 135), pow2f_or_zero(shS[q0] - eT + 155), d0);
+                digits10_df(yt[q0 + 1].s, yt[q0 + 1].c, pow2f_or_zero(shS[q0 + 1] - eT + 135),
+                          pow2f_or_zero(shS[q0 + 1] - eT + 155), d1);
                 unsigned char *p = ud + pch(k, g + 8 * h, nt) + 4 * t;
 #pragma unroll
-                for (int d = 0; d < kS; ++d) *reinterpret_cast<uint32_t *>(p + d * kDigitB) = pack_bf16(d0[d], d1[d]);
+                for (int d = 0; d < kS10; ++d) *reinterpret_cast<uint32_t *>(p + d * kDigitB) = pack_f16(d0[d], d1[d]);
             }
         __syncthreads();
 
         // ---- D_s, D_t: A = D^T (from D stored rows l, columns j: transposed load)
         df ws_[8];
         {
-            uint32_t fat[kS][4];
+            uint32_t fat[kS10][4];
 #pragma unroll
-            for (int p = 0; p < kS; ++p)
+            for (int p = 0; p < kS10; ++p)
                 mma::ldsm_x4_t(dd_s + p * kPlaneB + pch(0, r2, c2), fat[p][0], fat[p][1], fat[p][2], fat[p][3]);
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
-                uint32_t bb[kS][2];
+                uint32_t bb[kS10][2];
 #pragma unroll
-                for (int d = 0; d < kS; ++d) {
+                for (int d = 0; d < kS10; ++d) {
                     bb[d][0] = yb[d][2 * nt];
                     bb[d][1] = yb[d][2 * nt + 1];
                 }
-                float acc[6][4];
-                pairs21(acc, fat, bb);
+                float acc[kS10][4];
+                pairs15(acc, fat, bb);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) ws_[4 * nt + c] = combine_levels(acc, c);
+                for (int c = 0; c < 4; ++c) ws_[4 * nt + c] = combine5(acc, c);
             }
             if (e + gridDim.x < E) load_u(e + gridDim.x);   // next element's u, in flight through D_t and E
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
                 // row j = k: B = y_t digits at row j (rows = planes l, columns i)
-                uint32_t bt[kS][2];
+                uint32_t bt[kS10][2];
 #pragma unroll
-                for (int q = 0; q < kS; ++q) {
+                for (int q = 0; q < kS10; ++q) {
                     mma::ldsm_x2_t(ud_s + q * kDigitB + pch(rx, k, nt), bt[q][0], bt[q][1]);
                 }
-                float acc[6][4];
-                pairs21(acc, fat, bt);
+                float acc[kS10][4];
+                pairs15(acc, fat, bt);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const df v0 = combine_levels(acc, 2 * h), v1 = combine_levels(acc, 2 * h + 1);
+                    const df v0 = combine5(acc, 2 * h), v1 = combine5(acc, 2 * h + 1);
                     tb[tslot(g + 8 * h, k, 4 * nt + t)] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
                 }
             }
@@ -478,7 +481,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
         __syncthreads();
 
         // ---- E: w = 2^SH_r V_r + 2^SH_s V_s + 2^SH_t V_t, stored
-        const int base = (eU - 1022) + 2 * (eD - 1022) - 126 - 32;
+        const int base = (eU - 1022) + 2 * (eD - 1022) - 126 - 36;
         const int SHr = base + eR, SHs = base + eS, SHt = base + eT;
         const int SHm = max(SHr, max(SHs, SHt));
 #pragma unroll

@@ -2,15 +2,18 @@
 FP64-accurate form, independent of the GPU and of its arithmetic order.
 
 The method, in exact arithmetic: each operand of a contraction (u, D, and
-the intermediate [wr ws wt] = G grad u) is rounded to six balanced base-256
-digits against one power-of-two scale per element (D: one for the matrix),
-the digit products of levels p + q <= 7 are summed exactly, and the levels
-are combined.  This test evaluates that model in float64 (rounding each
-operand at 2^-48 of its scale and dropping the levels above 7, which is
-what the digits represent) and compares it with the FP64 oracle: the
-model's error is the method's own error floor, which the GPU parity tests'
-bound (2e-13 of ||w||_inf) must exceed.  Five digits per operand must miss
-the FP64 requirement, so the sixth is needed.
+the intermediate [wr ws wt] = G grad u) is rounded to balanced digits
+against one power-of-two scale per element (D: one for the matrix), the
+digit products of the kept levels are summed exactly, and the levels are
+combined.  Two digit systems are used: six base-256 digits (BF16 operands,
+levels 0..5 kept, order 7) and five base-1024 digits whose leading digit
+takes one bit less, so that no digit exceeds 512 (FP16 operands, levels
+0..4 kept, order 15).  This test evaluates that model in float64 (rounding
+each operand at the last digit and dropping the levels above the kept ones,
+which is what the digits represent) and compares it with the FP64 oracle:
+the model's error is the method's own error floor, which the GPU parity
+tests' bound (2e-13 of ||w||_inf) must exceed.  One digit fewer in either
+system must miss the FP64 requirement.
 """
 import numpy as np
 import pytest
@@ -25,47 +28,52 @@ def _scale(x, axis=None):
     return 2.0 ** (np.floor(np.log2(m)) + 1)
 
 
-def _expand(x, s, ndig):
-    """The ndig balanced base-256 digits of x / s as integer-valued arrays."""
-    M = np.round(x / s * 2.0 ** (8 * ndig)).astype(np.int64)
+def _expand(x, s, ndig, bits=8, head=0):
+    """The ndig balanced base-2^bits digits of x / s as integer-valued
+    arrays, the leading digit taking bits - head bits."""
+    M = np.round(x / s * 2.0 ** (bits * ndig - head)).astype(np.int64)
+    half, mask = 1 << (bits - 1), (1 << bits) - 1
     d = []
     for _ in range(ndig - 1):
-        lo = ((M + 128) & 255) - 128
+        lo = ((M + half) & mask) - half
         d.append(lo)
-        M = (M - lo) >> 8
+        M = (M - lo) >> bits
     d.append(M)
     return d[::-1]   # most significant first
 
 
-def _contract(Dd, sD, ud, su, ndig, path):
-    """sum_l D[.,l] u[..l..] from digit expansions with levels p + q <= ndig + 1."""
+def _contract(Dd, sD, ud, su, ndig, path, bits=8, head=0):
+    """sum_l D[.,l] u[..l..] from digit expansions with levels p + q <= ndig - 1."""
     out = 0.0
     for p in range(ndig):
         for q in range(ndig):
             if p + q > ndig - 1:
                 continue
-            out = out + np.einsum(path, Dd[p].astype(np.float64), ud[q].astype(np.float64)) * 2.0 ** (-8 * (p + q + 2))
+            w = 2.0 ** (-(bits * (p + q + 2) - 2 * head))
+            out = out + np.einsum(path, Dd[p].astype(np.float64), ud[q].astype(np.float64)) * w
     return out * sD * su
 
 
-def _slice_ax(u, G, D, ndig):
+def _slice_ax(u, G, D, ndig, bits=8, head=0):
     E = u.shape[0]
+    kw = dict(bits=bits, head=head)
     sD = float(_scale(D))
-    Dd = _expand(D, sD, ndig)
+    Dd = _expand(D, sD, ndig, **kw)
     su = _scale(u.reshape(E, -1), axis=1).reshape(E, 1, 1, 1)
-    ud = _expand(u, su, ndig)
-    ur = _contract(Dd, sD, ud, su, ndig, "il,ekjl->ekji")
-    us = _contract(Dd, sD, ud, su, ndig, "jl,ekli->ekji")
-    ut = _contract(Dd, sD, ud, su, ndig, "kl,elji->ekji")
+    ud = _expand(u, su, ndig, **kw)
+    ur = _contract(Dd, sD, ud, su, ndig, "il,ekjl->ekji", **kw)
+    us = _contract(Dd, sD, ud, su, ndig, "jl,ekli->ekji", **kw)
+    ut = _contract(Dd, sD, ud, su, ndig, "kl,elji->ekji", **kw)
     g = [G[:, a] for a in range(6)]
     wr = g[0] * ur + g[1] * us + g[2] * ut
     ws = g[1] * ur + g[3] * us + g[4] * ut
     wt = g[2] * ur + g[4] * us + g[5] * ut
     sw = np.maximum(np.maximum(_scale(wr.reshape(E, -1), axis=1), _scale(ws.reshape(E, -1), axis=1)),
                     _scale(wt.reshape(E, -1), axis=1)).reshape(E, 1, 1, 1)
-    xr, xs, xt = (_expand(a, sw, ndig) for a in (wr, ws, wt))
-    return (_contract(Dd, sD, xr, sw, ndig, "li,ekjl->ekji") + _contract(Dd, sD, xs, sw, ndig, "lj,ekli->ekji")
-            + _contract(Dd, sD, xt, sw, ndig, "lk,elji->ekji"))
+    xr, xs, xt = (_expand(a, sw, ndig, **kw) for a in (wr, ws, wt))
+    return (_contract(Dd, sD, xr, sw, ndig, "li,ekjl->ekji", **kw)
+            + _contract(Dd, sD, xs, sw, ndig, "lj,ekli->ekji", **kw)
+            + _contract(Dd, sD, xt, sw, ndig, "lk,elji->ekji", **kw))
 
 
 def _rel(w, ref):
@@ -115,3 +123,40 @@ def test_constant_field_floor(oracle_mod, mesh):
     w1 = _slice_ax(u1, mesh.G.numpy(), mesh.D.numpy(), 6)
     wr = oracle_mod.sem_ax(mesh.u.numpy(), mesh.G.numpy(), mesh.D.numpy())
     assert np.max(np.abs(w1)) <= 1e-12 * np.max(np.abs(wr))
+
+
+@pytest.fixture(scope="module")
+def mesh16():
+    return si.make_mesh(np.random.default_rng(91), 2, 15)
+
+
+def test_base1024_digits_are_balanced_and_exact(mesh16):
+    u = mesh16.u.numpy()
+    s = _scale(u)
+    d = _expand(u, s, 5, bits=10, head=1)
+    assert all(np.abs(x).max() <= 512 for x in d)
+    val = sum(x.astype(np.float64) * 2.0 ** -(10 * (k + 1) - 1) for k, x in enumerate(d)) * s
+    assert np.max(np.abs(val - u)) <= 2.0 ** -50 * s
+
+
+def test_base1024_leading_level_sums_fit_the_fp32_significand(mesh16):
+    """K = 16: levels 0..2 sum at most three digit pairs of magnitude
+    <= 512 x 512, below 2^24, so their FP32 accumulation is exact."""
+    D = mesh16.D.numpy()
+    u = mesh16.u.numpy()
+    Dd = _expand(D, float(_scale(D)), 5, bits=10, head=1)
+    ud = _expand(u, _scale(u), 5, bits=10, head=1)
+    for L in range(3):
+        acc = 0
+        for p in range(L + 1):
+            acc = acc + np.einsum("il,ekjl->ekji", np.abs(Dd[p]), np.abs(ud[L - p]))
+        assert acc.max() < 2 ** 24
+
+
+def test_five_base1024_digits_meet_the_fp64_bound_and_four_do_not(oracle_mod, mesh16):
+    u, G, D = mesh16.u.numpy(), mesh16.G.numpy(), mesh16.D.numpy()
+    ref = oracle_mod.sem_ax(u, G, D)
+    e5 = _rel(_slice_ax(u, G, D, 5, bits=10, head=1), ref)
+    e4 = _rel(_slice_ax(u, G, D, 4, bits=10, head=1), ref)
+    assert e5 <= 2e-13
+    assert e4 > 1e-12
