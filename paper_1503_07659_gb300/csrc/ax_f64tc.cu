@@ -1,35 +1,35 @@
-// FP64-accurate Ax with the six contractions on BF16 tensor cores by exact
+// FP64-accurate Ax with the six contractions on FP16 tensor cores by exact
 // slicing (the Ozaki scheme: Ozaki, Ogita, Oishi & Rump, Numer. Algorithms
 // 59, 2012; its tensor-core forms: Mukunoki, Ozaki, Ogita & Imamura, ICCS
 // 2020; Ootomo, Ozaki & Yokota, IJHPCA 2024).  Order n = 8 (N = 7).
 //
 // Slicing.  An operand x with one power-of-two scale 2^s per element is
-// written in balanced base-256 digits,
-//     x = 2^s sum_{q=1..6} d_q 2^(-8q) + (error <= 2^(s-49)),
-// with every d_q an integer of magnitude <= 256, which BF16 holds exactly.
-// A digit of D times a digit of u is an integer below 2^16 in magnitude; one
-// m16n8k16 product sums 16 of them (two digit pairs of the same level, 8
-// terms each), and one level L = p + q collects at most six pairs, so every
-// FP32 accumulator holds an integer below 2^22: the tensor-core sums are
-// exact.  Levels L = 2..7 are kept (21 digit pairs per contraction, 9
+// written in balanced base-1024 digits, the leading one taking nine bits,
+//     x = 2^s sum_{q=0..4} d_q 2^(-10q - 9) + (error <= 2^(s-50)),
+// with every d_q an integer of magnitude <= 528, which FP16 holds exactly.
+// A digit of D times a digit of u is an integer of magnitude below 2^18.1;
+// one m16n8k16 product sums 16 of them (two digit pairs of the same level,
+// 8 terms each), and one level L = p + q collects at most five pairs, so
+// every FP32 accumulator holds an integer below 2^24: the tensor-core sums
+// are exact.  Levels L = 0..4 are kept (15 digit pairs per contraction, 7
 // m16n8k16 + 3 m16n8k8 products per 16 x 8 output tile); the dropped levels
-// weigh less than 2^-48 of the element's scale.  The six level sums of an
+// weigh less than 2^-48 of the element's scale.  The five level sums of an
 // output are combined in double-float (an unevaluated sum of two floats).
 //
 // Per element (one CTA of 4 warps; warp w owns the planes k = 2w, 2w+1 for
 // every pointwise step, in the layout of the m16n8 accumulator of the
 // r-direction tile; u and G of the CTA's next element are fetched by TMA
 // bulk copies into shared memory while the current one finishes):
-//   A  u (FP64) -> per-element scale -> 6 BF16 digit planes in shared memory;
+//   A  u (FP64) -> per-element scale -> 5 FP16 digit planes in shared memory;
 //   B  ur, us, ut on tensor cores (B operand: the digits of D^T, held in
 //      registers for the CTA's lifetime); ur stays in registers, us and ut
 //      go through two swizzled double-float buffers;
 //   C  y = G [ur us ut] in double-float with G split hi + lo by bit
 //      operations after a per-node power-of-two scale; per-element scale of
-//      y; 3 x 6 digit planes;
+//      y; 3 x 5 digit planes;
 //   D  w_r, w_s, w_t on tensor cores (B operand: the digits of D);
 //   E  w = (w_r + w_s + w_t) * 2^(scales) in FP64, stored.
-// The only FP64 instructions are the final add and scale of each node.
+// The only FP64 instruction is the final add of each node.
 // Inputs with Inf or NaN make their element's output NaN.
 #include "ax_f64tc.cuh"
 
@@ -37,9 +37,9 @@ namespace semax {
 namespace oz {
 
 constexpr int kThreads = 128;                // one element per CTA pass
-constexpr int kPlane = 128;                  // bytes per 8 x 8 BF16 plane (rows XOR-swizzled)
+constexpr int kPlane = 128;                  // bytes per 8 x 8 FP16 plane (rows XOR-swizzled)
 constexpr int kSlice = 8 * kPlane;           // one digit of an 8^3 operand
-constexpr int kDigBytes = 3 * kS * kSlice;   // digits of wr, ws, wt (u reuses the first six)
+constexpr int kDigBytes = 3 * kS10 * kSlice; // digits of wr, ws, wt (u reuses the first five)
 constexpr int kBufBytes = 512 * 8;           // one double-float per node
 constexpr int kGBytes = 6 * 512 * 8;         // one element's G (FP64), staged
 constexpr int kUBytes = 512 * 8;             // one element's u (FP64), staged
@@ -51,31 +51,36 @@ constexpr size_t kSmem = kDigBytes + 2 * kBufBytes + kGBytes + kUBytes + 16 * si
 __device__ __forceinline__ int prow(int p, int j) { return p * kPlane + ((j ^ p) << 4); }
 
 // One 16 x 8 output tile of a contraction along direction DIR (0: r / i,
-// 1: s / j, 2: t / k) for warp w, all 21 digit pairs of levels 2..7.
+// 1: s / j, 2: t / k) for warp w, all 15 digit pairs of levels 0..4.
 // base: shared address of digit 0 of the operand; Bf[p]: the B fragment of
 // digit p of D^T (gradient) or D (transposed).  Accumulator rows:
 //   DIR 0: (k, j) = (2w + m / 8, m % 8), columns i;
 //   DIR 1: (k, i) = (2w + m / 8, m % 8), columns j;
 //   DIR 2: (j, i) = (2w + m / 8, m % 8), columns k.
 template <int DIR>
-__device__ __forceinline__ void contract(uint32_t base, int warp, int lane, const uint32_t (&Bf)[kS],
-                                         float (&acc)[6][4]) {
+__device__ __forceinline__ void contract(uint32_t base, int warp, int lane, const uint32_t (&Bf)[kS10],
+                                         float (&acc)[kS10][4]) {
     const int mi = lane >> 3, rr = lane & 7;
     const int blk = 2 * warp + (mi & 1);
+    // x4: digits q, q + 1 (lanes 16-31 address the second); x2: digit 4 (lanes 0-15)
     const uint32_t addr = base + (mi >> 1) * kSlice + (DIR == 2 ? prow(rr, blk) : prow(blk, rr));
-    uint32_t a[kS][2];
+    uint32_t a[kS10][2];
 #pragma unroll
-    for (int q = 0; q < kS; q += 2) {
+    for (int q = 0; q < 4; q += 2) {
         if (DIR == 0)
             mma::ldsm_x4(addr + q * kSlice, a[q][0], a[q][1], a[q + 1][0], a[q + 1][1]);
         else
             mma::ldsm_x4_t(addr + q * kSlice, a[q][0], a[q][1], a[q + 1][0], a[q + 1][1]);
     }
+    if (DIR == 0)
+        mma::ldsm_x2(addr + 4 * kSlice, a[4][0], a[4][1]);
+    else
+        mma::ldsm_x2_t(addr + 4 * kSlice, a[4][0], a[4][1]);
 #pragma unroll
-    for (int l = 0; l < 6; ++l) acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = 0.0f;
-    // level index L - 2 = p + q for D digit p and operand digit q (0-based)
-#define OZ_K8(L, p, q) mma::bf16_1688(acc[L], a[q][0], a[q][1], Bf[p])
-#define OZ_K16(L, p1, q1, p2, q2) mma::bf16_16816(acc[L], a[q1][0], a[q1][1], a[q2][0], a[q2][1], Bf[p1], Bf[p2])
+    for (int l = 0; l < kS10; ++l) acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = 0.0f;
+    // level L = p + q for D digit p and operand digit q (0-based)
+#define OZ_K8(L, p, q) mma::f16_1688(acc[L], a[q][0], a[q][1], Bf[p])
+#define OZ_K16(L, p1, q1, p2, q2) mma::f16_16816(acc[L], a[q1][0], a[q1][1], a[q2][0], a[q2][1], Bf[p1], Bf[p2])
     OZ_K8(0, 0, 0);
     OZ_K16(1, 0, 1, 1, 0);
     OZ_K16(2, 0, 2, 1, 1);
@@ -85,9 +90,6 @@ __device__ __forceinline__ void contract(uint32_t base, int warp, int lane, cons
     OZ_K16(4, 0, 4, 1, 3);
     OZ_K16(4, 2, 2, 3, 1);
     OZ_K8(4, 4, 0);
-    OZ_K16(5, 0, 5, 1, 4);
-    OZ_K16(5, 2, 3, 3, 2);
-    OZ_K16(5, 4, 1, 5, 0);
 #undef OZ_K8
 #undef OZ_K16
 }
@@ -104,10 +106,10 @@ __device__ __forceinline__ int tidx(int k, int j, int i) {
 
 // Write the s- or t-direction tile of warp w (levels combined) to its buffer.
 template <int DIR>
-__device__ __forceinline__ void store_tile(float2 *buf, const float (&acc)[6][4], int warp, int g, int t) {
+__device__ __forceinline__ void store_tile(float2 *buf, const float (&acc)[kS10][4], int warp, int g, int t) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const df v0 = combine_levels(acc, 2 * h), v1 = combine_levels(acc, 2 * h + 1);
+        const df v0 = combine5_k8(acc, 2 * h), v1 = combine5_k8(acc, 2 * h + 1);
         if (DIR == 1) {   // rows (k = 2w + h, i = g), columns j = 2t, 2t + 1: adjacent in [k][i][j]
             *reinterpret_cast<float4 *>(buf + sidx(2 * warp + h, 2 * t, g)) = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
         } else {          // rows (j = 2w + h, i = g), columns k = 2t, 2t + 1
@@ -152,17 +154,17 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
     int eD = 1;
     for (int q = lane; q < 64; q += 32) eD = max(eD, max(bexp(D[q]), 1));
     eD = __reduce_max_sync(0xffffffffu, eD);
-    uint32_t fg[kS], ft[kS];
+    uint32_t fg[kS10], ft[kS10];
     {
-        float x0[kS], x1[kS];
-        digits_fp64(D[g * 8 + 2 * t], eD, x0);
-        digits_fp64(D[g * 8 + 2 * t + 1], eD, x1);
+        float x0[kS10], x1[kS10];
+        digits10_fp64(D[g * 8 + 2 * t], eD, x0);
+        digits10_fp64(D[g * 8 + 2 * t + 1], eD, x1);
 #pragma unroll
-        for (int p = 0; p < kS; ++p) fg[p] = pack_bf16(x0[p], x1[p]);
-        digits_fp64(D[(2 * t) * 8 + g], eD, x0);
-        digits_fp64(D[(2 * t + 1) * 8 + g], eD, x1);
+        for (int p = 0; p < kS10; ++p) fg[p] = pack_f16(x0[p], x1[p]);
+        digits10_fp64(D[(2 * t) * 8 + g], eD, x0);
+        digits10_fp64(D[(2 * t + 1) * 8 + g], eD, x1);
 #pragma unroll
-        for (int p = 0; p < kS; ++p) ft[p] = pack_bf16(x0[p], x1[p]);
+        for (int p = 0; p < kS10; ++p) ft[p] = pack_f16(x0[p], x1[p]);
     }
 
     unsigned parity = 0;
@@ -189,38 +191,38 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         }
         const int eU = max4(sred);
         // u 2^-(eU - 1023) in (-2, 2) split hi + lo (47 bits), normalised; its
-        // digits at t = 128 u 2^-(eU - 1023) = 256 u 2^-(eU - 1022)
+        // digits at t = 256 u 2^-(eU - 1023) = 512 u 2^-(eU - 1022)
         const unsigned Ku = (unsigned)(eU - 127) << 23;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            float d0[kS], d1[kS];
+            float d0[kS10], d1[kS10];
             const unsigned mw = (unsigned)max(eU - 126, 1) << 20;
             const df a0 = split_g(uv[h].x, habs(uv[h].x), Ku, mw);
             const df a1 = split_g(uv[h].y, habs(uv[h].y), Ku, mw);
             const df n0 = dfx::fast_two_sum(a0.hi, a0.lo), n1 = dfx::fast_two_sum(a1.hi, a1.lo);
-            digits_df(n0.hi, n0.lo, 128.0f, 8388608.0f, d0);
-            digits_df(n1.hi, n1.lo, 128.0f, 8388608.0f, d1);
+            digits10_df(n0.hi, n0.lo, 256.0f, 268435456.0f, d0);
+            digits10_df(n1.hi, n1.lo, 256.0f, 268435456.0f, d1);
             unsigned char *p = dig + prow(2 * warp + h, g) + 4 * t;
 #pragma unroll
-            for (int q = 0; q < kS; ++q) *reinterpret_cast<uint32_t *>(p + q * kSlice) = pack_bf16(d0[q], d1[q]);
+            for (int q = 0; q < kS10; ++q) *reinterpret_cast<uint32_t *>(p + q * kSlice) = pack_f16(d0[q], d1[q]);
         }
         __syncthreads();
 
         // ---- B: gradient on tensor cores
         df vr[4];
         {
-            float acc[6][4];
+            float acc[kS10][4];
             contract<0>(dig_s, warp, lane, fg, acc);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) vr[q] = combine_levels(acc, q);
+            for (int q = 0; q < 4; ++q) vr[q] = combine5_k8(acc, q);
         }
         {
-            float acc[6][4];
+            float acc[kS10][4];
             contract<1>(dig_s, warp, lane, fg, acc);
             store_tile<1>(bs, acc, warp, g, t);
         }
         {
-            float acc[6][4];
+            float acc[kS10][4];
             contract<2>(dig_s, warp, lane, fg, acc);
             store_tile<2>(bt, acc, warp, g, t);
         }
@@ -284,18 +286,18 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             unsigned char *p = dig + prow(2 * warp + h, g) + 4 * t;
-            const float m0 = pow2f_or_zero(shn[2 * h] - eW + 134);       // |y 2^(sh - eW + 126)| < 1
-            const float m1 = pow2f_or_zero(shn[2 * h + 1] - eW + 134);
-            const float m0s = pow2f_or_zero(shn[2 * h] - eW + 150);      // m 2^16, finite when m is clamped
-            const float m1s = pow2f_or_zero(shn[2 * h + 1] - eW + 150);
+            const float m0 = pow2f_or_zero(shn[2 * h] - eW + 135);       // |y 2^(sh - eW + 126)| < 1
+            const float m1 = pow2f_or_zero(shn[2 * h + 1] - eW + 135);
+            const float m0s = pow2f_or_zero(shn[2 * h] - eW + 155);      // m 2^20, finite when m is clamped
+            const float m1s = pow2f_or_zero(shn[2 * h + 1] - eW + 155);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                float d0[kS], d1[kS];
-                digits_df(y[2 * h][a].s, y[2 * h][a].c, m0, m0s, d0);
-                digits_df(y[2 * h + 1][a].s, y[2 * h + 1][a].c, m1, m1s, d1);
+                float d0[kS10], d1[kS10];
+                digits10_df(y[2 * h][a].s, y[2 * h][a].c, m0, m0s, d0);
+                digits10_df(y[2 * h + 1][a].s, y[2 * h + 1][a].c, m1, m1s, d1);
 #pragma unroll
-                for (int q = 0; q < kS; ++q)
-                    *reinterpret_cast<uint32_t *>(p + (a * kS + q) * kSlice) = pack_bf16(d0[q], d1[q]);
+                for (int q = 0; q < kS10; ++q)
+                    *reinterpret_cast<uint32_t *>(p + (a * kS10 + q) * kSlice) = pack_f16(d0[q], d1[q]);
             }
         }
         __syncthreads();
@@ -303,26 +305,26 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         // ---- D: transposed contractions on tensor cores
         df vo[4];
         {
-            float acc[6][4];
+            float acc[kS10][4];
             contract<0>(dig_s, warp, lane, ft, acc);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) vo[q] = combine_levels(acc, q);
+            for (int q = 0; q < 4; ++q) vo[q] = combine5_k8(acc, q);
         }
         {
-            float acc[6][4];
-            contract<1>(dig_s + kS * kSlice, warp, lane, ft, acc);
+            float acc[kS10][4];
+            contract<1>(dig_s + kS10 * kSlice, warp, lane, ft, acc);
             store_tile<1>(bs, acc, warp, g, t);
         }
         {
-            float acc[6][4];
-            contract<2>(dig_s + 2 * kS * kSlice, warp, lane, ft, acc);
+            float acc[kS10][4];
+            contract<2>(dig_s + 2 * kS10 * kSlice, warp, lane, ft, acc);
             store_tile<2>(bt, acc, warp, g, t);
         }
         __syncthreads();
 
         // ---- E: sum, undo the scales, store
-        // w = 2^((eU - 1022) + 2 (eD - 1022) + (eW - 126) - 32) V_out
-        const int SH = (eU - 1022) + 2 * (eD - 1022) + (eW - 126) - 32;
+        // w = 2^((eU - 1022) + 2 (eD - 1022) + (eW - 126) - 36) V_out
+        const int SH = (eU - 1022) + 2 * (eD - 1022) + (eW - 126) - 36;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = 2 * warp + h, nb = k * 64 + g * 8 + 2 * t;

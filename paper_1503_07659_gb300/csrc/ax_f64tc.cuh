@@ -227,6 +227,18 @@ __device__ __forceinline__ df combine5(const float (&x)[kS10][4], int e) {
     return {s2.hi, __fadd_rn(r, s2.lo)};
 }
 
+// combine5 for K = 8 terms per product: the level sums then stay below 2^23
+// (levels 0..2) and both leading additions are error-free with the fast
+// two-sum (when |s1| < |x2| 2^-20 < 2^3, the sum needs at most 24 bits).
+__device__ __forceinline__ df combine5_k8(const float (&x)[kS10][4], int e) {
+    const float s1 = __fmaf_rn(x[1][e], 0x1p-10f, x[0][e]);
+    const float e1 = __fmaf_rn(x[1][e], 0x1p-10f, -__fsub_rn(s1, x[0][e]));
+    const float s2 = __fmaf_rn(x[2][e], 0x1p-20f, s1);
+    const float e2 = __fmaf_rn(x[2][e], 0x1p-20f, -__fsub_rn(s2, s1));
+    const float r = __fmaf_rn(x[3][e], 0x1p-30f, __fmaf_rn(x[4][e], 0x1p-40f, e1));
+    return {s2, __fadd_rn(r, e2)};
+}
+
 // x 2^-sh as hi + lo by bit operations: hi = the top 24 bits of x's
 // significand, lo = the next 23.  K = (896 + sh) << 23 turns the double's
 // exponent field (its low 9 bits, shifted into place with the significand)

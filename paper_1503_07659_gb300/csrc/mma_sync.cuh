@@ -55,6 +55,12 @@ __device__ __forceinline__ void f16_16816(float (&c)[4], uint32_t a0, uint32_t a
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
+// c += A (16 x 8, row) B (8 x 8, col), FP16 in, FP32 accumulate
+__device__ __forceinline__ void f16_1688(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a0), "r"(a1), "r"(b0));
+}
 
 }  // namespace mma
 }  // namespace semax
