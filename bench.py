@@ -455,8 +455,8 @@ def run_ours(args, rank, world):
              "us_per_call": t_t * 1e6, "rel_err_vs_f64": rel_err_gpu(semax, wt, w),
              "energy_rel_err": energy_rel_gpu(semax, mesh.u, wt, w),
              "hbm_frac_of_measured": world * dofs * bytes_per_node(8) / t_t / 1e9 / load_peaks().get("hbm_gbs", 6786.6),
-             "bound": "instruction issue (tensor pipe ~17 % busy; digit extraction and double-float work on the CUDA cores)",
-             "arith": "contractions on BF16 tensor cores by exact base-256 digit slicing (levels 2..7), "
+             "bound": "instruction issue (tensor pipe below 20 % busy; digit extraction and double-float work on the CUDA cores)",
+             "arith": "contractions on FP16 tensor cores by exact base-1024 digit slicing (5 digits, levels 0..4), "
                       "double-float level sums and geometric factor; FP64 in/out"}
     del wt
     # Helmholtz form w = h1 A u + h2 B u on the same workload (72 B/node)

@@ -103,21 +103,21 @@ int sem_ax_f64x(int64_t E, int N, const double *u, const double *G, const double
                 double *w, void *stream);
 
 /* FP64 inputs and outputs, FP64-accurate result; the six contractions run
- * on BF16 tensor cores by exact slicing (the Ozaki scheme).  Per element, u
+ * on FP16 tensor cores by exact slicing (the Ozaki scheme).  Per element, u
  * and the intermediate [wr ws wt] are scaled by a power of two and written
- * as six balanced base-256 digits (integers of magnitude <= 256, exact in
- * BF16), D likewise once per call; the digit products of levels 2..7 (21
+ * as five balanced base-1024 digits (integers of magnitude <= 528, exact in
+ * FP16), D likewise once per call; the digit products of levels 0..4 (15
  * pairs per contraction) are summed on tensor cores in FP32 accumulators
- * that stay below 2^22 (n = 8) or 2^23 (n = 16) and are therefore exact,
- * and the level sums are
- * combined in double-float.  The geometric-factor multiply runs in
- * double-float with G split by bit operations after a per-node power-of-two
- * scale.  Error against the FP64 definition ~1e-14 of ||w||_inf; entries
- * more than ~2^48 times smaller than their element's largest count only to
- * that precision.  An element with an Inf or NaN input returns NaN in every
+ * (exact: below 2^24 at n = 8, and for levels 0..2 at n = 16, whose levels
+ * 3 and 4 weigh 2^-30 and 2^-40), and the level sums are combined in
+ * double-float.  The geometric-factor multiply runs in double-float with G
+ * split by bit operations after a per-node power-of-two scale.  Error
+ * against the FP64 definition ~1e-13 of ||w||_inf or less; entries more
+ * than ~2^48 times smaller than their element's largest count only to that
+ * precision.  An element with an Inf or NaN input returns NaN in every
  * entry.  Orders N = 7 (n = 8) and N = 15 (n = 16) on tensor cores, any
  * D; other orders are computed by sem_ax_f64x.  N = 15 launches one
- * persistent 512-thread block per SM with 216 KB of shared memory. */
+ * persistent 512-thread block per SM with 207 KB of shared memory. */
 int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const double *D,
                  double *w, void *stream);
 

@@ -73,7 +73,7 @@ def sem_ax_f64x(u: torch.Tensor, G: torch.Tensor, D: torch.Tensor, w: torch.Tens
 
 def sem_ax_f64tc(u: torch.Tensor, G: torch.Tensor, D: torch.Tensor, w: torch.Tensor | None = None,
                  stream=None) -> torch.Tensor:
-    """FP64 in/out, FP64-accurate; contractions on BF16 tensor cores by exact digit slicing (N = 7)."""
+    """FP64 in/out, FP64-accurate; contractions on FP16 tensor cores by exact digit slicing (N = 7, 15)."""
     E, N = _dims(u, D)
     w = _out(w, u)
     check(_lib.lib().sem_ax_f64tc(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _stream(stream)), "sem_ax_f64tc")

@@ -1,8 +1,9 @@
 // Device helpers of the FP64-accurate tensor-core forms (exact digit
 // slicing, the Ozaki scheme): TMA bulk copies and mbarrier waits, balanced
-// base-256 digits of FP64 and double-float values, the double-float
-// combination of exact level sums, the bit-level split of FP64 into hi + lo
-// floats, and the double-float 3-term dot product of the geometric factor.
+// base-1024 digits (exact in FP16) of FP64 and double-float values, the
+// double-float combination of the level sums, the bit-level split of FP64
+// into hi + lo floats, and the double-float 3-term dot product of the
+// geometric factor.
 #pragma once
 
 #include <algorithm>
@@ -18,7 +19,6 @@ using dfx::acc2;
 using dfx::df;
 using mma::smem_u32;
 
-constexpr int kS = 6;                        // digits per operand
 constexpr int kBadExp = 1 << 20;             // marks a non-finite input in the exponent reductions
 
 // TMA bulk copy global -> shared, completing on an mbarrier transaction
@@ -53,91 +53,12 @@ __device__ __forceinline__ int bexp(double x) { return (__double2hiint(x) >> 20)
 // exponent, and word >= (e << 20) tests exponent >= e
 __device__ __forceinline__ unsigned habs(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
 
-// Two integer-valued floats (|v| <= 256) as a BF16 pair, a in the low half;
-// exact because such a float has no bits below its top 16.
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
-}
-
 // The integer v (|v| < 2^22) as a float, by the 1.5 * 2^23 bias.
 __device__ __forceinline__ float int_to_float(int v) { return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f); }
-
-// Balanced base-256 digits of x * 2^-(E - 1022), E >= the biased exponent of
-// x (at least 1): M = round(x * 2^(48 - (E - 1022))) = sum_q d[q] 2^(8 (5 - q)),
-// |M| <= 2^48, d[1..5] in [-128, 127], |d[0]| <= 256.  Integer arithmetic only.
-__device__ __forceinline__ void digits_fp64(double x, int E, float (&d)[kS]) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int eb = (int)((b >> 52) & 0x7ffu);
-    const unsigned long long m = (b & 0xfffffffffffffull) | (eb ? (1ull << 52) : 0ull);
-    const int s = min(E + 5 - max(eb, 1), 63);   // >= 5
-    long long M = (long long)((m + (1ull << (s - 1))) >> s);
-    if (b >> 63) M = -M;
-    int lo = (int)(M & 0xffffff);   // M = hi 2^24 + lo, lo in [0, 2^24)
-    int hi = (int)(M >> 24);
-    int q[kS];
-#pragma unroll
-    for (int i = kS - 1; i >= 3; --i) {
-        q[i] = ((lo + 128) & 255) - 128;
-        lo = (lo - q[i]) >> 8;
-    }
-    hi += lo;                       // carry (0 or 1)
-#pragma unroll
-    for (int i = 2; i >= 1; --i) {
-        q[i] = ((hi + 128) & 255) - 128;
-        hi = (hi - q[i]) >> 8;
-    }
-    q[0] = hi;
-#pragma unroll
-    for (int i = 0; i < kS; ++i) d[i] = int_to_float(q[i]);
-}
-
-// Balanced base-256 digits of the double-float value (hi + lo) m, m a power
-// of two, |hi m| < 256 (1 + 2^-20) and |lo| <= ulp(hi) / 2 (normalised):
-// (hi + lo) m = sum_q d[q] 2^(-8q) + (error <= 2^-40), |d[q]| <= 256.
-// Digits 0-2 come from hi alone, every step exact (t 256 is a scaling;
-// adding and subtracting 1.5 2^23 rounds to an integer; the remainder is
-// representable).  Then lo m, at most ulp(t) / 2 <= 2^-17, joins the
-// remainder (|r| <= 1/2 in units of 2^-16): one rounding of at most 2^-24
-// there, 2^-40 of t's unit, and |r + lo m 2^16| <= 1 keeps digit 3 within 256.
-__device__ __forceinline__ void digits_df(float hi, float lo, float m, float m16, float (&d)[kS]) {
-    constexpr float C = 12582912.0f;
-    float q = __fsub_rn(__fmaf_rn(hi, m, C), C);   // t = hi m is exact, so is t - q
-    float r = __fmaf_rn(hi, m, -q);
-    d[0] = q;
-#pragma unroll
-    for (int i = 1; i < 3; ++i) {
-        q = __fsub_rn(__fmaf_rn(r, 256.0f, C), C);
-        r = __fmaf_rn(r, 256.0f, -q);
-        d[i] = q;
-    }
-    r = __fmaf_rn(lo, m16, r);   // m16 = m 2^16
-#pragma unroll
-    for (int i = 3; i < kS; ++i) {
-        q = __fsub_rn(__fmaf_rn(r, 256.0f, C), C);
-        r = __fmaf_rn(r, 256.0f, -q);
-        d[i] = q;
-    }
-}
 
 // 2^k as a float for k in [-126, 127]; 0 below
 __device__ __forceinline__ float pow2f_or_zero(int k) {
     return k < -126 ? 0.0f : __uint_as_float((unsigned)(min(k, 127) + 127) << 23);
-}
-
-// V = x2 + x3 2^-8 + x4 2^-16 + x5 2^-24 + x6 2^-32 + x7 2^-40 (x_L the exact
-// level sums, |x_L| < 2^22) as an unevaluated sum hi + lo.  The two leading
-// additions are error-free with the fast two-sum: either the larger
-// magnitude comes first, or the sum is exact (x2 + x3 2^-8 needs at most 23
-// bits when |x2| < |x3| 2^-8, likewise for the next); the rest err by
-// < 2^-47 of |V|'s bound.
-__device__ __forceinline__ df combine_levels(const float (&x)[6][4], int e) {
-    // fast two-sums with the scaled operand formed inside the FMAs (x 2^-8k is exact)
-    const float s1 = __fmaf_rn(x[1][e], 0x1p-8f, x[0][e]);
-    const float e1 = __fmaf_rn(x[1][e], 0x1p-8f, -__fsub_rn(s1, x[0][e]));
-    const float s2 = __fmaf_rn(x[2][e], 0x1p-16f, s1);
-    const float e2 = __fmaf_rn(x[2][e], 0x1p-16f, -__fsub_rn(s2, s1));
-    const float r = __fmaf_rn(x[3][e], 0x1p-24f, __fmaf_rn(x[4][e], 0x1p-32f, __fmaf_rn(x[5][e], 0x1p-40f, e1)));
-    return {s2, __fadd_rn(r, e2)};
 }
 
 // ---- base-1024 digits in FP16 (five per operand)

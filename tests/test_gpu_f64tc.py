@@ -1,18 +1,19 @@
 """GPU parity of the tensor-core FP64-accurate form (exact digit slicing on
-BF16 tensor cores, sem_ax_f64tc) against the FP64 CPU oracle, through the C
+FP16 tensor cores, sem_ax_f64tc) against the FP64 CPU oracle, through the C
 ABI.
 
 Error measure: ||w - w_ref||_inf / ||w_ref||_inf over the whole output.
 
-Tolerance.  Each operand keeps 6 base-256 digits (truncation 2^-49 of its
-element's scale), the tensor-core level sums are exact, the level sums and
-the geometric-factor multiply run in double-float (~2^-47 per operation,
-G split to 47 bits), and the dropped digit levels weigh < 2^-48.  About ten
-such terms pass through two contractions with 8-term sums (the gradient's
-worst case is 8 max|D| max|u|), so the bound is of order
-10 * 8 * 2^-47 ~ 6e-13 of the element's scale, and typically 1e-14.  The test
-holds it to TOL_TC = 1e-12, the FP64 requirement; the typical error is
-checked to stay below 2e-13.
+Tolerance.  Each operand keeps 5 base-1024 digits (truncation 2^-50 of its
+element's scale), the tensor-core level sums are exact (order 7; at order 15
+the two lowest levels may round by a unit at weights 2^-30 and 2^-40), the
+level sums and the geometric-factor multiply run in double-float (~2^-47 per
+operation, G split to 47 bits), and the dropped digit levels weigh < 2^-48.
+About ten such terms pass through two contractions with n-term sums (the
+gradient's worst case is n max|D| max|u|), so the bound is of order
+10 * 16 * 2^-47 ~ 1e-12 of the element's scale, and typically 1e-14 to
+1e-13.  The test holds it to TOL_TC = 1e-12, the FP64 requirement; the
+typical error is checked to stay below 2e-13.
 """
 import numpy as np
 import pytest

@@ -5,10 +5,10 @@ The method, in exact arithmetic: each operand of a contraction (u, D, and
 the intermediate [wr ws wt] = G grad u) is rounded to balanced digits
 against one power-of-two scale per element (D: one for the matrix), the
 digit products of the kept levels are summed exactly, and the levels are
-combined.  Two digit systems are used: six base-256 digits (BF16 operands,
-levels 0..5 kept, order 7) and five base-1024 digits whose leading digit
-takes one bit less, so that no digit exceeds 512 (FP16 operands, levels
-0..4 kept, order 15).  This test evaluates that model in float64 (rounding
+combined.  The kernels use five base-1024 digits whose leading digit takes
+one bit less, so that no digit exceeds 512 (FP16 operands, levels 0..4
+kept); six base-256 digits (BF16 operands, levels 0..5) are the
+alternative the first form used.  This test evaluates that model in float64 (rounding
 each operand at the last digit and dropping the levels above the kept ones,
 which is what the digits represent) and compares it with the FP64 oracle:
 the model's error is the method's own error floor, which the GPU parity
@@ -85,78 +85,62 @@ def mesh():
     return si.make_mesh(np.random.default_rng(90), 12, 7)
 
 
-def test_digit_expansion_is_balanced_and_exact(mesh):
-    u = mesh.u.numpy()
-    s = _scale(u)
-    d = _expand(u, s, 6)
-    assert np.abs(d[0]).max() <= 256
-    assert all(np.abs(x).max() <= 128 for x in d[1:])
-    val = sum(x.astype(np.float64) * 2.0 ** (-8 * (k + 1)) for k, x in enumerate(d)) * s
-    assert np.max(np.abs(val - u)) <= 2.0 ** -49 * s
-
-
-def test_level_sums_fit_the_fp32_significand(mesh):
-    """Every level of a K = 8 contraction sums at most six digit pairs of
-    magnitude <= 256 x 256: below 2^22, so FP32 accumulation is exact."""
-    D = mesh.D.numpy()
-    u = mesh.u.numpy()
-    Dd, ud = _expand(D, float(_scale(D)), 6), _expand(u, _scale(u), 6)
-    for L in range(6):
-        acc = 0
-        for p in range(L + 1):
-            acc = acc + np.abs(np.einsum("il,ekjl->ekji", np.abs(Dd[p]), np.abs(ud[L - p])))
-        assert acc.max() < 2 ** 22
-
-
-def test_six_digits_meet_the_fp64_bound_and_five_do_not(oracle_mod, mesh):
-    u, G, D = mesh.u.numpy(), mesh.G.numpy(), mesh.D.numpy()
-    ref = oracle_mod.sem_ax(u, G, D)
-    e6 = _rel(_slice_ax(u, G, D, 6), ref)
-    e5 = _rel(_slice_ax(u, G, D, 5), ref)
-    assert e6 <= 2e-13          # the GPU tests' typical bound sits above the method's floor
-    assert e5 > 1e-12           # one digit fewer misses the FP64 requirement
-
-
-def test_constant_field_floor(oracle_mod, mesh):
-    """A 1 = 0 up to the six-digit truncation of D's rows (~1e-13 of ||A u||)."""
-    u1 = np.full(mesh.u.shape, 3.25)
-    w1 = _slice_ax(u1, mesh.G.numpy(), mesh.D.numpy(), 6)
-    wr = oracle_mod.sem_ax(mesh.u.numpy(), mesh.G.numpy(), mesh.D.numpy())
-    assert np.max(np.abs(w1)) <= 1e-12 * np.max(np.abs(wr))
-
-
 @pytest.fixture(scope="module")
 def mesh16():
     return si.make_mesh(np.random.default_rng(91), 2, 15)
 
 
-def test_base1024_digits_are_balanced_and_exact(mesh16):
-    u = mesh16.u.numpy()
-    s = _scale(u)
-    d = _expand(u, s, 5, bits=10, head=1)
-    assert all(np.abs(x).max() <= 512 for x in d)
-    val = sum(x.astype(np.float64) * 2.0 ** -(10 * (k + 1) - 1) for k, x in enumerate(d)) * s
-    assert np.max(np.abs(val - u)) <= 2.0 ** -50 * s
+B10 = dict(bits=10, head=1)   # the kernels' digit system
 
 
-def test_base1024_leading_level_sums_fit_the_fp32_significand(mesh16):
-    """K = 16: levels 0..2 sum at most three digit pairs of magnitude
-    <= 512 x 512, below 2^24, so their FP32 accumulation is exact."""
-    D = mesh16.D.numpy()
-    u = mesh16.u.numpy()
-    Dd = _expand(D, float(_scale(D)), 5, bits=10, head=1)
-    ud = _expand(u, _scale(u), 5, bits=10, head=1)
-    for L in range(3):
-        acc = 0
-        for p in range(L + 1):
-            acc = acc + np.einsum("il,ekjl->ekji", np.abs(Dd[p]), np.abs(ud[L - p]))
-        assert acc.max() < 2 ** 24
+def test_digit_expansion_is_balanced_and_exact(mesh, mesh16):
+    for m in (mesh, mesh16):
+        u = m.u.numpy()
+        s = _scale(u)
+        d = _expand(u, s, 5, **B10)
+        assert all(np.abs(x).max() <= 512 for x in d)
+        val = sum(x.astype(np.float64) * 2.0 ** -(10 * (k + 1) - 1) for k, x in enumerate(d)) * s
+        assert np.max(np.abs(val - u)) <= 2.0 ** -50 * s
 
 
-def test_five_base1024_digits_meet_the_fp64_bound_and_four_do_not(oracle_mod, mesh16):
-    u, G, D = mesh16.u.numpy(), mesh16.G.numpy(), mesh16.D.numpy()
+def test_level_sums_fit_the_fp32_significand(mesh, mesh16):
+    """Order 7 (K = 8): every level sums at most five digit pairs of
+    magnitude <= 512 x 512, below 2^24, so all five FP32 accumulators are
+    exact.  Order 15 (K = 16): levels 0..2 (at most three pairs) are."""
+    for m, levels in ((mesh, 5), (mesh16, 3)):
+        D = m.D.numpy()
+        u = m.u.numpy()
+        Dd, ud = _expand(D, float(_scale(D)), 5, **B10), _expand(u, _scale(u), 5, **B10)
+        for L in range(levels):
+            acc = 0
+            for p in range(L + 1):
+                acc = acc + np.einsum("il,ekjl->ekji", np.abs(Dd[p]), np.abs(ud[L - p]))
+            assert acc.max() < 2 ** 24
+
+
+@pytest.mark.parametrize("which", ["mesh", "mesh16"])
+def test_five_digits_meet_the_fp64_bound_and_four_do_not(oracle_mod, request, which):
+    m = request.getfixturevalue(which)
+    u, G, D = m.u.numpy(), m.G.numpy(), m.D.numpy()
     ref = oracle_mod.sem_ax(u, G, D)
-    e5 = _rel(_slice_ax(u, G, D, 5, bits=10, head=1), ref)
-    e4 = _rel(_slice_ax(u, G, D, 4, bits=10, head=1), ref)
-    assert e5 <= 2e-13
-    assert e4 > 1e-12
+    e5 = _rel(_slice_ax(u, G, D, 5, **B10), ref)
+    e4 = _rel(_slice_ax(u, G, D, 4, **B10), ref)
+    assert e5 <= 2e-13          # the GPU tests' typical bound sits above the method's floor
+    assert e4 > 1e-12           # one digit fewer misses the FP64 requirement
+
+
+def test_base256_system_needs_six_digits(oracle_mod, mesh):
+    """The BF16 alternative (base-256 digits, no headroom bit): six digits
+    reach the same floor, five do not."""
+    u, G, D = mesh.u.numpy(), mesh.G.numpy(), mesh.D.numpy()
+    ref = oracle_mod.sem_ax(u, G, D)
+    assert _rel(_slice_ax(u, G, D, 6), ref) <= 2e-13
+    assert _rel(_slice_ax(u, G, D, 5), ref) > 1e-12
+
+
+def test_constant_field_floor(oracle_mod, mesh):
+    """A 1 = 0 up to the five-digit truncation of D's rows (~1e-13 of ||A u||)."""
+    u1 = np.full(mesh.u.shape, 3.25)
+    w1 = _slice_ax(u1, mesh.G.numpy(), mesh.D.numpy(), 5, **B10)
+    wr = oracle_mod.sem_ax(mesh.u.numpy(), mesh.G.numpy(), mesh.D.numpy())
+    assert np.max(np.abs(w1)) <= 1e-12 * np.max(np.abs(wr))
