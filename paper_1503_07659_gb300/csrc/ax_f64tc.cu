@@ -81,13 +81,14 @@ __device__ __forceinline__ void contract(uint32_t base, int warp, int lane, cons
     // level L = p + q for D digit p and operand digit q (0-based)
 #define OZ_K8(L, p, q) mma::f16_1688(acc[L], a[q][0], a[q][1], Bf[p])
 #define OZ_K16(L, p1, q1, p2, q2) mma::f16_16816(acc[L], a[q1][0], a[q1][1], a[q2][0], a[q2][1], Bf[p1], Bf[p2])
+    // round-robin over the levels: consecutive products update different accumulators
     OZ_K8(0, 0, 0);
     OZ_K16(1, 0, 1, 1, 0);
     OZ_K16(2, 0, 2, 1, 1);
-    OZ_K8(2, 2, 0);
     OZ_K16(3, 0, 3, 1, 2);
-    OZ_K16(3, 2, 1, 3, 0);
     OZ_K16(4, 0, 4, 1, 3);
+    OZ_K8(2, 2, 0);
+    OZ_K16(3, 2, 1, 3, 0);
     OZ_K16(4, 2, 2, 3, 1);
     OZ_K8(4, 4, 0);
 #undef OZ_K8
@@ -265,10 +266,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 // renormalise: when the leading level sums of a gradient cancel
                 // exactly, its value sits in the low part, and so can y's
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const df n2 = dfx::two_sum(y[q][a].s, y[q][a].c);
-                    y[q][a] = acc2{n2.hi, n2.lo};
-                }
+                for (int a = 0; a < 3; ++a) y[q][a] = renorm(y[q][a]);
                 shn[q] = sh;
                 const float ym = fmaxf(fabsf(y[q][0].s), fmaxf(fabsf(y[q][1].s), fabsf(y[q][2].s)));
                 const int ev = (int)(__float_as_uint(ym) >> 23);
@@ -288,8 +286,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
             unsigned char *p = dig + prow(2 * warp + h, g) + 4 * t;
             const float m0 = pow2f_or_zero(shn[2 * h] - eW + 135);       // |y 2^(sh - eW + 126)| < 1
             const float m1 = pow2f_or_zero(shn[2 * h + 1] - eW + 135);
-            const float m0s = pow2f_or_zero(shn[2 * h] - eW + 155);      // m 2^20, finite when m is clamped
-            const float m1s = pow2f_or_zero(shn[2 * h + 1] - eW + 155);
+            const float m0s = times2p20(m0), m1s = times2p20(m1);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 float d0[kS10], d1[kS10];

@@ -61,6 +61,18 @@ __device__ __forceinline__ float pow2f_or_zero(int k) {
     return k < -126 ? 0.0f : __uint_as_float((unsigned)(min(k, 127) + 127) << 23);
 }
 
+// m 2^20 for a digit scale m = 2^k from pow2f_or_zero, clamped like it
+__device__ __forceinline__ float times2p20(float m) { return fminf(__fmul_rn(m, 0x1p20f), 0x1p127f); }
+
+// A Dot2 result s + c renormalised for digit extraction.  The fast two-sum
+// is exact when |s| >= |c|, the usual case (c collects rounding errors);
+// when a sum cancels below its own error terms it errs by at most ulp(c)/2,
+// under the Dot2 sum's own error bound.
+__device__ __forceinline__ acc2 renorm(acc2 y) {
+    const df n = dfx::fast_two_sum(y.s, y.c);
+    return acc2{n.hi, n.lo};
+}
+
 // ---- base-1024 digits in FP16 (five per operand)
 //
 // Balanced base-1024 digits are integers of magnitude <= 528 here, exact in
@@ -132,6 +144,12 @@ __device__ __forceinline__ void digits10_df(float hi, float lo, float m, float m
     r = __fmaf_rn(r, 1024.0f, -q);
     d[3] = q;
     d[4] = __fsub_rn(__fmaf_rn(r, 1024.0f, C), C);
+}
+
+// digits10_df of (hi + lo) 2^k (the scale of y's digits)
+__device__ __forceinline__ void digits10_at(float hi, float lo, int k, float (&d)[kS10]) {
+    const float m = pow2f_or_zero(k);
+    digits10_df(hi, lo, m, times2p20(m), d);
 }
 
 // V = x0 + x1 2^-10 + x2 2^-20 + x3 2^-30 + x4 2^-40 (x_L the level sums,

@@ -59,14 +59,15 @@ __device__ __forceinline__ int pch(int p, int r, int c) {
 // writes and the plane owners' reads are both conflict-free.
 __device__ __forceinline__ int tslot(int k, int j, int ip) { return (k * 128 + j * 8 + ip) ^ (((j ^ k) & 1) << 2); }
 
-// acc[L] += A_a B_b over the 15 digit pairs a + b = L <= 4
+// acc[L] += A_a B_b over the 15 digit pairs a + b = L <= 4, issued round-robin
+// over the levels so that consecutive products update different accumulators
 __device__ __forceinline__ void pairs15(float (&acc)[kS10][4], const uint32_t (&A)[kS10][4], const uint32_t (&B)[kS10][2]) {
 #pragma unroll
     for (int L = 0; L < kS10; ++L) acc[L][0] = acc[L][1] = acc[L][2] = acc[L][3] = 0.0f;
 #pragma unroll
-    for (int L = 0; L < kS10; ++L)
+    for (int a = 0; a < kS10; ++a)
 #pragma unroll
-        for (int a = 0; a <= L; ++a)
+        for (int L = a; L < kS10; ++L)
             mma::f16_16816(acc[L], A[a][0], A[a][1], A[a][2], A[a][3], B[L - a][0], B[L - a][1]);
 }
 
