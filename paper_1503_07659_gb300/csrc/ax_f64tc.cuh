@@ -146,12 +146,6 @@ __device__ __forceinline__ void digits10_df(float hi, float lo, float m, float m
     d[4] = __fsub_rn(__fmaf_rn(r, 1024.0f, C), C);
 }
 
-// digits10_df of (hi + lo) 2^k (the scale of y's digits)
-__device__ __forceinline__ void digits10_at(float hi, float lo, int k, float (&d)[kS10]) {
-    const float m = pow2f_or_zero(k);
-    digits10_df(hi, lo, m, times2p20(m), d);
-}
-
 // V = x0 + x1 2^-10 + x2 2^-20 + x3 2^-30 + x4 2^-40 (x_L the level sums,
 // x0..x2 exact, |x_L| < 2^25) as an unevaluated sum hi + lo.  The first
 // addition is error-free with the fast two-sum (the larger magnitude comes
