@@ -110,7 +110,8 @@ template <int DIR>
 __device__ __forceinline__ void store_tile(float2 *buf, const float (&acc)[kS10][4], int warp, int g, int t) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const df v0 = combine5_k8(acc, 2 * h), v1 = combine5_k8(acc, 2 * h + 1);
+        df v0, v1;
+        combine5_k8x2(acc, 2 * h, v0, v1);
         if (DIR == 1) {   // rows (k = 2w + h, i = g), columns j = 2t, 2t + 1: adjacent in [k][i][j]
             *reinterpret_cast<float4 *>(buf + sidx(2 * warp + h, 2 * t, g)) = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
         } else {          // rows (j = 2w + h, i = g), columns k = 2t, 2t + 1
@@ -161,11 +162,11 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         digits10_fp64(D[g * 8 + 2 * t], eD, x0);
         digits10_fp64(D[g * 8 + 2 * t + 1], eD, x1);
 #pragma unroll
-        for (int p = 0; p < kS10; ++p) fg[p] = pack_f16(x0[p], x1[p]);
+        for (int p = 0; p < kS10; ++p) fg[p] = pack_f16(-x0[p], -x1[p]);   // negated, like u's and y's
         digits10_fp64(D[(2 * t) * 8 + g], eD, x0);
         digits10_fp64(D[(2 * t + 1) * 8 + g], eD, x1);
 #pragma unroll
-        for (int p = 0; p < kS10; ++p) ft[p] = pack_f16(x0[p], x1[p]);
+        for (int p = 0; p < kS10; ++p) ft[p] = pack_f16(-x0[p], -x1[p]);
     }
 
     unsigned parity = 0;
@@ -201,8 +202,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
             const df a0 = split_g(uv[h].x, habs(uv[h].x), Ku, mw);
             const df a1 = split_g(uv[h].y, habs(uv[h].y), Ku, mw);
             const df n0 = dfx::fast_two_sum(a0.hi, a0.lo), n1 = dfx::fast_two_sum(a1.hi, a1.lo);
-            digits10_df(n0.hi, n0.lo, 256.0f, 268435456.0f, d0);
-            digits10_df(n1.hi, n1.lo, 256.0f, 268435456.0f, d1);
+            digits10_df2_neg(make_float2(n0.hi, n1.hi), make_float2(n0.lo, n1.lo), f2(256.0f), f2(268435456.0f), d0, d1);
             unsigned char *p = dig + prow(2 * warp + h, g) + 4 * t;
 #pragma unroll
             for (int q = 0; q < kS10; ++q) *reinterpret_cast<uint32_t *>(p + q * kSlice) = pack_f16(d0[q], d1[q]);
@@ -215,7 +215,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
             float acc[kS10][4];
             contract<0>(dig_s, warp, lane, fg, acc);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) vr[q] = combine5_k8(acc, q);
+            for (int q = 0; q < 4; q += 2) combine5_k8x2(acc, q, vr[q], vr[q + 1]);
         }
         {
             float acc[kS10][4];
@@ -290,8 +290,8 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 float d0[kS10], d1[kS10];
-                digits10_df(y[2 * h][a].s, y[2 * h][a].c, m0, m0s, d0);
-                digits10_df(y[2 * h + 1][a].s, y[2 * h + 1][a].c, m1, m1s, d1);
+                digits10_df2_neg(make_float2(y[2 * h][a].s, y[2 * h + 1][a].s), make_float2(y[2 * h][a].c, y[2 * h + 1][a].c),
+                                 make_float2(m0, m1), make_float2(m0s, m1s), d0, d1);
 #pragma unroll
                 for (int q = 0; q < kS10; ++q)
                     *reinterpret_cast<uint32_t *>(p + (a * kS10 + q) * kSlice) = pack_f16(d0[q], d1[q]);
@@ -305,7 +305,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
             float acc[kS10][4];
             contract<0>(dig_s, warp, lane, ft, acc);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) vo[q] = combine5_k8(acc, q);
+            for (int q = 0; q < 4; q += 2) combine5_k8x2(acc, q, vo[q], vo[q + 1]);
         }
         {
             float acc[kS10][4];

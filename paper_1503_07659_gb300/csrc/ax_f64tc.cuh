@@ -146,6 +146,57 @@ __device__ __forceinline__ void digits10_df(float hi, float lo, float m, float m
     d[4] = __fsub_rn(__fmaf_rn(r, 1024.0f, C), C);
 }
 
+// ---- the same on pairs of values with the packed FP32 instructions
+// (fma/add/mul.rn.f32x2: two results per instruction slot).  A - B is
+// formed as fma(B, -1, A), exact wherever the scalar form's subtraction is.
+
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// digits10_df of two values at once, the digits NEGATED: every step is the
+// scalar form's with -q = C - (t + C) computed as fma(t + C, -1, C) (exact),
+// so nd0[q] = -d0[q] bit for bit.  Negated digits of both operands of a
+// product leave the tensor-core sums unchanged.
+__device__ __forceinline__ void digits10_df2_neg(float2 hi, float2 lo, float2 m, float2 m20, float (&nd0)[kS10],
+                                                 float (&nd1)[kS10]) {
+    const float2 C = f2(12582912.0f), M1 = f2(-1.0f), K = f2(1024.0f);
+    float2 a = __ffma2_rn(hi, m, C);
+    float2 nq = __ffma2_rn(a, M1, C);
+    float2 r = __ffma2_rn(hi, m, nq);
+    nd0[0] = nq.x, nd1[0] = nq.y;
+    a = __ffma2_rn(r, K, C);
+    nq = __ffma2_rn(a, M1, C);
+    r = __ffma2_rn(r, K, nq);
+    nd0[1] = nq.x, nd1[1] = nq.y;
+    a = __ffma2_rn(r, K, C);
+    nq = __ffma2_rn(a, M1, C);
+    r = __ffma2_rn(r, K, nq);
+    const float2 S = __ffma2_rn(lo, m20, r);
+    const float2 nli = __ffma2_rn(__fadd2_rn(S, C), M1, C);
+    const float2 nd2 = __fadd2_rn(nq, nli);
+    nd0[2] = nd2.x, nd1[2] = nd2.y;
+    r = __fadd2_rn(S, nli);
+    a = __ffma2_rn(r, K, C);
+    nq = __ffma2_rn(a, M1, C);
+    r = __ffma2_rn(r, K, nq);
+    nd0[3] = nq.x, nd1[3] = nq.y;
+    nq = __ffma2_rn(__ffma2_rn(r, K, C), M1, C);
+    nd0[4] = nq.x, nd1[4] = nq.y;
+}
+
+// combine5_k8 of the outputs e and e + 1 (bit for bit the scalar form)
+__device__ __forceinline__ void combine5_k8x2(const float (&x)[kS10][4], int e, df &v0, df &v1) {
+    auto P = [&](int L) { return make_float2(x[L][e], x[L][e + 1]); };
+    const float2 M1 = f2(-1.0f);
+    const float2 s1 = __ffma2_rn(P(1), f2(0x1p-10f), P(0));
+    const float2 e1 = __ffma2_rn(P(1), f2(0x1p-10f), __ffma2_rn(s1, M1, P(0)));
+    const float2 s2 = __ffma2_rn(P(2), f2(0x1p-20f), s1);
+    const float2 e2 = __ffma2_rn(P(2), f2(0x1p-20f), __ffma2_rn(s2, M1, s1));
+    const float2 r = __ffma2_rn(P(3), f2(0x1p-30f), __ffma2_rn(P(4), f2(0x1p-40f), e1));
+    const float2 lo = __fadd2_rn(r, e2);
+    v0 = df{s2.x, lo.x};
+    v1 = df{s2.y, lo.y};
+}
+
 // V = x0 + x1 2^-10 + x2 2^-20 + x3 2^-30 + x4 2^-40 (x_L the level sums,
 // x0..x2 exact, |x_L| < 2^25) as an unevaluated sum hi + lo.  The first
 // addition is error-free with the fast two-sum (the larger magnitude comes
