@@ -197,6 +197,30 @@ __device__ __forceinline__ void combine5_k8x2(const float (&x)[kS10][4], int e, 
     v1 = df{s2.y, lo.y};
 }
 
+// Double-float values of two nodes, lane-wise.
+struct df2 {
+    float2 hi, lo;
+};
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }   // a - b
+
+__device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bb = sub2(s, a);
+    return {s, __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+
+// combine5 of the outputs e and e + 1 (bit for bit the scalar form)
+__device__ __forceinline__ void combine5x2(const float (&x)[kS10][4], int e, df &v0, df &v1) {
+    auto P = [&](int L) { return make_float2(x[L][e], x[L][e + 1]); };
+    const float2 s1 = __ffma2_rn(P(1), f2(0x1p-10f), P(0));
+    const float2 e1 = __ffma2_rn(P(1), f2(0x1p-10f), sub2(P(0), s1));
+    const df2 s2 = two_sum2(s1, __fmul2_rn(P(2), f2(0x1p-20f)));
+    const float2 r = __ffma2_rn(P(3), f2(0x1p-30f), __ffma2_rn(P(4), f2(0x1p-40f), e1));
+    const float2 lo = __fadd2_rn(r, s2.lo);
+    v0 = df{s2.hi.x, lo.x};
+    v1 = df{s2.hi.y, lo.y};
+}
+
 // V = x0 + x1 2^-10 + x2 2^-20 + x3 2^-30 + x4 2^-40 (x_L the level sums,
 // x0..x2 exact, |x_L| < 2^25) as an unevaluated sum hi + lo.  The first
 // addition is error-free with the fast two-sum (the larger magnitude comes

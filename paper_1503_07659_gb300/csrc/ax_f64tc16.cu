@@ -143,7 +143,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
 #pragma unroll
         for (int p = 0; p < kS10; ++p)
             *reinterpret_cast<unsigned short *>(dd + p * kPlaneB + pch(0, a, b >> 3) + 2 * (b & 7)) =
-                (unsigned short)(pack_f16(d[p], 0.0f) & 0xffffu);
+                (unsigned short)(pack_f16(-d[p], 0.0f) & 0xffffu);   // negated, like u's and y's
     }
     __syncthreads();
 
@@ -199,8 +199,8 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                     const df a0 = split_g(uv[nt][h].x, habs(uv[nt][h].x), Ku, mw);
                     const df a1 = split_g(uv[nt][h].y, habs(uv[nt][h].y), Ku, mw);
                     const df n0 = dfx::fast_two_sum(a0.hi, a0.lo), n1 = dfx::fast_two_sum(a1.hi, a1.lo);
-                    digits10_df(n0.hi, n0.lo, 256.0f, 268435456.0f, d0);
-                    digits10_df(n1.hi, n1.lo, 256.0f, 268435456.0f, d1);
+                    digits10_df2_neg(make_float2(n0.hi, n1.hi), make_float2(n0.lo, n1.lo), f2(256.0f), f2(268435456.0f),
+                                     d0, d1);
                     unsigned char *p = ud + pch(k, g + 8 * h, nt) + 4 * t;
 #pragma unroll
                     for (int q = 0; q < kS10; ++q) *reinterpret_cast<uint32_t *>(p + q * kDigitB) = pack_f16(d0[q], d1[q]);
@@ -226,9 +226,11 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 float acc[kS10][4];
                 pairs15(acc, fa, bu);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const df v = combine5(acc, c);
-                    sb[(4 * nt + c) * kThreads + tid] = make_float2(v.hi, v.lo);
+                for (int c = 0; c < 4; c += 2) {
+                    df v0, v1;
+                    combine5x2(acc, c, v0, v1);
+                    sb[(4 * nt + c) * kThreads + tid] = make_float2(v0.hi, v0.lo);
+                    sb[(4 * nt + c + 1) * kThreads + tid] = make_float2(v1.hi, v1.lo);
                 }
             }
 #pragma unroll
@@ -243,7 +245,8 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 pairs15(acc, fa, bu);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {   // rows kk = g + 8 h, columns i = 8 nt + 2 t, +1
-                    const df v0 = combine5(acc, 2 * h), v1 = combine5(acc, 2 * h + 1);
+                    df v0, v1;
+                    combine5x2(acc, 2 * h, v0, v1);
                     tb[tslot(g + 8 * h, k, 4 * nt + t)] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
                 }
             }
@@ -264,7 +267,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 float acc[kS10][4];
                 pairs15(acc, au, bd);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) vr[4 * nt + c] = combine5(acc, c);
+                for (int c = 0; c < 4; c += 2) combine5x2(acc, c, vr[4 * nt + c], vr[4 * nt + c + 1]);
             }
         }
         __syncthreads();
@@ -326,9 +329,9 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
             for (int h = 0; h < 2; ++h) {
                 const int q0 = 4 * nt + 2 * h;
                 float d0[kS10], d1[kS10];
-                digits10_df(yr[q0].s, yr[q0].c, pow2f_or_zero(shA[q0] - eR + 135), pow2f_or_zero(shA[q0] - eR + 155), d0);
-                digits10_df(yr[q0 + 1].s, yr[q0 + 1].c, pow2f_or_zero(shA[q0 + 1] - eR + 135),
-                          pow2f_or_zero(shA[q0 + 1] - eR + 155), d1);
+                digits10_df2_neg(make_float2(yr[q0].s, yr[q0 + 1].s), make_float2(yr[q0].c, yr[q0 + 1].c),
+                                 make_float2(pow2f_or_zero(shA[q0] - eR + 135), pow2f_or_zero(shA[q0 + 1] - eR + 135)),
+                                 make_float2(pow2f_or_zero(shA[q0] - eR + 155), pow2f_or_zero(shA[q0 + 1] - eR + 155)), d0, d1);
 #pragma unroll
                 for (int d = 0; d < kS10; ++d) ya[d][2 * nt + h] = pack_f16(d0[d], d1[d]);
             }
@@ -345,7 +348,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
             float acc[kS10][4];
             pairs15(acc, ya, bd);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) wr_[4 * nt + c] = combine5(acc, c);
+            for (int c = 0; c < 4; c += 2) combine5x2(acc, c, wr_[4 * nt + c], wr_[4 * nt + c + 1]);
         }
 
         // ---- C2: G's second half (ss, st, tt): finish y_s, y_t
@@ -425,16 +428,16 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
             for (int h = 0; h < 2; ++h) {
                 const int q0 = 4 * nt + 2 * h;
                 float d0[kS10], d1[kS10];
-                digits10_df(ys[q0].s, ys[q0].c, pow2f_or_zero(shS[q0] - eS + 135), pow2f_or_zero(shS[q0] - eS + 155), d0);
-                digits10_df(ys[q0 + 1].s, ys[q0 + 1].c, pow2f_or_zero(shS[q0 + 1] - eS + 135),
-                          pow2f_or_zero(shS[q0 + 1] - eS + 155), d1);
+                digits10_df2_neg(make_float2(ys[q0].s, ys[q0 + 1].s), make_float2(ys[q0].c, ys[q0 + 1].c),
+                                 make_float2(pow2f_or_zero(shS[q0] - eS + 135), pow2f_or_zero(shS[q0 + 1] - eS + 135)),
+                                 make_float2(pow2f_or_zero(shS[q0] - eS + 155), pow2f_or_zero(shS[q0 + 1] - eS + 155)), d0, d1);
                 // block (rows j = 8h.., columns i = 8nt..) transposed: the B fragment of
                 // K rows l = 8h.. (b0 for h = 0, b1 for h = 1) of n-tile nt
 #pragma unroll
                 for (int d = 0; d < kS10; ++d) yb[d][2 * nt + h] = mma::movm_t(pack_f16(d0[d], d1[d]));
-                digits10_df(yt[q0].s, yt[q0].c, pow2f_or_zero(shS[q0] - eT + 135), pow2f_or_zero(shS[q0] - eT + 155), d0);
-                digits10_df(yt[q0 + 1].s, yt[q0 + 1].c, pow2f_or_zero(shS[q0 + 1] - eT + 135),
-                          pow2f_or_zero(shS[q0 + 1] - eT + 155), d1);
+                digits10_df2_neg(make_float2(yt[q0].s, yt[q0 + 1].s), make_float2(yt[q0].c, yt[q0 + 1].c),
+                                 make_float2(pow2f_or_zero(shS[q0] - eT + 135), pow2f_or_zero(shS[q0 + 1] - eT + 135)),
+                                 make_float2(pow2f_or_zero(shS[q0] - eT + 155), pow2f_or_zero(shS[q0 + 1] - eT + 155)), d0, d1);
                 unsigned char *p = ud + pch(k, g + 8 * h, nt) + 4 * t;
 #pragma unroll
                 for (int d = 0; d < kS10; ++d) *reinterpret_cast<uint32_t *>(p + d * kDigitB) = pack_f16(d0[d], d1[d]);
@@ -459,7 +462,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 float acc[kS10][4];
                 pairs15(acc, fat, bb);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) ws_[4 * nt + c] = combine5(acc, c);
+                for (int c = 0; c < 4; c += 2) combine5x2(acc, c, ws_[4 * nt + c], ws_[4 * nt + c + 1]);
             }
             if (e + gridDim.x < E) load_u(e + gridDim.x);   // next element's u, in flight through D_t and E
 #pragma unroll
@@ -474,7 +477,8 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 pairs15(acc, fat, bt);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const df v0 = combine5(acc, 2 * h), v1 = combine5(acc, 2 * h + 1);
+                    df v0, v1;
+                    combine5x2(acc, 2 * h, v0, v1);
                     tb[tslot(g + 8 * h, k, 4 * nt + t)] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
                 }
             }
