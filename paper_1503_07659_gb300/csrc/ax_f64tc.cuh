@@ -209,6 +209,58 @@ __device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
     return {s, __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb))};
 }
 
+// Dot2 accumulators of two nodes, lane-wise, and the double-float
+// geometric-factor arithmetic on them (each step the scalar form's, in the
+// same order, so the results are bit-identical).
+struct acc2x2 {
+    float2 s, c;
+};
+__device__ __forceinline__ df2 pack_df2(df a, df b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+
+// split_g of two values (x.x with hw0, K0, mw0; x.y with hw1, K1, mw1)
+__device__ __forceinline__ df2 split_g2(double2 x, unsigned hw0, unsigned hw1, unsigned K0, unsigned K1, unsigned mw0,
+                                        unsigned mw1) {
+    const unsigned h0 = (unsigned)__double2hiint(x.x), l0 = (unsigned)__double2loint(x.x);
+    const unsigned h1 = (unsigned)__double2hiint(x.y), l1 = (unsigned)__double2loint(x.y);
+    const float hi0 = hw0 >= mw0 ? __uint_as_float((__funnelshift_l(l0, h0, 3) - K0) | (h0 & 0x80000000u)) : 0.0f;
+    const float hi1 = hw1 >= mw1 ? __uint_as_float((__funnelshift_l(l1, h1, 3) - K1) | (h1 & 0x80000000u)) : 0.0f;
+    const float2 r = __fadd2_rn(make_float2(__uint_as_float(0x4B000000u | ((l0 >> 6) & 0x7fffffu)),
+                                            __uint_as_float(0x4B000000u | ((l1 >> 6) & 0x7fffffu))),
+                                f2(-8388608.0f));
+    const float2 sc = __fmul2_rn(make_float2(__uint_as_float(__float_as_uint(hi0) & 0x7f800000u),
+                                             __uint_as_float(__float_as_uint(hi1) & 0x7f800000u)),
+                                 f2(0x1p-46f));
+    const float2 p = __fmul2_rn(r, sc);
+    return {make_float2(hi0, hi1), make_float2(__uint_as_float(__float_as_uint(p.x) | (h0 & 0x80000000u)),
+                                               __uint_as_float(__float_as_uint(p.y) | (h1 & 0x80000000u)))};
+}
+
+// a * x lane-wise (the exact product of the high parts plus the cross terms)
+__device__ __forceinline__ acc2x2 prod2(const df2 &a, const df2 &x) {
+    const float2 m = __fmul2_rn(a.hi, x.hi);
+    float2 r = __ffma2_rn(a.hi, x.hi, make_float2(-m.x, -m.y));
+    r = __ffma2_rn(a.hi, x.lo, r);
+    r = __ffma2_rn(a.lo, x.hi, r);
+    return {m, r};
+}
+
+// a += p * x lane-wise (dot2_step)
+__device__ __forceinline__ void dot2_step2(acc2x2 &a, const df2 &p, const df2 &x) {
+    const acc2x2 q = prod2(p, x);
+    const df2 t = two_sum2(a.s, q.s);
+    a.s = t.hi;
+    a.c = __fadd2_rn(a.c, __fadd2_rn(q.c, t.lo));
+}
+
+// dot3 lane-wise
+__device__ __forceinline__ acc2x2 dot3_2(const df2 &g0, const df2 &g1, const df2 &g2, const df2 &v0, const df2 &v1,
+                                         const df2 &v2) {
+    acc2x2 a = prod2(g0, v0);
+    dot2_step2(a, g1, v1);
+    dot2_step2(a, g2, v2);
+    return a;
+}
+
 // combine5 of the outputs e and e + 1 (bit for bit the scalar form)
 __device__ __forceinline__ void combine5x2(const float (&x)[kS10][4], int e, df &v0, df &v1) {
     auto P = [&](int L) { return make_float2(x[L][e], x[L][e + 1]); };

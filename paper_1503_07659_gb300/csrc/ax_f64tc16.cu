@@ -78,28 +78,6 @@ __device__ __forceinline__ int max16(const int *p) {
                max(max(max(c.x, c.y), max(c.z, c.w)), max(max(d.x, d.y), max(d.z, d.w))));
 }
 
-// the double-float value d 2^k (k <= 0) in floats; 0 when below the range
-__device__ __forceinline__ df scale_df(df d, int k) {
-    const float f = pow2f_or_zero(k);
-    return {__fmul_rn(d.hi, f), __fmul_rn(d.lo, f)};
-}
-
-// (a.s + a.c) 2^ka + (b.s + b.c) 2^kb, ka, kb <= 0, as acc2
-__device__ __forceinline__ acc2 add_scaled(acc2 a, int ka, acc2 b, int kb) {
-    const df x = scale_df(df{a.s, a.c}, ka), y = scale_df(df{b.s, b.c}, kb);
-    const df t = dfx::two_sum(x.hi, y.hi);
-    return acc2{t.hi, __fadd_rn(__fadd_rn(x.lo, y.lo), t.lo)};
-}
-
-// a * x for double-floats a (geometric factor) and x, as acc2
-__device__ __forceinline__ acc2 prod(df a, df x) {
-    const float m = __fmul_rn(a.hi, x.hi);
-    float r = __fmaf_rn(a.hi, x.hi, -m);
-    r = __fmaf_rn(a.hi, x.lo, r);
-    r = __fmaf_rn(a.lo, x.hi, r);
-    return acc2{m, r};
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
 ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
                   const double *__restrict__ D, double *__restrict__ w) {
@@ -272,47 +250,51 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
         }
         __syncthreads();
 
-        // ---- C1: G's first half (rr, rs, rt): y_r, and the r-parts of y_s, y_t
-        acc2 yr[8], ysp[8], ytp[8];
+        // ---- C1: G's first half (rr, rs, rt): y_r, and the r-parts of y_s, y_t,
+        // on the node pairs c = 0, 1 (p = 2 nt + h) lane-wise in packed FP32
+        acc2x2 YR[4], YSP[4], YTP[4];
         int shA[8];
         int tmax = INT_MIN;
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int j = g + 8 * h, nd2 = (k * 256 + j * 16 + 8 * nt + 2 * t) >> 1;
+                const int j = g + 8 * h, nd2 = (k * 256 + j * 16 + 8 * nt + 2 * t) >> 1, p = 2 * nt + h, q0 = 2 * p;
                 const float4 tv = tb[tslot(k, j, 4 * nt + t)];
                 double2 gv[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) gv[a] = gs[a * 2048 + nd2];
+                const float2 s0 = sb[q0 * kThreads + tid], s1 = sb[(q0 + 1) * kThreads + tid];
+                const df2 Vr = pack_df2(vr[q0], vr[q0 + 1]);
+                const df2 Vs{make_float2(s0.x, s1.x), make_float2(s0.y, s1.y)};
+                const df2 Vt{make_float2(tv.x, tv.z), make_float2(tv.y, tv.w)};
+                unsigned hw0[3], hw1[3], hm0 = 0, hm1 = 0;
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int q = 4 * nt + 2 * h + c;
-                    const float2 s2 = sb[q * kThreads + tid];
-                    const df Vs{s2.x, s2.y}, Vt = c ? df{tv.z, tv.w} : df{tv.x, tv.y};
-                    double Gc[3];
-                    unsigned hw[3], hm = 0;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        Gc[a] = c ? gv[a].y : gv[a].x;
-                        hw[a] = habs(Gc[a]);
-                        hm = max(hm, hw[a]);
-                    }
-                    const int eg = (int)(hm >> 20), sh = max(eg, 1) - 1023;
-                    const unsigned K = (unsigned)(896 + sh) << 23, mw = (unsigned)max(897 + sh, 1) << 20;
-                    df Gh[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) Gh[a] = split_g(Gc[a], hw[a], K, mw);
-                    const acc2 y = dot3(Gh[0], Gh[1], Gh[2], vr[q], Vs, Vt);
-                    const df yn = dfx::two_sum(y.s, y.c);
-                    yr[q] = acc2{yn.hi, yn.lo};
-                    ysp[q] = prod(Gh[1], vr[q]);
-                    ytp[q] = prod(Gh[2], vr[q]);
-                    shA[q] = sh;
-                    const int ev = (int)(__float_as_uint(fabsf(yn.hi)) >> 23);
-                    if (ev) tmax = max(tmax, ev + sh);
-                    if (eg == 0x7ff) tmax = kBadExp;
+                for (int a = 0; a < 3; ++a) {
+                    hw0[a] = habs(gv[a].x);
+                    hw1[a] = habs(gv[a].y);
+                    hm0 = max(hm0, hw0[a]);
+                    hm1 = max(hm1, hw1[a]);
                 }
+                const int eg0 = (int)(hm0 >> 20), sh0 = max(eg0, 1) - 1023;
+                const int eg1 = (int)(hm1 >> 20), sh1 = max(eg1, 1) - 1023;
+                const unsigned K0 = (unsigned)(896 + sh0) << 23, mw0 = (unsigned)max(897 + sh0, 1) << 20;
+                const unsigned K1 = (unsigned)(896 + sh1) << 23, mw1 = (unsigned)max(897 + sh1, 1) << 20;
+                df2 Gh[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) Gh[a] = split_g2(gv[a], hw0[a], hw1[a], K0, K1, mw0, mw1);
+                const acc2x2 y = dot3_2(Gh[0], Gh[1], Gh[2], Vr, Vs, Vt);
+                const df2 yn = two_sum2(y.s, y.c);
+                YR[p] = acc2x2{yn.hi, yn.lo};
+                YSP[p] = prod2(Gh[1], Vr);
+                YTP[p] = prod2(Gh[2], Vr);
+                shA[q0] = sh0;
+                shA[q0 + 1] = sh1;
+                const int ev0 = (int)(__float_as_uint(fabsf(yn.hi.x)) >> 23);
+                const int ev1 = (int)(__float_as_uint(fabsf(yn.hi.y)) >> 23);
+                if (ev0) tmax = max(tmax, ev0 + sh0);
+                if (ev1) tmax = max(tmax, ev1 + sh1);
+                if (eg0 == 0x7ff || eg1 == 0x7ff) tmax = kBadExp;
             }
         tmax = __reduce_max_sync(0xffffffffu, tmax);
         if (lane == 0) sred[16 + warp] = tmax;
@@ -329,7 +311,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
             for (int h = 0; h < 2; ++h) {
                 const int q0 = 4 * nt + 2 * h;
                 float d0[kS10], d1[kS10];
-                digits10_df2_neg(make_float2(yr[q0].s, yr[q0 + 1].s), make_float2(yr[q0].c, yr[q0 + 1].c),
+                digits10_df2_neg(YR[2 * nt + h].s, YR[2 * nt + h].c,
                                  make_float2(pow2f_or_zero(shA[q0] - eR + 135), pow2f_or_zero(shA[q0 + 1] - eR + 135)),
                                  make_float2(pow2f_or_zero(shA[q0] - eR + 155), pow2f_or_zero(shA[q0 + 1] - eR + 155)), d0, d1);
 #pragma unroll
@@ -353,54 +335,61 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
 
         // ---- C2: G's second half (ss, st, tt): finish y_s, y_t
         const bool toB = !mbar_wait(barB, pB);
-        acc2 ys[8], yt[8];
+        acc2x2 YS[4], YT[4];
         int shS[8];
         int smax = INT_MIN, tmx = INT_MIN;
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int j = g + 8 * h, nd2 = (k * 256 + j * 16 + 8 * nt + 2 * t) >> 1;
+                const int j = g + 8 * h, nd2 = (k * 256 + j * 16 + 8 * nt + 2 * t) >> 1, p = 2 * nt + h, q0 = 2 * p;
                 const float4 tv = tb[tslot(k, j, 4 * nt + t)];
                 double2 gv[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) gv[a] = gs[a * 2048 + nd2];
+                const float2 s0 = sb[q0 * kThreads + tid], s1 = sb[(q0 + 1) * kThreads + tid];
+                const df2 Vs{make_float2(s0.x, s1.x), make_float2(s0.y, s1.y)};
+                const df2 Vt{make_float2(tv.x, tv.z), make_float2(tv.y, tv.w)};
+                unsigned hw0[3], hw1[3], hm0 = 0, hm1 = 0;
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int q = 4 * nt + 2 * h + c;
-                    const float2 s2 = sb[q * kThreads + tid];
-                    const df Vs{s2.x, s2.y}, Vt = c ? df{tv.z, tv.w} : df{tv.x, tv.y};
-                    double Gc[3];
-                    unsigned hw[3], hm = 0;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        Gc[a] = c ? gv[a].y : gv[a].x;
-                        hw[a] = habs(Gc[a]);
-                        hm = max(hm, hw[a]);
-                    }
-                    const int eg = (int)(hm >> 20), sh = max(eg, 1) - 1023;
-                    const unsigned K = (unsigned)(896 + sh) << 23, mw = (unsigned)max(897 + sh, 1) << 20;
-                    df Gh[3];   // ss, st, tt
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) Gh[a] = split_g(Gc[a], hw[a], K, mw);
-                    // y_s = Grs r + Gss s + Gst t,  y_t = Grt r + Gst s + Gtt t
-                    acc2 bs = prod(Gh[0], Vs);
-                    dfx::dot2_step(bs, Gh[1], Vt);
-                    acc2 bt = prod(Gh[1], Vs);
-                    dfx::dot2_step(bt, Gh[2], Vt);
-                    const int sm = max(shA[q], sh);
-                    const acc2 s_ = add_scaled(ysp[q], shA[q] - sm, bs, sh - sm);
-                    const acc2 t_ = add_scaled(ytp[q], shA[q] - sm, bt, sh - sm);
-                    const df sn = dfx::two_sum(s_.s, s_.c), tn = dfx::two_sum(t_.s, t_.c);
-                    ys[q] = acc2{sn.hi, sn.lo};
-                    yt[q] = acc2{tn.hi, tn.lo};
-                    shS[q] = sm;
-                    const int es = (int)(__float_as_uint(fabsf(sn.hi)) >> 23);
-                    const int et = (int)(__float_as_uint(fabsf(tn.hi)) >> 23);
-                    if (es) smax = max(smax, es + sm);
-                    if (et) tmx = max(tmx, et + sm);
-                    if (eg == 0x7ff) smax = tmx = kBadExp;
+                for (int a = 0; a < 3; ++a) {
+                    hw0[a] = habs(gv[a].x);
+                    hw1[a] = habs(gv[a].y);
+                    hm0 = max(hm0, hw0[a]);
+                    hm1 = max(hm1, hw1[a]);
                 }
+                const int eg0 = (int)(hm0 >> 20), sh0 = max(eg0, 1) - 1023;
+                const int eg1 = (int)(hm1 >> 20), sh1 = max(eg1, 1) - 1023;
+                const unsigned K0 = (unsigned)(896 + sh0) << 23, mw0 = (unsigned)max(897 + sh0, 1) << 20;
+                const unsigned K1 = (unsigned)(896 + sh1) << 23, mw1 = (unsigned)max(897 + sh1, 1) << 20;
+                df2 Gh[3];   // ss, st, tt
+#pragma unroll
+                for (int a = 0; a < 3; ++a) Gh[a] = split_g2(gv[a], hw0[a], hw1[a], K0, K1, mw0, mw1);
+                // y_s = Grs r + Gss s + Gst t,  y_t = Grt r + Gst s + Gtt t
+                acc2x2 bs = prod2(Gh[0], Vs);
+                dot2_step2(bs, Gh[1], Vt);
+                acc2x2 bt = prod2(Gh[1], Vs);
+                dot2_step2(bt, Gh[2], Vt);
+                // align the two halves' sums to the larger of their scales
+                const int sm0 = max(shA[q0], sh0), sm1 = max(shA[q0 + 1], sh1);
+                const float2 fa = make_float2(pow2f_or_zero(shA[q0] - sm0), pow2f_or_zero(shA[q0 + 1] - sm1));
+                const float2 fb = make_float2(pow2f_or_zero(sh0 - sm0), pow2f_or_zero(sh1 - sm1));
+                const df2 xs{__fmul2_rn(YSP[p].s, fa), __fmul2_rn(YSP[p].c, fa)}, zs{__fmul2_rn(bs.s, fb), __fmul2_rn(bs.c, fb)};
+                const df2 xt{__fmul2_rn(YTP[p].s, fa), __fmul2_rn(YTP[p].c, fa)}, zt{__fmul2_rn(bt.s, fb), __fmul2_rn(bt.c, fb)};
+                const df2 ts = two_sum2(xs.hi, zs.hi), tt = two_sum2(xt.hi, zt.hi);
+                const df2 sn = two_sum2(ts.hi, __fadd2_rn(__fadd2_rn(xs.lo, zs.lo), ts.lo));
+                const df2 tn = two_sum2(tt.hi, __fadd2_rn(__fadd2_rn(xt.lo, zt.lo), tt.lo));
+                YS[p] = acc2x2{sn.hi, sn.lo};
+                YT[p] = acc2x2{tn.hi, tn.lo};
+                shS[q0] = sm0;
+                shS[q0 + 1] = sm1;
+                const int es0 = (int)(__float_as_uint(fabsf(sn.hi.x)) >> 23), es1 = (int)(__float_as_uint(fabsf(sn.hi.y)) >> 23);
+                const int et0 = (int)(__float_as_uint(fabsf(tn.hi.x)) >> 23), et1 = (int)(__float_as_uint(fabsf(tn.hi.y)) >> 23);
+                if (es0) smax = max(smax, es0 + sm0);
+                if (es1) smax = max(smax, es1 + sm1);
+                if (et0) tmx = max(tmx, et0 + sm0);
+                if (et1) tmx = max(tmx, et1 + sm1);
+                if (eg0 == 0x7ff || eg1 == 0x7ff) smax = tmx = kBadExp;
             }
         smax = __reduce_max_sync(0xffffffffu, smax);
         tmx = __reduce_max_sync(0xffffffffu, tmx);
@@ -428,14 +417,14 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
             for (int h = 0; h < 2; ++h) {
                 const int q0 = 4 * nt + 2 * h;
                 float d0[kS10], d1[kS10];
-                digits10_df2_neg(make_float2(ys[q0].s, ys[q0 + 1].s), make_float2(ys[q0].c, ys[q0 + 1].c),
+                digits10_df2_neg(YS[2 * nt + h].s, YS[2 * nt + h].c,
                                  make_float2(pow2f_or_zero(shS[q0] - eS + 135), pow2f_or_zero(shS[q0 + 1] - eS + 135)),
                                  make_float2(pow2f_or_zero(shS[q0] - eS + 155), pow2f_or_zero(shS[q0 + 1] - eS + 155)), d0, d1);
                 // block (rows j = 8h.., columns i = 8nt..) transposed: the B fragment of
                 // K rows l = 8h.. (b0 for h = 0, b1 for h = 1) of n-tile nt
 #pragma unroll
                 for (int d = 0; d < kS10; ++d) yb[d][2 * nt + h] = mma::movm_t(pack_f16(d0[d], d1[d]));
-                digits10_df2_neg(make_float2(yt[q0].s, yt[q0 + 1].s), make_float2(yt[q0].c, yt[q0 + 1].c),
+                digits10_df2_neg(YT[2 * nt + h].s, YT[2 * nt + h].c,
                                  make_float2(pow2f_or_zero(shS[q0] - eT + 135), pow2f_or_zero(shS[q0 + 1] - eT + 135)),
                                  make_float2(pow2f_or_zero(shS[q0] - eT + 155), pow2f_or_zero(shS[q0 + 1] - eT + 155)), d0, d1);
                 unsigned char *p = ud + pch(k, g + 8 * h, nt) + 4 * t;
@@ -489,28 +478,32 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
         const int base = (eU - 1022) + 2 * (eD - 1022) - 126 - 36;
         const int SHr = base + eR, SHs = base + eS, SHt = base + eT;
         const int SHm = max(SHr, max(SHs, SHt));
+        const float2 fr = f2(pow2f_or_zero(SHr - SHm)), fs = f2(pow2f_or_zero(SHs - SHm)), ft = f2(pow2f_or_zero(SHt - SHm));
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = g + 8 * h;
                 const float4 tv = tb[tslot(k, j, 4 * nt + t)];
+                const int q0 = 4 * nt + 2 * h;
+                // the node pair lane-wise: the three parts aligned to 2^SHm, summed in double-float
+                const df2 wa = pack_df2(wr_[q0], wr_[q0 + 1]), wb = pack_df2(ws_[q0], ws_[q0 + 1]);
+                const df2 a{__fmul2_rn(wa.hi, fr), __fmul2_rn(wa.lo, fr)}, b{__fmul2_rn(wb.hi, fs), __fmul2_rn(wb.lo, fs)};
+                const df2 cc{__fmul2_rn(make_float2(tv.x, tv.z), ft), __fmul2_rn(make_float2(tv.y, tv.w), ft)};
+                const df2 s1 = two_sum2(a.hi, b.hi);
+                const df2 s2 = two_sum2(s1.hi, cc.hi);
+                const float2 lo = __fadd2_rn(__fadd2_rn(__fadd2_rn(a.lo, b.lo), cc.lo), __fadd2_rn(s1.lo, s2.lo));
                 double o[2];
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    const int q = 4 * nt + 2 * h + c;
-                    const df a = scale_df(wr_[q], SHr - SHm), b = scale_df(ws_[q], SHs - SHm);
-                    const df cc = scale_df(c ? df{tv.z, tv.w} : df{tv.x, tv.y}, SHt - SHm);
-                    const df s1 = dfx::two_sum(a.hi, b.hi);
-                    const df s2 = dfx::two_sum(s1.hi, cc.hi);
-                    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(a.lo, b.lo), cc.lo), __fadd_rn(s1.lo, s2.lo));
+                    const float vh = c ? s2.hi.y : s2.hi.x, vl = c ? lo.y : lo.x;
                     // bit-level conversions and scaling: one FP64 add per node (the whole
                     // CTA runs this phase at once, so FP64-pipe work here is not hidden)
                     double dh, dl;
-                    if (dfx::f2d_scaled(s2.hi, SHm, dh) && dfx::f2d_scaled(lo, SHm, dl))
+                    if (dfx::f2d_scaled(vh, SHm, dh) && dfx::f2d_scaled(vl, SHm, dl))
                         o[c] = dh + dl;
                     else
-                        o[c] = scale2(dfx::f2d(s2.hi) + dfx::f2d(lo), SHm);
+                        o[c] = scale2(dfx::f2d(vh) + dfx::f2d(vl), SHm);
                     if (bad) o[c] = __longlong_as_double(0x7ff8000000000000ll);
                 }
                 *reinterpret_cast<double2 *>(we + k * 256 + j * 16 + 8 * nt + 2 * t) = make_double2(o[0], o[1]);
