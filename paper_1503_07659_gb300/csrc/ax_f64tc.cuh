@@ -16,7 +16,16 @@ namespace semax {
 namespace oz {
 
 using dfx::acc2;
+using dfx::acc2x2;
 using dfx::df;
+using dfx::df2;
+using dfx::dot2_step2;
+using dfx::dot3_2;
+using dfx::f2;
+using dfx::pack_df2;
+using dfx::prod2;
+using dfx::sub2;
+using dfx::two_sum2;
 using mma::smem_u32;
 
 constexpr int kBadExp = 1 << 20;             // marks a non-finite input in the exponent reductions
@@ -150,7 +159,7 @@ __device__ __forceinline__ void digits10_df(float hi, float lo, float m, float m
 // (fma/add/mul.rn.f32x2: two results per instruction slot).  A - B is
 // formed as fma(B, -1, A), exact wherever the scalar form's subtraction is.
 
-__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
 
 // digits10_df of two values at once, the digits NEGATED: every step is the
 // scalar form's with -q = C - (t + C) computed as fma(t + C, -1, C) (exact),
@@ -197,26 +206,6 @@ __device__ __forceinline__ void combine5_k8x2(const float (&x)[kS10][4], int e, 
     v1 = df{s2.y, lo.y};
 }
 
-// Double-float values of two nodes, lane-wise.
-struct df2 {
-    float2 hi, lo;
-};
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }   // a - b
-
-__device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
-    const float2 s = __fadd2_rn(a, b);
-    const float2 bb = sub2(s, a);
-    return {s, __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb))};
-}
-
-// Dot2 accumulators of two nodes, lane-wise, and the double-float
-// geometric-factor arithmetic on them (each step the scalar form's, in the
-// same order, so the results are bit-identical).
-struct acc2x2 {
-    float2 s, c;
-};
-__device__ __forceinline__ df2 pack_df2(df a, df b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
-
 // split_g of two values (x.x with hw0, K0, mw0; x.y with hw1, K1, mw1)
 __device__ __forceinline__ df2 split_g2(double2 x, unsigned hw0, unsigned hw1, unsigned K0, unsigned K1, unsigned mw0,
                                         unsigned mw1) {
@@ -233,32 +222,6 @@ __device__ __forceinline__ df2 split_g2(double2 x, unsigned hw0, unsigned hw1, u
     const float2 p = __fmul2_rn(r, sc);
     return {make_float2(hi0, hi1), make_float2(__uint_as_float(__float_as_uint(p.x) | (h0 & 0x80000000u)),
                                                __uint_as_float(__float_as_uint(p.y) | (h1 & 0x80000000u)))};
-}
-
-// a * x lane-wise (the exact product of the high parts plus the cross terms)
-__device__ __forceinline__ acc2x2 prod2(const df2 &a, const df2 &x) {
-    const float2 m = __fmul2_rn(a.hi, x.hi);
-    float2 r = __ffma2_rn(a.hi, x.hi, make_float2(-m.x, -m.y));
-    r = __ffma2_rn(a.hi, x.lo, r);
-    r = __ffma2_rn(a.lo, x.hi, r);
-    return {m, r};
-}
-
-// a += p * x lane-wise (dot2_step)
-__device__ __forceinline__ void dot2_step2(acc2x2 &a, const df2 &p, const df2 &x) {
-    const acc2x2 q = prod2(p, x);
-    const df2 t = two_sum2(a.s, q.s);
-    a.s = t.hi;
-    a.c = __fadd2_rn(a.c, __fadd2_rn(q.c, t.lo));
-}
-
-// dot3 lane-wise
-__device__ __forceinline__ acc2x2 dot3_2(const df2 &g0, const df2 &g1, const df2 &g2, const df2 &v0, const df2 &v1,
-                                         const df2 &v2) {
-    acc2x2 a = prod2(g0, v0);
-    dot2_step2(a, g1, v1);
-    dot2_step2(a, g2, v2);
-    return a;
 }
 
 // combine5 of the outputs e and e + 1 (bit for bit the scalar form)

@@ -85,6 +85,69 @@ __device__ __forceinline__ df acc_add(acc2 a, acc2 b) {
 }
 __device__ __forceinline__ df acc_sub(acc2 a, acc2 b) { return acc_add(a, acc2{-b.s, -b.c}); }
 
+// ---- two lanes at once with the packed FP32 instructions (fma/add/mul.rn.f32x2:
+// two results per issue slot).  Each lane takes the scalar form's steps in
+// the same order, so the results are bit-identical; a - b is formed as
+// fma(b, -1, a), exact like the subtraction.
+
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// Double-float values of two nodes, lane-wise.
+struct df2 {
+    float2 hi, lo;
+};
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }   // a - b
+
+__device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bb = sub2(s, a);
+    return {s, __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+
+// fast_two_sum lane-wise (|a| >= |b| in each lane)
+__device__ __forceinline__ df2 fast_two_sum2(float2 a, float2 b) {
+    const float2 s = __fadd2_rn(a, b);
+    return {s, sub2(b, sub2(s, a))};
+}
+
+// add(a, b) lane-wise
+__device__ __forceinline__ df2 add2(const df2 &a, const df2 &b) {
+    const df2 s = two_sum2(a.hi, b.hi);
+    return fast_two_sum2(s.hi, __fadd2_rn(__fadd2_rn(a.lo, b.lo), s.lo));
+}
+
+// Dot2 accumulators of two lanes
+struct acc2x2 {
+    float2 s, c;
+};
+__device__ __forceinline__ df2 pack_df2(df a, df b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+
+// a * x lane-wise (the exact product of the high parts plus the cross terms)
+__device__ __forceinline__ acc2x2 prod2(const df2 &a, const df2 &x) {
+    const float2 m = __fmul2_rn(a.hi, x.hi);
+    float2 r = __ffma2_rn(a.hi, x.hi, make_float2(-m.x, -m.y));
+    r = __ffma2_rn(a.hi, x.lo, r);
+    r = __ffma2_rn(a.lo, x.hi, r);
+    return {m, r};
+}
+
+// a += p * x lane-wise (dot2_step)
+__device__ __forceinline__ void dot2_step2(acc2x2 &a, const df2 &p, const df2 &x) {
+    const acc2x2 q = prod2(p, x);
+    const df2 t = two_sum2(a.s, q.s);
+    a.s = t.hi;
+    a.c = __fadd2_rn(a.c, __fadd2_rn(q.c, t.lo));
+}
+
+// dot3 lane-wise
+__device__ __forceinline__ acc2x2 dot3_2(const df2 &g0, const df2 &g1, const df2 &g2, const df2 &v0, const df2 &v1,
+                                         const df2 &v2) {
+    acc2x2 a = prod2(g0, v0);
+    dot2_step2(a, g1, v1);
+    dot2_step2(a, g2, v2);
+    return a;
+}
+
 // x * 2^-sh split into hi + lo by bit operations (no FP64 instruction).
 // Values whose scaled magnitude is below the float range flush to zero.
 // Inf and NaN are not representable here (they come out finite): the tile
@@ -135,48 +198,38 @@ __device__ __forceinline__ int biased_exponent(double x) {
     return (int)((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7ffu);
 }
 
-// h coefficients (df) from shared memory; volatile so they are not hoisted
-template <int h>
-__device__ __forceinline__ void ld_coef(const df *p, df (&c)[h]) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    if constexpr (h % 2 == 0) {
-#pragma unroll
-        for (int q = 0; q < h / 2; ++q)
-            asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
-                         : "=f"(c[2 * q].hi), "=f"(c[2 * q].lo), "=f"(c[2 * q + 1].hi), "=f"(c[2 * q + 1].lo)
-                         : "r"(a + 16 * q));
-    } else {
-#pragma unroll
-        for (int q = 0; q < h; ++q)
-            asm volatile("ld.shared.v2.f32 {%0,%1}, [%2];" : "=f"(c[q].hi), "=f"(c[q].lo) : "r"(a + 8 * q));
-    }
-}
-
-// y = M x by the even/odd split (P, Q: h x h df, row-major); each output
-// pair is written to shared memory as soon as it is formed (y[l * stride]),
-// so no output array stays live in registers.
+// y = M x by the even/odd split, the even and the odd sums as the two lanes
+// of one packed Dot2 chain; each output pair is written to shared memory as
+// soon as it is formed (y[l * stride]), so no output array stays live.  PQ[i * h + l] holds (P.hi, Q.hi, P.lo, Q.lo) of entry (i, l),
+// one 16-byte load; lane 0 forms e = x_l + x_{n-1-l} and pe, lane 1
+// o = x_l - x_{n-1-l} and qo, and the output pair (qo + pe, qo - pe) is
+// formed the same way.  Bit for bit the scalar form.
 template <int n>
-__device__ __forceinline__ void eo_apply_st(const df (&x)[n], const df *P, const df *Q, df *y, int stride) {
+__device__ __forceinline__ void eo_apply_st2(const df (&x)[n], const float4 *PQ, df *y, int stride) {
     constexpr int h = n / 2;
-    df e[h], o[h];
+    df2 eo[h];
 #pragma unroll
     for (int l = 0; l < h; ++l) {
-        e[l] = add(x[l], x[n - 1 - l]);
-        o[l] = sub(x[l], x[n - 1 - l]);
+        const df xr = x[n - 1 - l];
+        eo[l] = add2(df2{f2(x[l].hi), f2(x[l].lo)}, df2{make_float2(xr.hi, -xr.hi), make_float2(xr.lo, -xr.lo)});
     }
+    const unsigned base = (unsigned)__cvta_generic_to_shared(PQ);
 #pragma unroll 1
     for (int i = 0; i < h; ++i) {
-        df p[h], q[h];
-        ld_coef<h>(P + i * h, p);
-        ld_coef<h>(Q + i * h, q);
-        acc2 pe{0.f, 0.f}, qo{0.f, 0.f};
+        acc2x2 a{f2(0.f), f2(0.f)};
 #pragma unroll
         for (int l = 0; l < h; ++l) {
-            dot2_step(pe, p[l], e[l]);
-            dot2_step(qo, q[l], o[l]);
+            df2 c;   // volatile: the coefficients are not hoisted out of the i loop
+            asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                         : "=f"(c.hi.x), "=f"(c.hi.y), "=f"(c.lo.x), "=f"(c.lo.y)
+                         : "r"(base + 16u * (unsigned)(i * h + l)));
+            dot2_step2(a, c, eo[l]);
         }
-        y[i * stride] = acc_add(qo, pe);
-        y[(n - 1 - i) * stride] = acc_sub(qo, pe);
+        // lane 0: qo + pe, lane 1: qo - pe
+        const df2 t = two_sum2(f2(a.s.y), make_float2(a.s.x, -a.s.x));
+        const df2 r = fast_two_sum2(t.hi, __fadd2_rn(__fadd2_rn(f2(a.c.y), make_float2(a.c.x, -a.c.x)), t.lo));
+        y[i * stride] = df{r.hi.x, r.lo.x};
+        y[(n - 1 - i) * stride] = df{r.hi.y, r.lo.y};
     }
 }
 
@@ -241,8 +294,8 @@ __device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__rest
     constexpr int n2 = n * n, n3 = n * n * n, h = n / 2;
     constexpr int RP = eo_row_pitch<double>(n), PP = eo_plane_pitch<double>(n), EP = eo_elem_pitch<double>(n);
     double *sD = reinterpret_cast<double *>(smem_raw);
-    df *coef = reinterpret_cast<df *>(sD + round_up(n2, 2));
-    int *sexp = reinterpret_cast<int *>(coef + 4 * h * h);      // [0, epb): u, [epb, 2 epb): w
+    float4 *coef = reinterpret_cast<float4 *>(sD + round_up(n2, 2));   // [2][h * h]: (P, Q), (Pt, Qt) interleaved
+    int *sexp = reinterpret_cast<int *>(coef + 2 * h * h);      // [0, epb): u, [epb, 2 epb): w
     df *su = reinterpret_cast<df *>(sexp + round_up(2 * epb, 4));
     df *sr = su + cnt * EP, *ss = sr + cnt * EP;   // the t-direction reuses su
 
@@ -275,10 +328,10 @@ __device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__rest
         const int i = q / h, l = q - (q / h) * h;
         const double a = sD[i * n + l], b = sD[i * n + (n - 1 - l)];
         const double at = sD[l * n + i], bt = sD[(n - 1 - l) * n + i];
-        coef[q] = split_double(0.5 * (a + b), 0);
-        coef[h * h + q] = split_double(0.5 * (a - b), 0);
-        coef[2 * h * h + q] = split_double(0.5 * (at + bt), 0);
-        coef[3 * h * h + q] = split_double(0.5 * (at - bt), 0);
+        const df P = split_double(0.5 * (a + b), 0), Q = split_double(0.5 * (a - b), 0);
+        const df Pt = split_double(0.5 * (at + bt), 0), Qt = split_double(0.5 * (at - bt), 0);
+        coef[q] = make_float4(P.hi, Q.hi, P.lo, Q.lo);
+        coef[h * h + q] = make_float4(Pt.hi, Qt.hi, Pt.lo, Qt.lo);
     }
     for (int f = threadIdx.x; f < cnt * n3; f += blockDim.x) {
         const int e = f / n3, r = f - e * n3;
@@ -295,7 +348,7 @@ __device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__rest
     }
     __syncthreads();
 
-    const df *P = coef, *Q = coef + h * h, *Pt = coef + 2 * h * h, *Qt = coef + 3 * h * h;
+    const float4 *PQ = coef, *PQt = coef + h * h;
     const int lines = cnt * n2;
     // gradient, r- and s-lines
 #pragma unroll 1
@@ -307,7 +360,7 @@ __device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__rest
             const int stride = dir == 0 ? 1 : RP;
             df x[n];
             ld_line<n>(su + off, stride, x);
-            eo_apply_st<n>(x, P, Q, out + off, stride);
+            eo_apply_st2<n>(x, PQ, out + off, stride);
         }
     }
     __syncthreads();
@@ -318,7 +371,7 @@ __device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__rest
         const int off = e * EP + j * RP + i;
         df x[n];
         ld_line<n>(su + off, PP, x);
-        eo_apply_st<n>(x, P, Q, su + off, PP);
+        eo_apply_st2<n>(x, PQ, su + off, PP);
         const double *Gq = Ge + (size_t)e * 6 * n3 + ji;
         int mx = 0;
 #pragma unroll 2
@@ -345,7 +398,7 @@ __device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__rest
             const int stride = dir == 0 ? 1 : (dir == 1 ? RP : PP);
             df x[n];
             ld_line_split<n>(io + off, stride, sexp[epb + e] - 1023, x);
-            eo_apply_st<n>(x, Pt, Qt, io + off, stride);
+            eo_apply_st2<n>(x, PQt, io + off, stride);
         }
     }
     __syncthreads();
