@@ -259,6 +259,28 @@ def test_f64tc_max_size_offsets_past_2_31(semax, oracle_mod):
     assert r[0] / r[1] <= TYPICAL_TC
 
 
+def test_f64tc_order15_max_size_offsets_past_2_31(semax, oracle_mod):
+    """E = 90000 elements of order 15 (369M nodes, 24 GB): G's element
+    offsets pass 2^31 values from e = 87382 on (e * 6 * 4096), in the
+    persistent kernel whose CTAs walk the elements with a stride of the SM
+    count.  Checked against the oracle on elements on both sides of that
+    point and at the end, and against the FP64 kernel whole."""
+    base = si.make_mesh(np.random.default_rng(81), 16, 15, device="cuda")
+    E = 90000
+    G = base.G.repeat((E + 15) // 16, 1, 1, 1, 1)[:E].contiguous()
+    gen = torch.Generator(device="cuda").manual_seed(82)
+    u = torch.rand((E, 16, 16, 16), generator=gen, dtype=torch.float64, device="cuda") * 2 - 1
+    w = semax.sem_ax_f64tc(u, G, base.D)
+    torch.cuda.synchronize()
+    idx = np.array([0, 87381, 87382, 88000, E - 2, E - 1])
+    it = torch.from_numpy(idx).cuda()
+    ref = oracle_mod.sem_ax(u[it].cpu(), base.G[it.remainder(16)].cpu(), base.D.cpu())
+    assert rel_err(w[it], ref) <= TYPICAL_TC
+    w64 = semax.sem_ax(u, G, base.D)
+    r = semax.reduce(w, w64).cpu().numpy()
+    assert r[0] / r[1] <= TYPICAL_TC
+
+
 def test_energy_norm_on_the_gpu(semax, oracle_mod):
     """u^T A u with the FP64 reduction on the GPU: equal to the oracle's energy
     for the FP64 and both FP64-accurate forms, and positive for random u."""
