@@ -216,12 +216,10 @@ __device__ __forceinline__ df2 split_g2(double2 x, unsigned hw0, unsigned hw1, u
     const float2 r = __fadd2_rn(make_float2(__uint_as_float(0x4B000000u | ((l0 >> 6) & 0x7fffffu)),
                                             __uint_as_float(0x4B000000u | ((l1 >> 6) & 0x7fffffu))),
                                 f2(-8388608.0f));
-    const float2 sc = __fmul2_rn(make_float2(__uint_as_float(__float_as_uint(hi0) & 0x7f800000u),
-                                             __uint_as_float(__float_as_uint(hi1) & 0x7f800000u)),
-                                 f2(0x1p-46f));
-    const float2 p = __fmul2_rn(r, sc);
-    return {make_float2(hi0, hi1), make_float2(__uint_as_float(__float_as_uint(p.x) | (h0 & 0x80000000u)),
-                                               __uint_as_float(__float_as_uint(p.y) | (h1 & 0x80000000u)))};
+    const float2 sc = __fmul2_rn(make_float2(__uint_as_float(__float_as_uint(hi0) & 0xff800000u),
+                                             __uint_as_float(__float_as_uint(hi1) & 0xff800000u)),
+                                 f2(0x1p-46f));   // signed, as in split_g
+    return {make_float2(hi0, hi1), __fmul2_rn(r, sc)};
 }
 
 // combine5 of the outputs e and e + 1 (bit for bit the scalar form)
@@ -274,8 +272,9 @@ __device__ __forceinline__ df split_g(double x, unsigned hw, unsigned K, unsigne
     const unsigned f = __funnelshift_l(l32, h32, 3);
     const float hi = hw >= min_word ? __uint_as_float((f - K) | (h32 & 0x80000000u)) : 0.0f;
     const float r = __fsub_rn(__uint_as_float(0x4B000000u | ((l32 >> 6) & 0x7fffffu)), 8388608.0f);
-    const float sc = __fmul_rn(__uint_as_float(__float_as_uint(hi) & 0x7f800000u), 0x1p-46f);   // 0 with hi
-    return {hi, __uint_as_float(__float_as_uint(__fmul_rn(r, sc)) | (h32 & 0x80000000u))};
+    // 2^(ef - 127 - 46) with hi's sign (so lo takes x's sign), 0 with hi
+    const float sc = __fmul_rn(__uint_as_float(__float_as_uint(hi) & 0xff800000u), 0x1p-46f);
+    return {hi, __fmul_rn(r, sc)};
 }
 
 // y = sum_b Gh[b] V[b] (double-float products, Dot2-style accumulation)

@@ -163,8 +163,8 @@ __device__ __forceinline__ df split_double(double x, int sh) {
     const unsigned f = __funnelshift_l(l32, h32, 3);
     const float hi = (h32 & 0x7fffffffu) >= min_word ? __uint_as_float((f - ((unsigned)(896 + sh) << 23)) | sign) : 0.f;
     const float r = __fsub_rn(__uint_as_float(0x4B000000u | ((l32 >> 6) & 0x7fffffu)), 8388608.0f);   // r23
-    const float sc = __fmul_rn(__uint_as_float(__float_as_uint(hi) & 0x7f800000u), 0x1p-46f);   // 2^(ef-127-46)
-    return {hi, __uint_as_float(__float_as_uint(__fmul_rn(r, sc)) | sign)};
+    const float sc = __fmul_rn(__uint_as_float(__float_as_uint(hi) & 0xff800000u), 0x1p-46f);   // +-2^(ef-127-46)
+    return {hi, __fmul_rn(r, sc)};   // lo takes hi's sign through sc
 }
 
 // a float (normal or zero) as a double, exactly, by bit operations
