@@ -190,7 +190,6 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
     if (blockIdx.x < E) prefetch_u(blockIdx.x);
 
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
-        const float *ue = u + e * 4096;
         const float *Ge = G + e * (GEO ? 24 : 6 * 4096);
         float *we = w + e * 4096;
         if (GEO && tid < 24) {   // trilinear map coefficients of this element

@@ -239,8 +239,8 @@ __device__ __forceinline__ void ld_line(const df *p, int stride, df (&x)[n]) {
 #pragma unroll
         for (int q = 0; q < n / 2; ++q) {
             const float4 v = reinterpret_cast<const float4 *>(p)[q];
-            x[2 * q] = {v.x, v.y};
-            x[2 * q + 1] = {v.z, v.w};
+            x[2 * q] = df{v.x, v.y};
+            x[2 * q + 1] = df{v.z, v.w};
         }
     } else {
 #pragma unroll
