@@ -329,6 +329,13 @@ def variants(semax, reps: int) -> dict:
     r["arith"] = "double-float tiles (FP64 in/out, FP64-accurate) in the one persistent launch"
     out["batched_plan_f64x_mix"] = r
     planx.close()
+    plantc = semax.Plan([(x.N, x.u, x.G, x.D, w) for x, w in zip(mix, ws)], f64x=True, f64tc=True)
+    r = rate(plantc, dofs, dofs * bytes_per_node(8))
+    r["rel_err_vs_f64"] = max(rel_err_gpu(semax, w, rw) for w, rw in zip(ws, ref_ws))
+    r["arith"] = ("orders 7 and 15 on the tensor-core FP64-accurate kernels beside the persistent launch "
+                  "(forked stream in the same graph), the other even orders on the double-float tile")
+    out["batched_plan_f64tc_mix"] = r
+    plantc.close()
     del ref_ws
     out["mix_orders"] = {x.N: x.E for x in mix}
     plan.close()

@@ -13,7 +13,8 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import SemaxError, semax_group, check, SEMAX_F32, SEMAX_F64
+from ._lib import (SemaxError, semax_group, check, SEMAX_F32, SEMAX_F64, SEMAX_PLAN_F64X, SEMAX_PLAN_F64TC,
+                   SEMAX_PCG_F64X, SEMAX_PCG_F64TC, SEMAX_PCG_MIXED)
 
 __all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_bf16x3_geo", "sem_ax_batched", "Plan", "reduce",
            "sem_ax_from_host", "SemaxError", "library_path"]
@@ -130,11 +131,13 @@ def sem_ax_batched(groups, workspace: torch.Tensor | None = None, stream=None) -
 class Plan:
     """Graph-captured persistent batched launch (see sem_ax_plan_create)."""
 
-    def __init__(self, groups, tune: bool = False, cache_path: str | None = None, f64x: bool = False):
+    def __init__(self, groups, tune: bool = False, cache_path: str | None = None, f64x: bool = False,
+                 f64tc: bool = False):
         self._arr, ng = _groups(groups)
         self._handle = ctypes.c_void_p()
+        flags = (SEMAX_PLAN_F64X if f64x else 0) | (SEMAX_PLAN_F64TC if f64tc else 0)
         check(_lib.lib().sem_ax_plan_create(ctypes.byref(self._handle), self._arr, ng, int(bool(tune)),
-                                            cache_path.encode() if cache_path else None, 1 if f64x else 0),
+                                            cache_path.encode() if cache_path else None, flags),
               "sem_ax_plan_create")
 
     def __call__(self, stream=None) -> None:
@@ -241,7 +244,8 @@ class PCG:
                  f64tc: bool = False, mixed: bool = False):
         self._keep = (G, D, gs)
         self._handle = ctypes.c_void_p()
-        flags = (1 if f64x else 0) | (2 if f64tc else 0) | (4 if mixed else 0)
+        flags = ((SEMAX_PCG_F64X if f64x else 0) | (SEMAX_PCG_F64TC if f64tc else 0)
+                 | (SEMAX_PCG_MIXED if mixed else 0))
         check(_lib.lib().sem_pcg_create(ctypes.byref(self._handle), G.shape[0], D.shape[0] - 1, _ptr(G), _ptr(D),
                                         gs._handle, flags), "sem_pcg_create")
 

@@ -26,6 +26,7 @@ namespace semax {
 
 constexpr int kMaxGroups = 32;
 constexpr int MAP_F64X = 3;   // the double-float FP64-accurate tile (even n)
+constexpr int MAP_F64TC = 4;  // orders 7 and 15 under SEMAX_PLAN_F64TC: the tensor-core form, own launch
 constexpr int kBatchThreads = 256;
 
 struct GroupDev {
@@ -262,7 +263,8 @@ extern "C" int sem_ax_batched(const semax_group *groups, int ngroups, void *work
 // ---------------------------------------------------------------- plans and tuning
 
 struct semax_plan {
-    BatchParams P;
+    BatchParams P;                    // the groups of the persistent launch
+    std::vector<semax_group> tc;      // SEMAX_PLAN_F64TC: the groups of order 7 and 15 (own launches)
     std::vector<TileChoice> choice;   // by n
     unsigned long long *counter = nullptr;
     cudaGraph_t graph = nullptr;
@@ -379,10 +381,19 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
                                   const char *cache_path, int flags) {
     if (!plan) return SEMAX_EINVAL;
     *plan = nullptr;
-    if (flags & ~SEMAX_PLAN_F64X) return SEMAX_EINVAL;
+    if (flags & ~(SEMAX_PLAN_F64X | SEMAX_PLAN_F64TC)) return SEMAX_EINVAL;
     int st = check_groups(groups, ngroups);
     if (st != SEMAX_OK) return st;
     semax_plan *p = new semax_plan();
+    // SEMAX_PLAN_F64TC: orders 7 and 15 leave the persistent launch for the
+    // tensor-core FP64-accurate kernels, captured on a forked stream beside it
+    std::vector<semax_group> rest;
+    for (int q = 0; q < ngroups; ++q) {
+        if ((flags & SEMAX_PLAN_F64TC) && (groups[q].N == 7 || groups[q].N == 15))
+            p->tc.push_back(groups[q]);
+        else
+            rest.push_back(groups[q]);
+    }
     p->choice.assign(17, TileChoice{1, MAP_COLUMN});
     for (int n = 2; n <= 16; ++n) p->choice[n] = default_choice(n);
     std::vector<bool> have(17, false);
@@ -399,14 +410,14 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
         for (int n = 2; n <= 16 && st == SEMAX_OK; ++n) {
             if ((flags & SEMAX_PLAN_F64X) && n % 2 == 0) continue;   // fixed double-float tile
             int best_g = -1;
-            for (int q = 0; q < ngroups; ++q)
-                if (groups[q].N + 1 == n && groups[q].E > 0 && (best_g < 0 || groups[q].E > groups[best_g].E))
+            for (int q = 0; q < (int)rest.size(); ++q)
+                if (rest[q].N + 1 == n && rest[q].E > 0 && (best_g < 0 || rest[q].E > rest[best_g].E))
                     best_g = q;
             if (best_g < 0) continue;
             float best = 1e30f;
             for (TileChoice c : candidates(n)) {
                 float t = 0.f;
-                st = time_candidate(groups[best_g], c, p->counter, cs, &t);
+                st = time_candidate(rest[best_g], c, p->counter, cs, &t);
                 if (st != SEMAX_OK) break;
                 if (t < best) { best = t; p->choice[n] = c; }
             }
@@ -418,18 +429,42 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
 
     if (st == SEMAX_OK && (flags & SEMAX_PLAN_F64X))
         for (int n = 2; n <= 16; n += 2) p->choice[n] = TileChoice{f64x_epb(n), MAP_F64X};
+    cudaStream_t cs2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (st == SEMAX_OK && !p->tc.empty()) {
+        st = cuda_status(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
+        if (st == SEMAX_OK) st = cuda_status(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        if (st == SEMAX_OK) st = cuda_status(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    }
     if (st == SEMAX_OK) {
-        build_params(p->P, groups, ngroups, p->choice);
+        build_params(p->P, rest.data(), (int)rest.size(), p->choice);
         LaunchShape ls;
-        st = prepare_batched(p->P, &ls);
+        if (!rest.empty()) st = prepare_batched(p->P, &ls);
         if (st == SEMAX_OK) st = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         if (st == SEMAX_OK) {
-            int lst = enqueue_batched(p->P, ls, p->counter, cs);
+            int lst = SEMAX_OK;
+            if (!p->tc.empty()) {   // fork: the tensor-core groups on cs2, joined back before the end
+                lst = cuda_status(cudaEventRecord(fork, cs));
+                if (lst == SEMAX_OK) lst = cuda_status(cudaStreamWaitEvent(cs2, fork, 0));
+                for (size_t q = 0; q < p->tc.size() && lst == SEMAX_OK; ++q) {
+                    const semax_group &g = p->tc[q];
+                    if (g.E > 0) lst = sem_ax_f64tc(g.E, g.N, g.u, g.G, g.D, g.w, cs2);
+                }
+                if (lst == SEMAX_OK) lst = cuda_status(cudaEventRecord(join, cs2));
+            }
+            if (lst == SEMAX_OK && !rest.empty()) lst = enqueue_batched(p->P, ls, p->counter, cs);
+            if (!p->tc.empty()) {
+                const int jst = cuda_status(cudaStreamWaitEvent(cs, join, 0));
+                if (lst == SEMAX_OK) lst = jst;
+            }
             int est = cuda_status(cudaStreamEndCapture(cs, &p->graph));
             st = lst != SEMAX_OK ? lst : est;
         }
         if (st == SEMAX_OK) st = cuda_status(cudaGraphInstantiate(&p->exec, p->graph, 0));
     }
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (cs2) cudaStreamDestroy(cs2);
     if (cs) cudaStreamDestroy(cs);
     if (st != SEMAX_OK) {
         destroy_plan(p);
@@ -452,6 +487,13 @@ extern "C" int sem_ax_plan_destroy(semax_plan *plan) {
 
 extern "C" int sem_ax_plan_config(const semax_plan *plan, int N, int *elems_per_tile, int *mapping) {
     if (!plan || plan->magic != 0x5e3a9u) return SEMAX_ENOPLAN;
+    for (const semax_group &g : plan->tc) {
+        if (g.N == N) {   // launched apart, one element per CTA pass
+            if (elems_per_tile) *elems_per_tile = 1;
+            if (mapping) *mapping = MAP_F64TC;
+            return SEMAX_OK;
+        }
+    }
     for (int q = 0; q < plan->P.ngroups; ++q) {
         if (plan->P.g[q].n == N + 1) {
             if (elems_per_tile) *elems_per_tile = plan->P.g[q].epb;

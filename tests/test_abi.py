@@ -114,3 +114,21 @@ def test_bf16_geo_validation(lib):
     assert f(4, 15, u, None, xq, D, w, 3, None) == -1
     assert f(4, 15, u + 4, X, xq, D, w, 3, None) == -3
     assert f(4, 15, u, X, xq, D, u + 64, 3, None) == -4
+
+
+def test_binding_constants_match_the_header():
+    """The flag and enum values the Python binding passes are the header's."""
+    import paper_1503_07659_gb300._lib as L
+    text = open(os.path.join(ROOT, "include", "semax.h")).read()
+    vals = dict((k, int(v)) for k, v in re.findall(r"\b(SEMAX_[A-Z0-9_]+)\s*=\s*(-?\d+)", text))
+    for name in ("SEMAX_F64", "SEMAX_F32", "SEMAX_PLAN_F64X", "SEMAX_PLAN_F64TC", "SEMAX_PCG_F64X",
+                 "SEMAX_PCG_F64TC", "SEMAX_PCG_MIXED"):
+        assert getattr(L, name) == vals[name], name
+    for code, name in L.STATUS_NAMES.items():
+        assert vals[name] == code, name
+
+
+def test_plan_rejects_unknown_flags(lib):
+    h = ctypes.c_void_p()
+    assert lib.sem_ax_plan_create(ctypes.byref(h), None, 0, 0, None, 8) == -1   # SEMAX_EINVAL
+    assert lib.sem_ax_plan_create(ctypes.byref(h), None, 0, 0, None, 4) == -1

@@ -117,6 +117,60 @@ def test_plan_f64x_with_odd_orders_and_tuning(semax, oracle_mod):
     plan.close()
 
 
+@pytest.mark.parametrize("f64x", [False, True])
+def test_plan_with_tensor_core_orders(semax, mix, f64x):
+    """SEMAX_PLAN_F64TC: the groups of order 7 and 15 run sem_ax_f64tc beside
+    the persistent launch (a forked stream in the captured graph) and equal
+    that call bit for bit; the other groups equal the plan without the flag,
+    bit for bit, so the fork and join change nothing else.  Replays agree."""
+    ws = [torch.full_like(m.u, float("nan")) for m in mix]
+    plan = semax.Plan(_groups(mix, ws), f64x=f64x, f64tc=True)
+    plan()
+    torch.cuda.synchronize()
+    ws0 = [torch.full_like(m.u, float("nan")) for m in mix]
+    base = semax.Plan(_groups(mix, ws0), f64x=f64x)
+    base()
+    torch.cuda.synchronize()
+    for m, w, w0 in zip(mix, ws, ws0):
+        if m.N in (7, 15):
+            assert plan.config(m.N) == (1, 4)
+            assert torch.equal(w, semax.sem_ax_f64tc(m.u, m.G, m.D)), m.N
+        else:
+            assert plan.config(m.N) == base.config(m.N)
+            assert torch.equal(w, w0), m.N
+    first = [w.clone() for w in ws]
+    plan()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(first, ws))
+    plan.close()
+    base.close()
+
+
+def test_plan_tensor_core_orders_only_and_tuning(semax, oracle_mod):
+    """A plan whose groups all take the tensor-core kernels has no
+    persistent launch; with tuning, only the other orders are timed."""
+    rng = np.random.default_rng(29)
+    tc = [si.make_mesh(rng, E, N, device="cuda") for N, E in [(7, 9), (15, 3), (7, 1)]]
+    ws = [torch.empty_like(m.u) for m in tc]
+    plan = semax.Plan(_groups(tc, ws), f64tc=True)
+    plan()
+    torch.cuda.synchronize()
+    for m, w in zip(tc, ws):
+        ref = oracle_mod.sem_ax(m.u.cpu(), m.G.cpu(), m.D.cpu())
+        assert np.max(np.abs(w.cpu().numpy() - ref)) / np.max(np.abs(ref)) <= 2e-13, m.N
+    plan.close()
+    mixed = tc + [si.make_mesh(rng, E, N, device="cuda") for N, E in [(3, 20), (5, 6)]]
+    ws = [torch.empty_like(m.u) for m in mixed]
+    plan = semax.Plan(_groups(mixed, ws), tune=True, f64x=True, f64tc=True)
+    plan()
+    torch.cuda.synchronize()
+    for m, w in zip(mixed, ws):
+        ref = oracle_mod.sem_ax(m.u.cpu(), m.G.cpu(), m.D.cpu())
+        assert np.max(np.abs(w.cpu().numpy() - ref)) / np.max(np.abs(ref)) <= 1e-12, m.N
+    assert plan.config(7)[1] == 4 and plan.config(3)[1] == 3 and plan.config(5)[1] == 3
+    plan.close()
+
+
 @pytest.mark.parametrize("count", [1, 1000, 3 * 1024 * 1024 + 7])
 def test_reduce_against_definition(semax, oracle_mod, count):
     g = torch.Generator(device="cpu").manual_seed(count)
