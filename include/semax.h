@@ -121,6 +121,22 @@ int sem_ax_f64x(int64_t E, int N, const double *u, const double *G, const double
 int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const double *D,
                  double *w, void *stream);
 
+/* The tensor-core FP64-accurate Ax with the geometric factor prepared once
+ * (for repeated applications with the same G, as in an iterative solver).
+ * sem_ax_f64tc_prepare splits each node's six G entries into (hi, lo) float
+ * pairs after the per-node power-of-two scale, exactly as sem_ax_f64tc does
+ * on every call, and keeps each node's largest biased exponent: per element
+ * 6 n^3 float pairs followed by n^3 int32, E * 26624 bytes at N = 7
+ * (sem_ax_f64tc_prepare_size), the same HBM traffic per call as FP64 G.
+ * sem_ax_f64tc_prepared then computes, bit for bit, what sem_ax_f64tc
+ * computes from G, without the split.  N = 7 only (SEMAX_EUNSUPPORTED_N
+ * otherwise).  Gp: device memory, 16-byte aligned, owned by the caller, not
+ * overlapping G or w. */
+int sem_ax_f64tc_prepare_size(int64_t E, int N, size_t *bytes);
+int sem_ax_f64tc_prepare(int64_t E, int N, const double *G, void *Gp, void *stream);
+int sem_ax_f64tc_prepared(int64_t E, int N, const double *u, const void *Gp, const double *D,
+                          double *w, void *stream);
+
 /* FP32 storage and FP32 compute.  G_scale is NULL or [E] per-element factors
  * s_e: the kernel then treats the stored G as G_e / s_e and multiplies the
  * element's result by s_e (use powers of two so that this is exact). */
@@ -239,7 +255,9 @@ int sem_ax_diag(int64_t E, int N, const double *G, const double *D, double *diag
  * masked.  Create allocates the work vectors and computes the preconditioner;
  * G, D and gs stay bound to the solver; flags = 0 applies A with the FP64
  * kernel of sem_ax, SEMAX_PCG_F64X with that of sem_ax_f64x, SEMAX_PCG_F64TC
- * with that of sem_ax_f64tc (at most one of the two flags).  SEMAX_PCG_MIXED
+ * with that of sem_ax_f64tc (at most one of the two flags; at N = 7 from G
+ * prepared once at create, sem_ax_f64tc_prepared, E * 26624 bytes more
+ * device memory, the same results bit for bit).  SEMAX_PCG_MIXED
  * (combinable with either) is mixed-precision iterative refinement: each
  * outer step computes the true residual r = b - A x with the FP64-accurate
  * operator, solves A d = r from d = 0 by PCG whose recurrences are FP64 but

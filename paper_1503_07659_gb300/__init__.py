@@ -81,6 +81,32 @@ def sem_ax_f64tc(u: torch.Tensor, G: torch.Tensor, D: torch.Tensor, w: torch.Ten
     return w
 
 
+def f64tc_prepare(G: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The prepared geometric factor of sem_ax_f64tc_prepared (order 7): a
+    uint8 device tensor of E * 26624 bytes."""
+    if G.dim() != 5 or G.shape[1] != 6:
+        raise ValueError("f64tc_prepare: G must be [E, 6, n, n, n]")
+    E, N = G.shape[0], G.shape[2] - 1
+    size = ctypes.c_size_t(0)
+    check(_lib.lib().sem_ax_f64tc_prepare_size(E, N, ctypes.byref(size)), "sem_ax_f64tc_prepare_size")
+    if out is None:
+        out = torch.empty(size.value, dtype=torch.uint8, device=G.device)
+    elif out.numel() * out.element_size() < size.value:
+        raise ValueError("f64tc_prepare: out too small")
+    check(_lib.lib().sem_ax_f64tc_prepare(E, N, _ptr(G), _ptr(out), _stream(stream)), "sem_ax_f64tc_prepare")
+    return out
+
+
+def sem_ax_f64tc_prepared(u: torch.Tensor, Gp: torch.Tensor, D: torch.Tensor, w: torch.Tensor | None = None,
+                          stream=None) -> torch.Tensor:
+    """sem_ax_f64tc with the geometric factor from f64tc_prepare, bit for bit."""
+    E, N = _dims(u, D)
+    w = _out(w, u)
+    check(_lib.lib().sem_ax_f64tc_prepared(E, N, _ptr(u), _ptr(Gp), _ptr(D), _ptr(w), _stream(stream)),
+          "sem_ax_f64tc_prepared")
+    return w
+
+
 def sem_ax_f32(u, G, D, w=None, G_scale=None, stream=None) -> torch.Tensor:
     """FP32 storage and compute; optional per-element G scale [E]."""
     E, N = _dims(u, D)

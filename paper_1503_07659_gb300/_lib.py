@@ -25,7 +25,8 @@ STATUS_NAMES = {
 
 # every symbol include/semax.h declares
 EXPORTS = (
-    "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_bf16x3_geo",
+    "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f64tc_prepare_size", "sem_ax_f64tc_prepare",
+    "sem_ax_f64tc_prepared", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_bf16x3_geo",
     "sem_ax_batched_workspace_size", "sem_ax_batched",
     "sem_ax_plan_create", "sem_ax_plan_exec", "sem_ax_plan_destroy", "sem_ax_plan_config",
     "semax_gs_create", "semax_gs_apply", "semax_gs_destroy", "sem_ax_diag",
@@ -58,6 +59,9 @@ def _load():
         "sem_ax": [i64, i32, vp, vp, vp, vp, vp],
         "sem_ax_f64x": [i64, i32, vp, vp, vp, vp, vp],
         "sem_ax_f64tc": [i64, i32, vp, vp, vp, vp, vp],
+        "sem_ax_f64tc_prepare_size": [i64, i32, ctypes.POINTER(sz)],
+        "sem_ax_f64tc_prepare": [i64, i32, vp, vp, vp],
+        "sem_ax_f64tc_prepared": [i64, i32, vp, vp, vp, vp, vp],
         "sem_ax_helmholtz": [i64, i32, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp],
         "sem_ax_f32": [i64, i32, vp, vp, vp, vp, vp, vp],
         "sem_ax_bf16x3": [i64, i32, vp, vp, vp, vp, vp, i32, vp],

@@ -43,7 +43,11 @@ constexpr int kDigBytes = 3 * kS10 * kSlice; // digits of wr, ws, wt (u reuses t
 constexpr int kBufBytes = 512 * 8;           // one double-float per node
 constexpr int kGBytes = 6 * 512 * 8;         // one element's G (FP64), staged
 constexpr int kUBytes = 512 * 8;             // one element's u (FP64), staged
-constexpr size_t kSmem = kDigBytes + 2 * kBufBytes + kGBytes + kUBytes + 16 * sizeof(int);   // + mbarrier in the last 8 of them
+constexpr int kEgBytes = 512 * 4;            // prepared form: each node's largest G exponent, after G
+constexpr int kPreBytes = kGBytes + kEgBytes; // one element of the prepared geometric factor (26 KB)
+// + mbarrier in the last 8 of the reduction slots
+template <bool PRE>
+constexpr size_t smem_bytes() { return kDigBytes + 2 * kBufBytes + (PRE ? kPreBytes : kGBytes) + kUBytes + 16 * sizeof(int); }
 
 // Byte offset of row j of plane p inside a digit slice: the 16-byte rows of
 // a plane are permuted by p, so that ldmatrix over the 8 rows of a plane
@@ -123,6 +127,10 @@ __device__ __forceinline__ void store_tile(float2 *buf, const float (&acc)[kS10]
 
 __device__ __forceinline__ int max4(const int *p) { return max(max(p[0], p[1]), max(p[2], p[3])); }
 
+// PRE = false: G is FP64 [E][6][512]; PRE = true: G points at the prepared
+// form, per element 6 x 512 (hi, lo) float pairs (G split as below) and 512
+// ints (each node's largest biased exponent of G).
+template <bool PRE>
 __global__ void __launch_bounds__(kThreads, 4)
 ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
                 const double *__restrict__ D, double *__restrict__ w) {
@@ -131,8 +139,11 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
     float2 *bs = reinterpret_cast<float2 *>(smem + kDigBytes);   // s-direction results
     float2 *bt = bs + 512;                                         // t-direction results
     const double2 *gst = reinterpret_cast<const double2 *>(bt + 512);   // staged G [6][256 node pairs]
-    const double2 *ust = gst + 6 * 256;                            // staged u [256 node pairs]
-    int *sred = reinterpret_cast<int *>(smem + kDigBytes + 2 * kBufBytes + kGBytes + kUBytes);   // [0, 4) u, [4, 8) y exponents
+    const float4 *gpre = reinterpret_cast<const float4 *>(gst);         // prepared: [6][256 node pairs] (hi, lo) x 2
+    const int2 *egst = reinterpret_cast<const int2 *>(reinterpret_cast<const unsigned char *>(gst) + kGBytes);
+    const double2 *ust = reinterpret_cast<const double2 *>(reinterpret_cast<const unsigned char *>(gst) +
+                                                           (PRE ? kPreBytes : kGBytes));   // staged u [256 node pairs]
+    int *sred = reinterpret_cast<int *>(smem + kDigBytes + 2 * kBufBytes + (PRE ? kPreBytes : kGBytes) + kUBytes);   // [0, 4) u, [4, 8) y exponents
     const uint32_t bar = smem_u32(sred + 8);                      // mbarrier of the staged u and G (8-byte aligned)
     const uint32_t dig_s = smem_u32(dig), gst_s = smem_u32(gst), ust_s = smem_u32(ust);
 
@@ -144,9 +155,12 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
     // completes one phase of the mbarrier.
     auto prefetch = [&](int64_t ep) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads before async writes
-        mbar_expect_tx(bar, kUBytes + kGBytes);
+        mbar_expect_tx(bar, kUBytes + (PRE ? kPreBytes : kGBytes));
         bulk_g2s(ust_s, u + ep * 512, kUBytes, bar);
-        bulk_g2s(gst_s, G + ep * 3072, kGBytes, bar);
+        if (PRE)
+            bulk_g2s(gst_s, reinterpret_cast<const unsigned char *>(G) + ep * kPreBytes, kPreBytes, bar);
+        else
+            bulk_g2s(gst_s, G + ep * 3072, kGBytes, bar);
     };
     if (tid == 0) mbar_init(bar, 1);
     __syncthreads();
@@ -237,8 +251,16 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         for (int h = 0; h < 2; ++h) {
             const int k = 2 * warp + h, nb = k * 64 + g * 8 + 2 * t;
             double2 gv[6];
+            float4 gp[6];
+            int2 eg2;
+            if (PRE) {
 #pragma unroll
-            for (int a = 0; a < 6; ++a) gv[a] = gst[a * 256 + (nb >> 1)];
+                for (int a = 0; a < 6; ++a) gp[a] = gpre[a * 256 + (nb >> 1)];
+                eg2 = egst[nb >> 1];
+            } else {
+#pragma unroll
+                for (int a = 0; a < 6; ++a) gv[a] = gst[a * 256 + (nb >> 1)];
+            }
             const float4 tv = *reinterpret_cast<const float4 *>(bt + tidx(k, g, 2 * t));
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
@@ -246,20 +268,28 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 const float2 sv = bs[sidx(k, g, 2 * t + c)];
                 const df Vs{sv.x, sv.y};
                 const df Vt = c ? df{tv.z, tv.w} : df{tv.x, tv.y};
-                double Gc[6];
-                unsigned hws[6], hmax = 0;
-#pragma unroll
-                for (int a = 0; a < 6; ++a) {
-                    Gc[a] = c ? gv[a].y : gv[a].x;
-                    hws[a] = habs(Gc[a]);
-                    hmax = max(hmax, hws[a]);
-                }
-                const int eg = (int)(hmax >> 20);   // largest biased exponent of the node's G
-                const int sh = max(eg, 1) - 1023;   // G * 2^-sh has magnitude < 2
-                const unsigned K = (unsigned)(896 + sh) << 23;
                 df Gh[6];
+                int eg;   // largest biased exponent of the node's G
+                if (PRE) {
 #pragma unroll
-                for (int a = 0; a < 6; ++a) Gh[a] = split_g(Gc[a], hws[a], K, (unsigned)max(897 + sh, 1) << 20);
+                    for (int a = 0; a < 6; ++a) Gh[a] = c ? df{gp[a].z, gp[a].w} : df{gp[a].x, gp[a].y};
+                    eg = c ? eg2.y : eg2.x;
+                } else {
+                    double Gc[6];
+                    unsigned hws[6], hmax = 0;
+#pragma unroll
+                    for (int a = 0; a < 6; ++a) {
+                        Gc[a] = c ? gv[a].y : gv[a].x;
+                        hws[a] = habs(Gc[a]);
+                        hmax = max(hmax, hws[a]);
+                    }
+                    eg = (int)(hmax >> 20);
+                    const int sh = max(eg, 1) - 1023;
+                    const unsigned K = (unsigned)(896 + sh) << 23;
+#pragma unroll
+                    for (int a = 0; a < 6; ++a) Gh[a] = split_g(Gc[a], hws[a], K, (unsigned)max(897 + sh, 1) << 20);
+                }
+                const int sh = max(eg, 1) - 1023;   // G * 2^-sh has magnitude < 2
                 y[q][0] = dot3(Gh[0], Gh[1], Gh[2], vr[q], Vs, Vt);
                 y[q][1] = dot3(Gh[1], Gh[3], Gh[4], vr[q], Vs, Vt);
                 y[q][2] = dot3(Gh[2], Gh[4], Gh[5], vr[q], Vs, Vt);
@@ -349,8 +379,10 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
     if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+template <bool PRE>
 static int launch(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s) {
-    auto kern = ax_f64tc_kernel;
+    auto kern = ax_f64tc_kernel<PRE>;
+    constexpr size_t kSmem = smem_bytes<PRE>();
     int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     if (st != SEMAX_OK) return st;
     st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -362,6 +394,36 @@ static int launch(int64_t E, const double *u, const double *G, const double *D, 
     const int64_t grid = std::min<int64_t>(E, (int64_t)device_sm_count() * std::max(per_sm, 1));
     kern<<<(unsigned)grid, kThreads, kSmem, s>>>(E, u, G, D, w);
     return launch_status();
+}
+
+// The prepared geometric factor: per node, G's six entries split hi + lo
+// exactly as ax_f64tc_kernel<false> splits them, and the largest biased
+// exponent of the six.  One thread per node, coalesced in both layouts.
+__global__ void __launch_bounds__(256) prepare_kernel(int64_t E, const double *__restrict__ G,
+                                                      unsigned char *__restrict__ Gp) {
+    const int64_t total = E * 512, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
+        const int64_t e = p >> 9;
+        const int q = (int)(p & 511);
+        const double *Ge = G + e * 3072 + q;
+        double Gc[6];
+        unsigned hws[6], hmax = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            Gc[a] = ld_stream(Ge + a * 512);
+            hws[a] = habs(Gc[a]);
+            hmax = max(hmax, hws[a]);
+        }
+        const int eg = (int)(hmax >> 20), sh = max(eg, 1) - 1023;
+        const unsigned K = (unsigned)(896 + sh) << 23, mw = (unsigned)max(897 + sh, 1) << 20;
+        float2 *out = reinterpret_cast<float2 *>(Gp + e * kPreBytes);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            const df d = split_g(Gc[a], hws[a], K, mw);
+            out[a * 512 + q] = make_float2(d.hi, d.lo);
+        }
+        reinterpret_cast<int *>(Gp + e * kPreBytes + kGBytes)[q] = eg;
+    }
 }
 
 }  // namespace oz
@@ -377,7 +439,41 @@ extern "C" int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, 
                             void *stream) {
     int st = check_args(E, N, u, G, D, w);
     if (st != SEMAX_OK || E == 0) return st;
-    if (N == 7) return oz::launch(E, u, G, D, w, (cudaStream_t)stream);
+    if (N == 7) return oz::launch<false>(E, u, G, D, w, (cudaStream_t)stream);
     if (N == 15) return launch_f64tc16(E, u, G, D, w, (cudaStream_t)stream);
     return sem_ax_f64x(E, N, u, G, D, w, stream);   // other orders: the double-float tile
+}
+
+extern "C" int sem_ax_f64tc_prepare_size(int64_t E, int N, size_t *bytes) {
+    if (!bytes || E < 0) return SEMAX_EINVAL;
+    if (N != 7) return SEMAX_EUNSUPPORTED_N;
+    *bytes = (size_t)E * oz::kPreBytes;
+    return SEMAX_OK;
+}
+
+extern "C" int sem_ax_f64tc_prepare(int64_t E, int N, const double *G, void *Gp, void *stream) {
+    if (E < 0) return SEMAX_EINVAL;
+    if (N != 7) return SEMAX_EUNSUPPORTED_N;
+    if (E == 0) return SEMAX_OK;
+    if (!G || !Gp) return SEMAX_EINVAL;
+    if (!aligned16(G) || !aligned16(Gp)) return SEMAX_EALIGN;
+    if (overlaps(G, (size_t)E * 3072 * sizeof(double), Gp, (size_t)E * oz::kPreBytes)) return SEMAX_EALIAS;
+    const int64_t blocks = std::min<int64_t>((E * 512 + 255) / 256, (int64_t)device_sm_count() * 8);
+    oz::prepare_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(E, G, (unsigned char *)Gp);
+    return launch_status();
+}
+
+extern "C" int sem_ax_f64tc_prepared(int64_t E, int N, const double *u, const void *Gp, const double *D, double *w,
+                                     void *stream) {
+    if (E < 0) return SEMAX_EINVAL;
+    if (N != 7) return SEMAX_EUNSUPPORTED_N;
+    if (E == 0) return SEMAX_OK;
+    if (!u || !Gp || !D || !w) return SEMAX_EINVAL;
+    if (!aligned16(u) || !aligned16(Gp) || !aligned16(w) || ((uintptr_t)D % alignof(double)) != 0)
+        return SEMAX_EALIGN;
+    const size_t ub = (size_t)E * 512 * sizeof(double);
+    if (overlaps(w, ub, u, ub) || overlaps(w, ub, Gp, (size_t)E * oz::kPreBytes) ||
+        overlaps(w, ub, D, 64 * sizeof(double)))
+        return SEMAX_EALIAS;
+    return oz::launch<true>(E, u, reinterpret_cast<const double *>(Gp), D, w, (cudaStream_t)stream);
 }

@@ -394,6 +394,7 @@ struct semax_pcg {
     double *part = nullptr, *scal = nullptr;
     float *G32 = nullptr, *D32 = nullptr, *p32 = nullptr, *w32 = nullptr;   // SEMAX_PCG_MIXED
     double *d = nullptr;                                                   // its correction vector
+    void *Gp = nullptr;                 // SEMAX_PCG_F64TC at N = 7: the prepared geometric factor
     unsigned *counters = nullptr;                                          // last-block reductions (2)
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
@@ -407,6 +408,7 @@ struct semax_pcg {
 // w = A_L v, FP64-accurate, with the operator the solver was created with
 static int pcg_apply_a64(semax_pcg *s, const double *v, double *w, cudaStream_t cs) {
     if (s->flags & SEMAX_PCG_F64X) return sem_ax_f64x(s->E, s->N, v, s->G, s->D, w, cs);
+    if (s->Gp) return sem_ax_f64tc_prepared(s->E, s->N, v, s->Gp, s->D, w, cs);   // bit for bit sem_ax_f64tc
     if (s->flags & SEMAX_PCG_F64TC) return sem_ax_f64tc(s->E, s->N, v, s->G, s->D, w, cs);
     return launch_plain<double>(s->E, s->N, default_tile<double>(s->N + 1), v, s->G, s->D, w, nullptr,
                                 Helm<double>{nullptr, 1.0, 0.0}, cs);
@@ -431,6 +433,7 @@ static void pcg_free(semax_pcg *s) {
     cudaFree(s->p32);
     cudaFree(s->w32);
     cudaFree(s->d);
+    cudaFree(s->Gp);
     cudaFree(s->counters);
     s->magic = 0;
     delete s;
@@ -507,6 +510,13 @@ extern "C" int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G
             to_f32_kernel<<<1, kSolverThreads, 0, s->cs>>>(nn, D, s->D32);
             st = launch_status();
         }
+    }
+    // the tensor-core operator at order 7 reads G prepared once (split into float pairs)
+    if (st == SEMAX_OK && (flags & SEMAX_PCG_F64TC) && N == 7) {
+        size_t bytes = 0;
+        st = sem_ax_f64tc_prepare_size(E, N, &bytes);
+        if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->Gp, bytes));
+        if (st == SEMAX_OK) st = sem_ax_f64tc_prepare(E, N, G, s->Gp, s->cs);
     }
     // Jacobi: invdiag = 1 / (Q Q^T diag(A_L)) at free nodes, 0 at Dirichlet nodes
     if (st == SEMAX_OK) st = launch_diag_N(E, N, G, D, s->invdiag, s->cs);

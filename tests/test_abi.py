@@ -62,6 +62,29 @@ def test_argument_validation(lib, fn):
     assert call(4, 7, D=A + (3 << 32) + 64) == -4   # w overlaps D
 
 
+def test_prepared_f64tc_validation(lib):
+    size = ctypes.c_size_t(0)
+    assert lib.sem_ax_f64tc_prepare_size(10, 7, ctypes.byref(size)) == 0 and size.value == 10 * 26624
+    assert lib.sem_ax_f64tc_prepare_size(10, 15, ctypes.byref(size)) == -2     # order 7 only
+    assert lib.sem_ax_f64tc_prepare_size(-1, 7, ctypes.byref(size)) == -1
+    assert lib.sem_ax_f64tc_prepare_size(10, 7, None) == -1
+    G, Gp = A, A + (1 << 32)
+    assert lib.sem_ax_f64tc_prepare(0, 7, None, None, None) == 0
+    assert lib.sem_ax_f64tc_prepare(4, 5, G, Gp, None) == -2
+    assert lib.sem_ax_f64tc_prepare(4, 7, None, Gp, None) == -1
+    assert lib.sem_ax_f64tc_prepare(4, 7, G, Gp + 8, None) == -3             # EALIGN
+    assert lib.sem_ax_f64tc_prepare(4, 7, G, G + 4096, None) == -4           # EALIAS
+    u, D, w = A + (2 << 32), A + (3 << 32), A + (4 << 32)
+    f = lib.sem_ax_f64tc_prepared
+    assert f(0, 7, None, None, None, None, None) == 0
+    assert f(4, 15, u, Gp, D, w, None) == -2
+    assert f(-1, 7, u, Gp, D, w, None) == -1
+    assert f(4, 7, u, None, D, w, None) == -1
+    assert f(4, 7, u, Gp + 8, D, w, None) == -3
+    assert f(4, 7, u, Gp, D, Gp + 1024, None) == -4                         # w overlaps Gp
+    assert f(4, 7, u, Gp, D, u + 1024, None) == -4                          # w overlaps u
+
+
 def test_bf16_rejects_bad_terms(lib):
     assert lib.sem_ax_bf16x3(4, 15, A, A + (1 << 32), A + (2 << 32), A + (3 << 32), None, 4, None) == -1
 

@@ -281,6 +281,36 @@ def test_f64tc_order15_max_size_offsets_past_2_31(semax, oracle_mod):
     assert r[0] / r[1] <= TYPICAL_TC
 
 
+def test_f64tc_prepared_equals_f64tc_bit_for_bit(semax, oracle_mod):
+    """The geometric factor prepared once gives sem_ax_f64tc's result bit for
+    bit: on a ragged mesh, at the bench size, with zero nodes and elements,
+    scaled G, a non-finite entry, and for a second u on the same Gp."""
+    m = si.make_mesh(np.random.default_rng(95), 37, 7, device="cuda")
+    Gp = semax.f64tc_prepare(m.G)
+    torch.cuda.synchronize()
+    assert Gp.numel() == 37 * 26624
+    w = semax.sem_ax_f64tc_prepared(m.u, Gp, m.D)
+    assert torch.equal(w, semax.sem_ax_f64tc(m.u, m.G, m.D))
+    assert rel_err(w, oracle_mod.sem_ax(m.u.cpu(), m.G.cpu(), m.D.cpu())) <= TYPICAL_TC
+    u2 = torch.rand_like(m.u) - 0.5
+    assert torch.equal(semax.sem_ax_f64tc_prepared(u2, Gp, m.D), semax.sem_ax_f64tc(u2, m.G, m.D))
+    G = m.G.clone()
+    G[3] = 0.0
+    G[5, :, 1, 2, 3] = 0.0
+    G[7] *= 2.0 ** 700
+    G[9] *= 2.0 ** -900
+    G[11, 2, 4, 4, 4] = float("inf")
+    Gp2 = semax.f64tc_prepare(G)
+    w2 = semax.sem_ax_f64tc_prepared(m.u, Gp2, m.D)
+    ref = semax.sem_ax_f64tc(m.u, G, m.D)
+    keep = torch.arange(37, device=w2.device) != 11
+    assert torch.equal(w2[keep], ref[keep])
+    assert torch.isnan(w2[11]).all() and torch.isnan(ref[11]).all()
+    big = si.make_workload(1, device="cuda")[0]
+    Gpb = semax.f64tc_prepare(big.G)
+    assert torch.equal(semax.sem_ax_f64tc_prepared(big.u, Gpb, big.D), semax.sem_ax_f64tc(big.u, big.G, big.D))
+
+
 def test_energy_norm_on_the_gpu(semax, oracle_mod):
     """u^T A u with the FP64 reduction on the GPU: equal to the oracle's energy
     for the FP64 and both FP64-accurate forms, and positive for random u."""
