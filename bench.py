@@ -289,7 +289,13 @@ def variants(semax, reps: int) -> dict:
         r["rel_err_vs_f64"] = rel_err_gpu(semax, w64, ref)
         r["energy_rel_err"] = energy_rel_gpu(semax, m.u, w64, ref)
         out[f"{name}_N15_E8192"] = r
-    del w64
+    gp = semax.f64tc_prepare(m.G)
+    wp = torch.empty_like(w64)
+    r = rate(lambda: semax.sem_ax_f64tc_prepared(m.u, gp, m.D, wp), dofs, dofs * 72)
+    r["bit_identical_to_f64tc"] = bool(torch.equal(wp, w64))
+    r["arith"] = "G split into float pairs once (sem_ax_f64tc_prepare), 72 B per node"
+    out["f64tc_prepared_N15_E8192"] = r
+    del w64, wp, gp
     u, G, D = m.u.float(), m.G.float(), m.D.float()
     u64 = m.u
     X = torch.from_numpy(m.X).float().cuda().contiguous()

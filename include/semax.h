@@ -125,13 +125,15 @@ int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const doubl
  * (for repeated applications with the same G, as in an iterative solver).
  * sem_ax_f64tc_prepare splits each node's six G entries into (hi, lo) float
  * pairs after the per-node power-of-two scale, exactly as sem_ax_f64tc does
- * on every call, and keeps each node's largest biased exponent: per element
- * 6 n^3 float pairs followed by n^3 int32, E * 26624 bytes at N = 7
- * (sem_ax_f64tc_prepare_size), the same HBM traffic per call as FP64 G.
- * sem_ax_f64tc_prepared then computes, bit for bit, what sem_ax_f64tc
- * computes from G, without the split.  N = 7 only (SEMAX_EUNSUPPORTED_N
- * otherwise).  Gp: device memory, 16-byte aligned, owned by the caller, not
- * overlapping G or w. */
+ * on every call, and keeps each node's largest biased exponent (at N = 15
+ * for each half (rr, rs, rt) and (ss, st, tt) of G, as that kernel splits
+ * them): per element 6 n^3 float pairs and n^3 (N = 15: 2 n^3) int32,
+ * E * 26624 bytes at N = 7 and E * 229376 at N = 15
+ * (sem_ax_f64tc_prepare_size), 4 to 8 bytes per node more HBM traffic per
+ * call than FP64 G.  sem_ax_f64tc_prepared then computes, bit for bit, what
+ * sem_ax_f64tc computes from G, without the split.  N = 7 and N = 15
+ * (SEMAX_EUNSUPPORTED_N otherwise).  Gp: device memory, 16-byte aligned,
+ * owned by the caller, not overlapping G or w. */
 int sem_ax_f64tc_prepare_size(int64_t E, int N, size_t *bytes);
 int sem_ax_f64tc_prepare(int64_t E, int N, const double *G, void *Gp, void *stream);
 int sem_ax_f64tc_prepared(int64_t E, int N, const double *u, const void *Gp, const double *D,

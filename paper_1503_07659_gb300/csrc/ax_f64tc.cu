@@ -431,6 +431,10 @@ __global__ void __launch_bounds__(256) prepare_kernel(int64_t E, const double *_
 
 namespace semax {
 int launch_f64tc16(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s);
+int launch_f64tc16_prepared(int64_t E, const double *u, const void *Gp, const double *D, double *w,
+                            cudaStream_t s);
+int prepare_f64tc16(int64_t E, const double *G, void *Gp, cudaStream_t s);
+size_t f64tc16_prepared_bytes_per_element();
 }
 
 using namespace semax;
@@ -444,20 +448,27 @@ extern "C" int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, 
     return sem_ax_f64x(E, N, u, G, D, w, stream);   // other orders: the double-float tile
 }
 
+// bytes of one element of the prepared geometric factor, 0 if N has none
+static size_t prepared_bytes(int N) {
+    return N == 7 ? (size_t)oz::kPreBytes : (N == 15 ? f64tc16_prepared_bytes_per_element() : 0);
+}
+
 extern "C" int sem_ax_f64tc_prepare_size(int64_t E, int N, size_t *bytes) {
     if (!bytes || E < 0) return SEMAX_EINVAL;
-    if (N != 7) return SEMAX_EUNSUPPORTED_N;
-    *bytes = (size_t)E * oz::kPreBytes;
+    if (!prepared_bytes(N)) return SEMAX_EUNSUPPORTED_N;
+    *bytes = (size_t)E * prepared_bytes(N);
     return SEMAX_OK;
 }
 
 extern "C" int sem_ax_f64tc_prepare(int64_t E, int N, const double *G, void *Gp, void *stream) {
     if (E < 0) return SEMAX_EINVAL;
-    if (N != 7) return SEMAX_EUNSUPPORTED_N;
+    if (!prepared_bytes(N)) return SEMAX_EUNSUPPORTED_N;
     if (E == 0) return SEMAX_OK;
     if (!G || !Gp) return SEMAX_EINVAL;
     if (!aligned16(G) || !aligned16(Gp)) return SEMAX_EALIGN;
-    if (overlaps(G, (size_t)E * 3072 * sizeof(double), Gp, (size_t)E * oz::kPreBytes)) return SEMAX_EALIAS;
+    const size_t n3 = (size_t)(N + 1) * (N + 1) * (N + 1);
+    if (overlaps(G, (size_t)E * 6 * n3 * sizeof(double), Gp, (size_t)E * prepared_bytes(N))) return SEMAX_EALIAS;
+    if (N == 15) return prepare_f64tc16(E, G, Gp, (cudaStream_t)stream);
     const int64_t blocks = std::min<int64_t>((E * 512 + 255) / 256, (int64_t)device_sm_count() * 8);
     oz::prepare_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(E, G, (unsigned char *)Gp);
     return launch_status();
@@ -466,14 +477,15 @@ extern "C" int sem_ax_f64tc_prepare(int64_t E, int N, const double *G, void *Gp,
 extern "C" int sem_ax_f64tc_prepared(int64_t E, int N, const double *u, const void *Gp, const double *D, double *w,
                                      void *stream) {
     if (E < 0) return SEMAX_EINVAL;
-    if (N != 7) return SEMAX_EUNSUPPORTED_N;
+    if (!prepared_bytes(N)) return SEMAX_EUNSUPPORTED_N;
     if (E == 0) return SEMAX_OK;
     if (!u || !Gp || !D || !w) return SEMAX_EINVAL;
     if (!aligned16(u) || !aligned16(Gp) || !aligned16(w) || ((uintptr_t)D % alignof(double)) != 0)
         return SEMAX_EALIGN;
-    const size_t ub = (size_t)E * 512 * sizeof(double);
-    if (overlaps(w, ub, u, ub) || overlaps(w, ub, Gp, (size_t)E * oz::kPreBytes) ||
-        overlaps(w, ub, D, 64 * sizeof(double)))
+    const size_t n = (size_t)N + 1, ub = (size_t)E * n * n * n * sizeof(double);
+    if (overlaps(w, ub, u, ub) || overlaps(w, ub, Gp, (size_t)E * prepared_bytes(N)) ||
+        overlaps(w, ub, D, n * n * sizeof(double)))
         return SEMAX_EALIAS;
+    if (N == 15) return launch_f64tc16_prepared(E, u, Gp, D, w, (cudaStream_t)stream);
     return oz::launch<true>(E, u, reinterpret_cast<const double *>(Gp), D, w, (cudaStream_t)stream);
 }

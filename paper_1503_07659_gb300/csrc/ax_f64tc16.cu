@@ -44,7 +44,10 @@ constexpr int kTB = kN3 * 8;                 // double-float per node: t-directi
 constexpr int kSB = kN3 * 8;                 // double-float per node: the s-gradient, parked (32 KB)
 constexpr int kGS = 3 * kN3 * 8;             // half of an element's G (96 KB)
 constexpr int kRed = 64 * 4;                 // reduction slots
-constexpr size_t kSmem = kUD + kDD + kTB + kSB + kGS + kRed + 16;   // + two mbarriers
+constexpr int kEgB = kN3 * 4;                // prepared form: each node's largest exponent of the half (16 KB)
+constexpr int kGSP = kGS + kEgB;             // prepared form: one half of an element (112 KB)
+template <bool PRE>
+constexpr size_t smem_bytes() { return kUD + kDD + kTB + kSB + (PRE ? kGSP : kGS) + kRed + 16; }   // + two mbarriers
 
 // Byte offset of (row r, 16-byte chunk c) of the 16 x 16 BF16 plane p: the
 // 32 chunks of a plane are permuted by p and by bit 2 of r, so that ldmatrix
@@ -78,6 +81,11 @@ __device__ __forceinline__ int max16(const int *p) {
                max(max(max(c.x, c.y), max(c.z, c.w)), max(max(d.x, d.y), max(d.z, d.w))));
 }
 
+// PRE = false: G is FP64 [E][6][4096]; PRE = true: G points at the prepared
+// form, per element two halves (rr, rs, rt) and (ss, st, tt), each 3 x 4096
+// (hi, lo) float pairs (split as below, against the half's per-node scale)
+// followed by 4096 ints (each node's largest biased exponent in the half).
+template <bool PRE>
 __global__ void __launch_bounds__(kThreads, 1)
 ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
                   const double *__restrict__ D, double *__restrict__ w) {
@@ -87,7 +95,9 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
     float4 *tb = reinterpret_cast<float4 *>(dd + kDD);                 // [2048] node pairs
     float2 *sb = reinterpret_cast<float2 *>(dd + kDD + kTB);           // [8][512] per-thread slots
     const double2 *gs = reinterpret_cast<const double2 *>(dd + kDD + kTB + kSB);   // [3][2048]
-    int *sred = reinterpret_cast<int *>(dd + kDD + kTB + kSB + kGS);   // 4 x 16 slots
+    const float4 *gsp = reinterpret_cast<const float4 *>(gs);                       // prepared: [3][2048] pairs x 2
+    const int2 *egs = reinterpret_cast<const int2 *>(dd + kDD + kTB + kSB + kGS);   // prepared: [2048]
+    int *sred = reinterpret_cast<int *>(dd + kDD + kTB + kSB + (PRE ? kGSP : kGS));   // 4 x 16 slots
     const uint32_t ud_s = smem_u32(ud), dd_s = smem_u32(dd), gs_s = smem_u32(gs);
     const uint32_t barA = smem_u32(sred + 64), barB = barA + 8;
 
@@ -100,12 +110,18 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
         mbar_init(barB, 1);
     }
     __syncthreads();
-    auto stage = [&](uint32_t bar, const double *src) {
+    // half h (0: rr, rs, rt; 1: ss, st, tt) of element ep into the staging buffer
+    auto stage = [&](uint32_t bar, int64_t ep, int h) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, kGS);
-        bulk_g2s(gs_s, src, kGS, bar);
+        if (PRE) {
+            mbar_expect_tx(bar, kGSP);
+            bulk_g2s(gs_s, reinterpret_cast<const unsigned char *>(G) + (2 * ep + h) * (int64_t)kGSP, kGSP, bar);
+        } else {
+            mbar_expect_tx(bar, kGS);
+            bulk_g2s(gs_s, G + (2 * ep + h) * 3 * kN3, kGS, bar);
+        }
     };
-    if (tid == 0) stage(barA, G + (int64_t)blockIdx.x * 6 * kN3);
+    if (tid == 0) stage(barA, blockIdx.x, 0);
 
     // ---- D digits, once per CTA: [p][16 x 16] in the plane layout
     int eD = 1;
@@ -148,7 +164,6 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
 
     unsigned pA = 0, pB = 0;
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x, pA ^= 1u, pB ^= 1u) {
-        const double *Ge = G + e * 6 * kN3;
         double *we = w + e * kN3;
 
         // ---- A: u -> digits
@@ -262,27 +277,46 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 const int j = g + 8 * h, nd2 = (k * 256 + j * 16 + 8 * nt + 2 * t) >> 1, p = 2 * nt + h, q0 = 2 * p;
                 const float4 tv = tb[tslot(k, j, 4 * nt + t)];
                 double2 gv[3];
+                float4 gp[3];
+                int2 eg2;
+                if (PRE) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) gv[a] = gs[a * 2048 + nd2];
+                    for (int a = 0; a < 3; ++a) gp[a] = gsp[a * 2048 + nd2];
+                    eg2 = egs[nd2];
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) gv[a] = gs[a * 2048 + nd2];
+                }
                 const float2 s0 = sb[q0 * kThreads + tid], s1 = sb[(q0 + 1) * kThreads + tid];
                 const df2 Vr = pack_df2(vr[q0], vr[q0 + 1]);
                 const df2 Vs{make_float2(s0.x, s1.x), make_float2(s0.y, s1.y)};
                 const df2 Vt{make_float2(tv.x, tv.z), make_float2(tv.y, tv.w)};
-                unsigned hw0[3], hw1[3], hm0 = 0, hm1 = 0;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    hw0[a] = habs(gv[a].x);
-                    hw1[a] = habs(gv[a].y);
-                    hm0 = max(hm0, hw0[a]);
-                    hm1 = max(hm1, hw1[a]);
-                }
-                const int eg0 = (int)(hm0 >> 20), sh0 = max(eg0, 1) - 1023;
-                const int eg1 = (int)(hm1 >> 20), sh1 = max(eg1, 1) - 1023;
-                const unsigned K0 = (unsigned)(896 + sh0) << 23, mw0 = (unsigned)max(897 + sh0, 1) << 20;
-                const unsigned K1 = (unsigned)(896 + sh1) << 23, mw1 = (unsigned)max(897 + sh1, 1) << 20;
                 df2 Gh[3];
+                int eg0, eg1;
+                if (PRE) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) Gh[a] = split_g2(gv[a], hw0[a], hw1[a], K0, K1, mw0, mw1);
+                    for (int a = 0; a < 3; ++a)
+                        Gh[a] = df2{make_float2(gp[a].x, gp[a].z), make_float2(gp[a].y, gp[a].w)};
+                    eg0 = eg2.x;
+                    eg1 = eg2.y;
+                } else {
+                    unsigned hw0[3], hw1[3], hm0 = 0, hm1 = 0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        hw0[a] = habs(gv[a].x);
+                        hw1[a] = habs(gv[a].y);
+                        hm0 = max(hm0, hw0[a]);
+                        hm1 = max(hm1, hw1[a]);
+                    }
+                    eg0 = (int)(hm0 >> 20);
+                    eg1 = (int)(hm1 >> 20);
+                    const int s0 = max(eg0, 1) - 1023, s1 = max(eg1, 1) - 1023;
+                    const unsigned K0 = (unsigned)(896 + s0) << 23, mw0 = (unsigned)max(897 + s0, 1) << 20;
+                    const unsigned K1 = (unsigned)(896 + s1) << 23, mw1 = (unsigned)max(897 + s1, 1) << 20;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) Gh[a] = split_g2(gv[a], hw0[a], hw1[a], K0, K1, mw0, mw1);
+                }
+                const int sh0 = max(eg0, 1) - 1023, sh1 = max(eg1, 1) - 1023;
                 const acc2x2 y = dot3_2(Gh[0], Gh[1], Gh[2], Vr, Vs, Vt);
                 const df2 yn = two_sum2(y.s, y.c);
                 YR[p] = acc2x2{yn.hi, yn.lo};
@@ -299,7 +333,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
         tmax = __reduce_max_sync(0xffffffffu, tmax);
         if (lane == 0) sred[16 + warp] = tmax;
         __syncthreads();
-        if (tid == 0) stage(barB, Ge + 3 * kN3);   // every thread has read G's first half
+        if (tid == 0) stage(barB, e, 1);   // every thread has read G's first half
         const int eRraw = max16(sred + 16);
         const int eR = eRraw == INT_MIN ? 0 : min(eRraw, kBadExp);
 
@@ -345,27 +379,46 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 const int j = g + 8 * h, nd2 = (k * 256 + j * 16 + 8 * nt + 2 * t) >> 1, p = 2 * nt + h, q0 = 2 * p;
                 const float4 tv = tb[tslot(k, j, 4 * nt + t)];
                 double2 gv[3];
+                float4 gp[3];
+                int2 eg2;
+                if (PRE) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) gv[a] = gs[a * 2048 + nd2];
+                    for (int a = 0; a < 3; ++a) gp[a] = gsp[a * 2048 + nd2];
+                    eg2 = egs[nd2];
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) gv[a] = gs[a * 2048 + nd2];
+                }
                 const float2 s0 = sb[q0 * kThreads + tid], s1 = sb[(q0 + 1) * kThreads + tid];
                 const df2 Vs{make_float2(s0.x, s1.x), make_float2(s0.y, s1.y)};
                 const df2 Vt{make_float2(tv.x, tv.z), make_float2(tv.y, tv.w)};
-                unsigned hw0[3], hw1[3], hm0 = 0, hm1 = 0;
+                df2 Gh[3];
+                int eg0, eg1;
+                if (PRE) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    hw0[a] = habs(gv[a].x);
-                    hw1[a] = habs(gv[a].y);
-                    hm0 = max(hm0, hw0[a]);
-                    hm1 = max(hm1, hw1[a]);
+                    for (int a = 0; a < 3; ++a)
+                        Gh[a] = df2{make_float2(gp[a].x, gp[a].z), make_float2(gp[a].y, gp[a].w)};
+                    eg0 = eg2.x;
+                    eg1 = eg2.y;
+                } else {
+                    unsigned hw0[3], hw1[3], hm0 = 0, hm1 = 0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        hw0[a] = habs(gv[a].x);
+                        hw1[a] = habs(gv[a].y);
+                        hm0 = max(hm0, hw0[a]);
+                        hm1 = max(hm1, hw1[a]);
+                    }
+                    eg0 = (int)(hm0 >> 20);
+                    eg1 = (int)(hm1 >> 20);
+                    const int s0 = max(eg0, 1) - 1023, s1 = max(eg1, 1) - 1023;
+                    const unsigned K0 = (unsigned)(896 + s0) << 23, mw0 = (unsigned)max(897 + s0, 1) << 20;
+                    const unsigned K1 = (unsigned)(896 + s1) << 23, mw1 = (unsigned)max(897 + s1, 1) << 20;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) Gh[a] = split_g2(gv[a], hw0[a], hw1[a], K0, K1, mw0, mw1);
                 }
-                const int eg0 = (int)(hm0 >> 20), sh0 = max(eg0, 1) - 1023;
-                const int eg1 = (int)(hm1 >> 20), sh1 = max(eg1, 1) - 1023;
-                const unsigned K0 = (unsigned)(896 + sh0) << 23, mw0 = (unsigned)max(897 + sh0, 1) << 20;
-                const unsigned K1 = (unsigned)(896 + sh1) << 23, mw1 = (unsigned)max(897 + sh1, 1) << 20;
-                df2 Gh[3];   // ss, st, tt
-#pragma unroll
-                for (int a = 0; a < 3; ++a) Gh[a] = split_g2(gv[a], hw0[a], hw1[a], K0, K1, mw0, mw1);
-                // y_s = Grs r + Gss s + Gst t,  y_t = Grt r + Gst s + Gtt t
+                const int sh0 = max(eg0, 1) - 1023, sh1 = max(eg1, 1) - 1023;
+                // Gh: ss, st, tt.  y_s = Grs r + Gss s + Gst t,  y_t = Grt r + Gst s + Gtt t
                 acc2x2 bs = prod2(Gh[0], Vs);
                 dot2_step2(bs, Gh[1], Vt);
                 acc2x2 bt = prod2(Gh[1], Vs);
@@ -403,7 +456,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
             mbar_wait(barB, pB);
             return;
         }
-        if (tid == 0 && e + gridDim.x < E) stage(barA, Ge + (int64_t)gridDim.x * 6 * kN3);   // next element's first half
+        if (tid == 0 && e + gridDim.x < E) stage(barA, e + gridDim.x, 0);   // next element's first half
         const int eSraw = max16(sred + 32), eTraw = max16(sred + 48);
         const int eS = eSraw == INT_MIN ? 0 : min(eSraw, kBadExp), eT = eTraw == INT_MIN ? 0 : min(eTraw, kBadExp);
         const bool bad = eU == 0x7ff || eD == 0x7ff || eRraw >= kBadExp || eSraw >= kBadExp || eTraw >= kBadExp;
@@ -518,12 +571,67 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
 
 }  // namespace oz16
 
-int launch_f64tc16(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s) {
-    auto kern = oz16::ax_f64tc16_kernel;
-    int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz16::kSmem));
+template <bool PRE>
+static int launch16(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s) {
+    auto kern = oz16::ax_f64tc16_kernel<PRE>;
+    constexpr size_t kSmem = oz16::smem_bytes<PRE>();
+    int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     if (st != SEMAX_OK) return st;
     const int64_t grid = std::min<int64_t>(E, (int64_t)device_sm_count());
-    kern<<<(unsigned)grid, oz16::kThreads, oz16::kSmem, s>>>(E, u, G, D, w);
+    kern<<<(unsigned)grid, oz16::kThreads, kSmem, s>>>(E, u, G, D, w);
+    return launch_status();
+}
+
+int launch_f64tc16(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s) {
+    return launch16<false>(E, u, G, D, w, s);
+}
+
+int launch_f64tc16_prepared(int64_t E, const double *u, const void *Gp, const double *D, double *w,
+                            cudaStream_t s) {
+    return launch16<true>(E, u, reinterpret_cast<const double *>(Gp), D, w, s);
+}
+
+size_t f64tc16_prepared_bytes_per_element() { return 2 * (size_t)oz16::kGSP; }
+
+namespace oz16 {
+// The prepared geometric factor of order 15: per node and half, the three
+// entries split hi + lo exactly as ax_f64tc16_kernel<false> splits them, and
+// the half's largest biased exponent.  One thread per node.
+__global__ void __launch_bounds__(256) prepare16_kernel(int64_t E, const double *__restrict__ G,
+                                                        unsigned char *__restrict__ Gp) {
+    const int64_t total = E * kN3, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
+        const int64_t e = p >> 12;
+        const int q = (int)(p & (kN3 - 1));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const double *Gh = G + (2 * e + h) * 3 * kN3 + q;
+            double Gc[3];
+            unsigned hws[3], hmax = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                Gc[a] = ld_stream(Gh + a * kN3);
+                hws[a] = habs(Gc[a]);
+                hmax = max(hmax, hws[a]);
+            }
+            const int eg = (int)(hmax >> 20), sh = max(eg, 1) - 1023;
+            const unsigned K = (unsigned)(896 + sh) << 23, mw = (unsigned)max(897 + sh, 1) << 20;
+            unsigned char *half = Gp + (2 * e + h) * (int64_t)kGSP;
+            float2 *out = reinterpret_cast<float2 *>(half);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const df d = split_g(Gc[a], hws[a], K, mw);
+                out[a * kN3 + q] = make_float2(d.hi, d.lo);
+            }
+            reinterpret_cast<int *>(half + kGS)[q] = eg;
+        }
+    }
+}
+}  // namespace oz16
+
+int prepare_f64tc16(int64_t E, const double *G, void *Gp, cudaStream_t s) {
+    const int64_t blocks = std::min<int64_t>((E * oz16::kN3 + 255) / 256, (int64_t)device_sm_count() * 8);
+    oz16::prepare16_kernel<<<(unsigned)blocks, 256, 0, s>>>(E, G, (unsigned char *)Gp);
     return launch_status();
 }
 

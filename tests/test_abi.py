@@ -65,7 +65,8 @@ def test_argument_validation(lib, fn):
 def test_prepared_f64tc_validation(lib):
     size = ctypes.c_size_t(0)
     assert lib.sem_ax_f64tc_prepare_size(10, 7, ctypes.byref(size)) == 0 and size.value == 10 * 26624
-    assert lib.sem_ax_f64tc_prepare_size(10, 15, ctypes.byref(size)) == -2     # order 7 only
+    assert lib.sem_ax_f64tc_prepare_size(10, 15, ctypes.byref(size)) == 0 and size.value == 10 * 229376
+    assert lib.sem_ax_f64tc_prepare_size(10, 5, ctypes.byref(size)) == -2      # orders 7 and 15 only
     assert lib.sem_ax_f64tc_prepare_size(-1, 7, ctypes.byref(size)) == -1
     assert lib.sem_ax_f64tc_prepare_size(10, 7, None) == -1
     G, Gp = A, A + (1 << 32)
@@ -77,7 +78,7 @@ def test_prepared_f64tc_validation(lib):
     u, D, w = A + (2 << 32), A + (3 << 32), A + (4 << 32)
     f = lib.sem_ax_f64tc_prepared
     assert f(0, 7, None, None, None, None, None) == 0
-    assert f(4, 15, u, Gp, D, w, None) == -2
+    assert f(4, 5, u, Gp, D, w, None) == -2
     assert f(-1, 7, u, Gp, D, w, None) == -1
     assert f(4, 7, u, None, D, w, None) == -1
     assert f(4, 7, u, Gp + 8, D, w, None) == -3

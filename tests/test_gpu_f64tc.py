@@ -311,6 +311,28 @@ def test_f64tc_prepared_equals_f64tc_bit_for_bit(semax, oracle_mod):
     assert torch.equal(semax.sem_ax_f64tc_prepared(big.u, Gpb, big.D), semax.sem_ax_f64tc(big.u, big.G, big.D))
 
 
+def test_f64tc_prepared_order15_equals_f64tc_bit_for_bit(semax, oracle_mod):
+    """Order 15: the prepared halves give sem_ax_f64tc's result bit for bit,
+    ragged, with zero, far-apart-scale and non-finite G, and at the bench size."""
+    m = si.make_mesh(np.random.default_rng(96), 21, 15, device="cuda")
+    G = m.G.clone()
+    G[2] = 0.0
+    G[4, 3:] *= 2.0 ** 80
+    G[6, :3, ::2] *= 2.0 ** -70
+    G[8, 5, 1, 2, 3] = float("nan")
+    for GG in (m.G, G):
+        Gp = semax.f64tc_prepare(GG)
+        assert Gp.numel() == 21 * 229376
+        w = semax.sem_ax_f64tc_prepared(m.u, Gp, m.D)
+        ref = semax.sem_ax_f64tc(m.u, GG, m.D)
+        keep = torch.arange(21, device=w.device) != (8 if GG is G else -1)
+        assert torch.equal(w[keep], ref[keep])
+    assert torch.isnan(w[8]).all()
+    big = si.make_workload(2, device="cuda")[0]
+    Gpb = semax.f64tc_prepare(big.G)
+    assert torch.equal(semax.sem_ax_f64tc_prepared(big.u, Gpb, big.D), semax.sem_ax_f64tc(big.u, big.G, big.D))
+
+
 def test_energy_norm_on_the_gpu(semax, oracle_mod):
     """u^T A u with the FP64 reduction on the GPU: equal to the oracle's energy
     for the FP64 and both FP64-accurate forms, and positive for random u."""
