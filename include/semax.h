@@ -133,7 +133,8 @@ int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const doubl
  * call than FP64 G.  sem_ax_f64tc_prepared then computes, bit for bit, what
  * sem_ax_f64tc computes from G, without the split.  N = 7 and N = 15
  * (SEMAX_EUNSUPPORTED_N otherwise).  Gp: device memory, 16-byte aligned,
- * owned by the caller, not overlapping G or w. */
+ * owned by the caller, not overlapping G or w, and prepared for the same E
+ * and N (its size is not checked, like G's in sem_ax). */
 int sem_ax_f64tc_prepare_size(int64_t E, int N, size_t *bytes);
 int sem_ax_f64tc_prepare(int64_t E, int N, const double *G, void *Gp, void *stream);
 int sem_ax_f64tc_prepared(int64_t E, int N, const double *u, const void *Gp, const double *D,
