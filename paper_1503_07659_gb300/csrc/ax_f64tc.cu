@@ -352,6 +352,8 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         // ---- E: sum, undo the scales, store
         // w = 2^((eU - 1022) + 2 (eD - 1022) + (eW - 126) - 36) V_out
         const int SH = (eU - 1022) + 2 * (eD - 1022) + (eW - 126) - 36;
+        const bool fastSH = SH >= -896 && SH <= 896;   // the same for the whole element
+        const unsigned cSH = (unsigned)(896 + SH) << 20;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = 2 * warp + h, nb = k * 64 + g * 8 + 2 * t;
@@ -366,7 +368,9 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 const float lo = __fadd_rn(__fadd_rn(__fadd_rn(vo[2 * h + c].lo, sv.y), tl), __fadd_rn(a.lo, b.lo));
                 // bit-level conversions with the scale in the exponent field: one FP64 add
                 double dh, dl;
-                if (dfx::f2d_scaled(b.hi, SH, dh) && dfx::f2d_scaled(lo, SH, dl))
+                if (fastSH)
+                    o[c] = dfx::f2d_shift(b.hi, cSH) + dfx::f2d_shift(lo, cSH);
+                else if (dfx::f2d_scaled(b.hi, SH, dh) && dfx::f2d_scaled(lo, SH, dl))
                     o[c] = dh + dl;
                 else
                     o[c] = scale2(dfx::f2d(b.hi) + dfx::f2d(lo), SH);

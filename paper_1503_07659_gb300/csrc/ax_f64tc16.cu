@@ -531,6 +531,8 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
         const int base = (eU - 1022) + 2 * (eD - 1022) - 126 - 36;
         const int SHr = base + eR, SHs = base + eS, SHt = base + eT;
         const int SHm = max(SHr, max(SHs, SHt));
+        const bool fastSH = SHm >= -896 && SHm <= 896;   // the same for the whole element
+        const unsigned cSH = (unsigned)(896 + SHm) << 20;
         const float2 fr = f2(pow2f_or_zero(SHr - SHm)), fs = f2(pow2f_or_zero(SHs - SHm)), ft = f2(pow2f_or_zero(SHt - SHm));
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
@@ -553,7 +555,9 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                     // bit-level conversions and scaling: one FP64 add per node (the whole
                     // CTA runs this phase at once, so FP64-pipe work here is not hidden)
                     double dh, dl;
-                    if (dfx::f2d_scaled(vh, SHm, dh) && dfx::f2d_scaled(vl, SHm, dl))
+                    if (fastSH)
+                        o[c] = dfx::f2d_shift(vh, cSH) + dfx::f2d_shift(vl, cSH);
+                    else if (dfx::f2d_scaled(vh, SHm, dh) && dfx::f2d_scaled(vl, SHm, dl))
                         o[c] = dh + dl;
                     else
                         o[c] = scale2(dfx::f2d(vh) + dfx::f2d(vl), SHm);

@@ -194,6 +194,16 @@ __device__ __forceinline__ bool f2d_scaled(float f, int sh, double &out) {
     return true;
 }
 
+// f * 2^SH as a double when SH is in [-896, 896], where every normal float's
+// exponent plus 896 + SH stays in the double's normal range: exponent-field
+// arithmetic only, csh = (896 + SH) << 20 computed once per element; the same
+// bits as f2d_scaled; 0 for zero and subnormal f.
+__device__ __forceinline__ double f2d_shift(float f, unsigned csh) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned hw = (((b >> 3) & 0x0fffffffu) + csh) | (b & 0x80000000u);
+    return (b & 0x7f800000u) ? __hiloint2double((int)hw, (int)(b << 29)) : 0.0;
+}
+
 __device__ __forceinline__ int biased_exponent(double x) {
     return (int)((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7ffu);
 }
@@ -413,8 +423,12 @@ __device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__rest
         }
         const df acc = add(add(sr[s], ss[s]), su[s]);
         const int su_e = sexp[e] > 0 ? sexp[e] : 1, sw_e = sexp[epb + e] > 0 ? sexp[epb + e] : 1;
+        const int SH = su_e + sw_e - 2046;
         double dh, dl;
-        if (f2d_scaled(acc.hi, su_e + sw_e - 2046, dh) && f2d_scaled(acc.lo, su_e + sw_e - 2046, dl)) {
+        if (SH >= -896 && SH <= 896) {
+            const unsigned cSH = (unsigned)(896 + SH) << 20;
+            we[f] = f2d_shift(acc.hi, cSH) + f2d_shift(acc.lo, cSH);
+        } else if (f2d_scaled(acc.hi, SH, dh) && f2d_scaled(acc.lo, SH, dl)) {
             we[f] = dh + dl;                       // exact scaling, one FP64 add
         } else {
             const double su_scale = __longlong_as_double((long long)su_e << 52);
