@@ -10,13 +10,20 @@ nodes per second) for that workload, plus
   e2e           the same metric with u, G, D, w in pinned host memory, streamed
                 by the kernel over NVLink-C2C (and, for comparison, with
                 explicit copies);
-  roofline      the FP64 kernel against the FP64 pipe peak (the path is bound by
-                FP64 arithmetic on GB300, not by HBM);
+  roofline      the FP64 kernel against the FP64 pipe peak measured in the same
+                run by an FMA-chain probe (the path is bound by FP64 arithmetic on
+                GB300, not by HBM); the FP64-accurate tensor-core form carries its
+                own roofline block against the measured HBM copy bandwidth;
   variants      FP32 / BF16-split (N=15, E=8192), the uneven-order batched plan,
                 and N=7, E=262144 in FP64 and FP32, each with GDOF/s, GB/s and its
                 error against the FP64 GPU path (itself held to 1e-12 of the CPU
                 oracle by the parity tests), measured with the FP64 GPU reducer;
-  cpu_baseline  the FP64 CPU oracle on the host cores.
+                the L2-resident workloads (N=7, E=512 and the uneven-order mix)
+                with and without an L2 flush between calls;
+  cpu_baseline  the FP64 CPU oracle on the host cores (all of them and one; the
+                median of three runs each).  Its output on the N=7, E=32768
+                workload and on a seeded 1% sample of N=7, E=262144 also gives
+                every form's error against the oracle (`rel_err_vs_oracle`).
 
 `--impl reference` times the CPU oracle alone (the reference arm).
 Under torchrun each rank runs its own E=32768 shard (weak scaling, no
@@ -28,7 +35,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -45,8 +51,15 @@ import sem_inputs as si  # noqa: E402
 
 METRIC = "Ax GDOF/s and HBM GB/s (FP64 vs mixed/batched) on 1 GB300 at stated error"
 WORKLOAD = dict(N=7, E=32768)
-FP64_PEAK_TFLOPS = 1.2586   # 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (GB300 FP64 pipe)
-KERNEL_SOURCES = ["ax_tile.cuh", "ax_eo.cuh", "ax_plain.cuh", "ax_f64.cu", "common.cuh"]
+# nominal FP64 pipe rate from unit counts and the maximum clock, for context
+# only: the roofline's peak is the probe's measurement in the same run
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk x flop x Hz
+# sources of the kernels whose ncu DRAM traffic is kept under profiles/ (the
+# traffic is used only while these still hash to what was profiled)
+KERNEL_SOURCES = {
+    "ax_f64_n8_e32768": ["ax_tile.cuh", "ax_eo.cuh", "ax_plain.cuh", "ax_f64.cu", "common.cuh"],
+    "ax_f64tc_n8_e32768": ["ax_f64tc.cu", "ax_f64tc.cuh", "ax_f64x.cuh", "mma_sync.cuh", "common.cuh"],
+}
 
 
 def flops_per_element(n: int) -> int:
@@ -170,6 +183,30 @@ def time_region(fn, steps: int, warmup: int, world: int = 1) -> float:
     return max_over_ranks(a.elapsed_time(b) / 1e3, world)
 
 
+def time_each(fn, reps: int, flush: torch.Tensor | None = None, warmup: int = 3) -> float:
+    """Median seconds of `reps` single calls, each between its own CUDA events
+    on the current stream.  With `flush` (a buffer of twice the L2 size), the
+    buffer is written before every call, outside the events, so each call
+    starts with none of its inputs in L2."""
+    for _ in range(warmup):
+        fn()
+    s = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in evs:
+        if flush is not None:
+            flush.fill_(1)
+        a.record(s)
+        fn()
+        b.record(s)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in evs) / 1e3
+
+
+def l2_flush_buffer() -> torch.Tensor:
+    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    return torch.empty(2 * l2, dtype=torch.uint8, device="cuda")
+
+
 def rel_err_gpu(semax, w, ref) -> float:
     r = semax.reduce(w.reshape(-1), ref.reshape(-1)).cpu().numpy()
     return float(r[0] / r[1]) if r[1] > 0 else float(r[0])
@@ -183,26 +220,27 @@ def energy_rel_gpu(semax, u, w, ref) -> float:
     return abs(e - e0) / abs(e0)
 
 
-def kernel_source_sha() -> str:
+def kernel_source_sha(name: str) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[name]:
         with open(os.path.join(ROOT, "paper_1503_07659_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic() -> float | None:
-    """DRAM bytes per launch of the FP64 kernel from the committed ncu summary,
-    only if the kernel sources still hash to what was profiled."""
-    path = os.path.join(ROOT, "profiles", "ax_f64_n8_e32768.md")
-    if not os.path.exists(path):
+def profiled_traffic(name: str, field: str = "dram_bytes_per_launch") -> float | None:
+    """DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
+    of a kernel on the bench's workload, from profiles/<name>.json, only if the
+    kernel's sources still hash to what was profiled."""
+    path = os.path.join(ROOT, "profiles", name + ".json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
         return None
-    text = open(path).read()
-    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not (m_sha and m_tr) or m_sha.group(1) != kernel_source_sha():
+    if rec.get("kernel_source_sha") != kernel_source_sha(name):
         return None
-    return float(m_tr.group(1))
+    return float(rec[field]) if field in rec else None
 
 
 def load_peaks() -> dict:
@@ -215,54 +253,80 @@ def load_peaks() -> dict:
 
 # ---------------------------------------------------------------- CPU oracle baseline
 
-def cpu_baseline(mesh_host, target_s: float = 10.0) -> dict:
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle(mesh_host, nthreads: int, min_s: float) -> tuple[float, int, int, np.ndarray]:
+    """One timed run of the oracle: passes over the whole workload until min_s
+    has elapsed (at least one).  Returns (seconds per pass, threads, passes, w)."""
+    import oracle
+    u, G, D = mesh_host
+    reps, used, w = 0, 0, None
+    t0 = time.perf_counter()
+    while reps == 0 or time.perf_counter() - t0 < min_s:
+        w, used = oracle.sem_ax(u, G, D, nthreads=nthreads, return_threads=True)
+        reps += 1
+    return (time.perf_counter() - t0) / reps, int(used), reps, w
+
+
+def cpu_baseline(mesh_host) -> tuple[dict, np.ndarray]:
+    """The FP64 CPU oracle on the N=7, E=32768 workload: on every core of the
+    process's affinity set and on one core, the median of three runs each.
+    Returns the baseline record and the oracle's output."""
     import oracle
     oracle.build()
     u, G, D = mesh_host
-    E = u.shape[0]
-    n = D.shape[0]
-    reps, t0 = 0, time.perf_counter()
-    used = 0
-    while True:
-        _, used = oracle.sem_ax(u, G, D, return_threads=True)
-        reps += 1
-        if time.perf_counter() - t0 >= target_s or reps >= 50:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": reps * E * n ** 3 / dt / 1e9, "unit": "GDOF/s", "cores": int(used), "kind": "oracle",
-            "sample": f"full N=7 E={E} workload x {reps} pass(es), {dt:.1f} s, FP64 plain C loop nest "
-                      f"(-O2 -ffp-contract=off, OpenMP over elements)"}
+    dofs = u.shape[0] * D.shape[0] ** 3
+    cores = host_cores()
+    runs_all = [time_oracle(mesh_host, cores, 2.0) for _ in range(3)]
+    runs_one = [time_oracle(mesh_host, 1, 0.0) for _ in range(3)]
+    t_all = statistics.median(r[0] for r in runs_all)
+    t_one = statistics.median(r[0] for r in runs_one)
+    rec = {"value": dofs / t_all / 1e9, "unit": "GDOF/s", "cores": runs_all[0][1], "kind": "oracle",
+           "sample": (f"full N=7 E={u.shape[0]} workload ({dofs} nodes), median of 3 runs of "
+                      f"{runs_all[0][2]} pass(es) each on {runs_all[0][1]} threads; FP64 plain C loop nest "
+                      f"(-O2 -ffp-contract=off, OpenMP over elements)"),
+           "one_core": {"value": dofs / t_one / 1e9, "unit": "GDOF/s", "cores": runs_one[0][1],
+                        "sample": "the same workload, median of 3 single-pass runs on 1 thread"}}
+    return rec, runs_all[0][3]
+
+
+def config_dict(E: int, dofs: int) -> dict:
+    """The workload both arms report (the driver compares the two)."""
+    return {"workload": "sem_ax FP64 N=7 E=32768 per GPU (16.8M nodes, 1.07 GB/call)",
+            "N": 7, "E_per_gpu": E, "nodes_per_gpu": dofs,
+            "l2": "inputs larger than L2 (1.07 GB per step vs 129 MB L2), no flush"}
 
 
 def run_reference(args, rank, world):
-    """The reference arm: the FP64 CPU oracle on the host cores."""
+    """The reference arm: the FP64 CPU oracle on the host cores, one pass over
+    the whole N=7, E=32768 workload per step."""
     if rank != 0:
         return
     import oracle
     oracle.build()
     m = si.make_workload(1, device="cpu")[0]
     u, G, D = m.u.numpy(), m.G.numpy(), m.D.numpy()
-    n = m.n
-    chunk = 1024                       # elements per timed step (a bounded sample)
-    sl = [(c, min(m.E, c + chunk)) for c in range(0, m.E, chunk)]
-    for q in range(args.warmup):
-        a, b = sl[q % len(sl)]
-        oracle.sem_ax(u[a:b], G[a:b], D)
+    cores = host_cores()
+    for _ in range(args.warmup):
+        oracle.sem_ax(u, G, D, nthreads=cores)
     t0 = time.perf_counter()
     used = 0
-    for q in range(args.steps):
-        a, b = sl[q % len(sl)]
-        _, used = oracle.sem_ax(u[a:b], G[a:b], D, return_threads=True)
+    for _ in range(args.steps):
+        _, used = oracle.sem_ax(u, G, D, nthreads=cores, return_threads=True)
     dt = time.perf_counter() - t0
-    value = args.steps * chunk * n ** 3 / dt / 1e9
+    value = args.steps * m.dofs / dt / 1e9
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "sem_ax FP64 N=7 E=32768 (16.8M nodes)", "N": 7, "E": m.E,
-                       "step_sample": f"{chunk} elements per step, cycling through the workload"},
+            "data": "synthetic", "config": config_dict(m.E, m.dofs),
             "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": int(used), "kind": "oracle",
-                             "sample": f"{chunk}-element slices of the N=7 E=32768 workload, {args.steps} steps"},
+                             "sample": f"the whole N=7 E=32768 workload per step, {args.steps} steps, "
+                                       f"{int(used)} OpenMP threads"},
             "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -318,6 +382,27 @@ def variants(semax, reps: int) -> dict:
     del u, u64, G, D, w, ref, X, xq
     torch.cuda.empty_cache()
 
+    flush = l2_flush_buffer()
+
+    def flushed(fn, dofs, nbytes, r=reps):
+        """{"l2_warm": back-to-back calls (inputs partly in L2), "l2_flushed":
+        single calls after an L2 flush}"""
+        warm = rate(fn, dofs, nbytes, r)
+        t = time_each(fn, r, flush)
+        return {"l2_warm": warm, "l2_flushed": {"gdofs": dofs / t / 1e9, "hbm_gbs": nbytes / t / 1e9,
+                                                "us_per_call": t * 1e6}}
+
+    # N=7, E=512 (16.8 MB, fits in the 129 MB L2): with and without a flush
+    m = si.make_workload(0, device="cuda")[0]
+    w0 = torch.empty_like(m.u)
+    gp0 = semax.f64tc_prepare(m.G)
+    out["f64_N7_E512"] = flushed(lambda: semax.sem_ax(m.u, m.G, m.D, w0), m.dofs, m.dofs * bytes_per_node(8))
+    out["f64tc_N7_E512"] = flushed(lambda: semax.sem_ax_f64tc(m.u, m.G, m.D, w0), m.dofs,
+                                   m.dofs * bytes_per_node(8))
+    out["f64tc_prepared_N7_E512"] = flushed(lambda: semax.sem_ax_f64tc_prepared(m.u, gp0, m.D, w0), m.dofs,
+                                            m.dofs * bytes_per_node(8))
+    del m, w0, gp0
+
     # uneven orders, one persistent graph-captured launch vs per-order launches
     mix = si.make_workload(3, device="cuda")
     dofs = sum(x.dofs for x in mix)
@@ -325,9 +410,12 @@ def variants(semax, reps: int) -> dict:
     plan = semax.Plan([(x.N, x.u, x.G, x.D, w) for x, w in zip(mix, ws)], tune=True)
     r = rate(plan, dofs, dofs * bytes_per_node(8))
     r["tuned"] = {x.N: plan.config(x.N) for x in mix}
+    r["l2_flushed"] = flushed(plan, dofs, dofs * bytes_per_node(8))["l2_flushed"]
     out["batched_plan_mix"] = r
-    out["per_order_launches_mix"] = rate(lambda: [semax.sem_ax(x.u, x.G, x.D, w) for x, w in zip(mix, ws)],
-                                         dofs, dofs * bytes_per_node(8))
+    per_order = lambda: [semax.sem_ax(x.u, x.G, x.D, w) for x, w in zip(mix, ws)]  # noqa: E731
+    r = rate(per_order, dofs, dofs * bytes_per_node(8))
+    r["l2_flushed"] = flushed(per_order, dofs, dofs * bytes_per_node(8))["l2_flushed"]
+    out["per_order_launches_mix"] = r
     ref_ws = [w.clone() for w in ws]
     planx = semax.Plan([(x.N, x.u, x.G, x.D, w) for x, w in zip(mix, ws)], f64x=True)
     r = rate(planx, dofs, dofs * bytes_per_node(8))
@@ -337,7 +425,9 @@ def variants(semax, reps: int) -> dict:
     planx.close()
     plantc = semax.Plan([(x.N, x.u, x.G, x.D, w) for x, w in zip(mix, ws)], f64x=True, f64tc=True)
     r = rate(plantc, dofs, dofs * bytes_per_node(8))
+    r["l2_flushed"] = flushed(plantc, dofs, dofs * bytes_per_node(8))["l2_flushed"]
     r["rel_err_vs_f64"] = max(rel_err_gpu(semax, w, rw) for w, rw in zip(ws, ref_ws))
+    r["status"] = plantc.status()
     r["arith"] = ("orders 7 and 15 on the tensor-core FP64-accurate kernels beside the persistent launch "
                   "(forked stream in the same graph), the other even orders on the double-float tile")
     out["batched_plan_f64tc_mix"] = r
@@ -389,6 +479,11 @@ def variants(semax, reps: int) -> dict:
     dofs = m.dofs
     w64 = torch.empty_like(m.u)
     out["f64_N7_E262144"] = rate(lambda: semax.sem_ax(m.u, m.G, m.D, w64), dofs, dofs * bytes_per_node(8), 10)
+    # the seeded 1% element sample (2,621 elements) the oracle checks
+    idx = np.sort(np.random.default_rng([1503, 7659, 4, 1]).choice(m.E, size=m.E // 100, replace=False))
+    it = torch.from_numpy(idx).cuda()
+    sample = {"u": m.u[it].cpu().numpy(), "G": m.G[it].cpu().numpy(), "D": m.D.cpu().numpy(),
+              "elements": int(idx.size), "of": int(m.E)}
     u, G, D = m.u.float(), m.G.float(), m.D.float()
     del m
     w32 = torch.empty_like(u)
@@ -396,9 +491,33 @@ def variants(semax, reps: int) -> dict:
     r["rel_err_vs_f64"] = rel_err_gpu(semax, w32, w64)
     r["energy_rel_err"] = energy_rel_gpu(semax, u, w32, w64)
     out["f32_N7_E262144"] = r
+    sample["w"] = {"f64_N7_E262144": w64[it].cpu().numpy(), "f32_N7_E262144": w32[it].double().cpu().numpy()}
     del u, G, D, w32, w64
     torch.cuda.empty_cache()
-    return out
+    return out, sample
+
+
+def probe_peak(semax, prec: str, iters: int, launches: int, dev_index: int) -> dict:
+    """The FMA pipe's measured throughput (semax_fma_probe: 8 chains of
+    dependent FMAs per thread, 8 blocks of 256 threads per SM), CUDA events
+    around `launches` back-to-back launches, clocks sampled meanwhile."""
+    semax.fma_probe(prec, iters=iters)              # warm-up
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    flops = 0.0
+    for _ in range(launches):
+        flops += semax.fma_probe(prec, iters=iters)[1]
+    b.record(s)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t = a.elapsed_time(b) / 1e3
+    return {"tflops": flops / t / 1e12, "seconds": t, "clocks": clk,
+            "how": f"semax_fma_probe {prec}: 8 independent FMA chains x {iters} steps per thread, "
+                   f"8 x 256 threads per SM, {launches} launches between CUDA events"}
 
 
 def run_ours(args, rank, world):
@@ -417,6 +536,10 @@ def run_ours(args, rank, world):
     t_step = t / args.steps
     value = world * dofs / t_step / 1e9
 
+    # the FP64 pipe's peak, measured now, against which the headline kernel is graded
+    fp64_peak = probe_peak(semax, "f64", 4096, 10, dev.index)
+    fp32_peak = probe_peak(semax, "f32", 65536, 20, dev.index)
+
     # end to end from pinned host memory.  Primary: the kernel reads u, G, D
     # and writes w in pinned host memory over NVLink-C2C (every byte crosses
     # the link inside the timed region).  Secondary: explicit copies.
@@ -427,12 +550,13 @@ def run_ours(args, rank, world):
     w_h = torch.empty_like(u_h).pin_memory()
     t_zc = time_region(lambda: semax.sem_ax(u_h, G_h, D_h, w_h), e2e_steps,
                        max(3, args.warmup // 10), world) / e2e_steps
-    assert torch.equal(w_h, w.cpu()), "host-memory result differs from the device-resident result"
+    w_host = w.cpu()
+    assert torch.equal(w_h, w_host), "host-memory result differs from the device-resident result"
     w_h.zero_()
     bufs = semax.sem_ax_from_host(u_h, G_h, D_h, w_h)
     t_cp = time_region(lambda: semax.sem_ax_from_host(u_h, G_h, D_h, w_h, bufs), e2e_steps,
                        max(3, args.warmup // 10), world) / e2e_steps
-    assert torch.equal(w_h, w.cpu()), "end-to-end result differs from the device-resident result"
+    assert torch.equal(w_h, w_host), "end-to-end result differs from the device-resident result"
     # the host link's ceiling for this step: a plain pinned-to-device copy of
     # the step's input bytes (copy engine; more streams or other chunk sizes
     # measured the same ~210 GB/s on this machine)
@@ -450,27 +574,41 @@ def run_ours(args, rank, world):
            "copy_path": {"value": world * dofs / t_cp / 1e9, "unit": "GDOF/s",
                          "path": "cudaMemcpyAsync H2D of u, G, D; sem_ax; D2H of w"}}
     del bufs, u_h, G_h, w_h
+    outputs = {"sem_ax": w_host}      # host copies, checked against the oracle below
+
+    peaks = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    nbytes = dofs * bytes_per_node(8)
 
     # FP64-accurate double-float form on the same workload
     wx = torch.empty_like(w)
     t_x = time_region(lambda: semax.sem_ax_f64x(mesh.u, mesh.G, mesh.D, wx), args.steps, args.warmup,
                       world) / args.steps
-    f64x = {"gdofs": world * dofs / t_x / 1e9, "hbm_gbs": world * dofs * bytes_per_node(8) / t_x / 1e9,
+    f64x = {"gdofs": world * dofs / t_x / 1e9, "hbm_gbs": world * nbytes / t_x / 1e9,
             "us_per_call": t_x * 1e6, "rel_err_vs_f64": rel_err_gpu(semax, wx, w),
             "energy_rel_err": energy_rel_gpu(semax, mesh.u, wx, w),
             "arith": "double-float contractions on the FP32 pipe, FP64 geometric factor; FP64 in/out"}
+    outputs["sem_ax_f64x"] = wx.cpu()
     del wx
     # FP64-accurate tensor-core form (exact digit slicing) on the same workload
     wt = torch.empty_like(w)
-    t_t = time_region(lambda: semax.sem_ax_f64tc(mesh.u, mesh.G, mesh.D, wt), args.steps, args.warmup,
-                      world) / args.steps
-    f64tc = {"gdofs": world * dofs / t_t / 1e9, "hbm_gbs": world * dofs * bytes_per_node(8) / t_t / 1e9,
+    tc_call = lambda: semax.sem_ax_f64tc(mesh.u, mesh.G, mesh.D, wt)  # noqa: E731
+    t_t = time_region(tc_call, args.steps, args.warmup, world) / args.steps
+    f64tc = {"gdofs": world * dofs / t_t / 1e9, "hbm_gbs": world * nbytes / t_t / 1e9,
              "us_per_call": t_t * 1e6, "rel_err_vs_f64": rel_err_gpu(semax, wt, w),
              "energy_rel_err": energy_rel_gpu(semax, mesh.u, wt, w),
-             "hbm_frac_of_measured": world * dofs * bytes_per_node(8) / t_t / 1e9 / load_peaks().get("hbm_gbs", 6786.6),
-             "bound": "instruction issue (tensor pipe below 20 % busy; digit extraction and double-float work on the CUDA cores)",
              "arith": "contractions on FP16 tensor cores by exact base-1024 digit slicing (5 digits, levels 0..4), "
-                      "double-float level sums and geometric factor; FP64 in/out"}
+                      "double-float level sums and geometric factor; FP64 in/out",
+             "roofline": {"bound": "hbm", "kernel": "oz::ax_f64tc_kernel<false> (N=7)",
+                          "achieved": nbytes / t_t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": nbytes / t_t / 1e9 / hbm_peak,
+                          "traffic": profiled_traffic("ax_f64tc_n8_e32768"),
+                          "algorithmic_bytes_per_launch": nbytes,
+                          "bytes_per_node": 64, "peak_source": hbm_src + ", of measured",
+                          "limiter": "instruction issue (digit extraction, level sums and the double-float "
+                                     "geometric factor on the CUDA cores; tensor pipe below 20 % busy)"}}
+    outputs["sem_ax_f64tc"] = wt.cpu()
     # the same with G prepared once (split into float pairs): bit for bit, without the split per call
     gp = semax.f64tc_prepare(mesh.G)
     torch.cuda.synchronize()
@@ -480,12 +618,23 @@ def run_ours(args, rank, world):
     b_ev.record()
     torch.cuda.synchronize()
     wp = torch.empty_like(w)
-    t_p = time_region(lambda: semax.sem_ax_f64tc_prepared(mesh.u, gp, mesh.D, wp), args.steps, args.warmup,
-                      world) / args.steps
+    tp_call = lambda: semax.sem_ax_f64tc_prepared(mesh.u, gp, mesh.D, wp)  # noqa: E731
+    t_p = time_region(tp_call, args.steps, args.warmup, world) / args.steps
+    pre_bytes = gp.numel() / mesh.E / 512 + 16          # prepared G, u and w per node
     f64tc["prepared_G"] = {"gdofs": world * dofs / t_p / 1e9, "us_per_call": t_p * 1e6,
-                           "bytes_per_node": (gp.numel() / mesh.E + 8 * 512 * 2) / 512,
+                           "hbm_gbs_at_64B_per_node": world * nbytes / t_p / 1e9,
+                           "hbm_frac_at_64B_per_node": world * nbytes / t_p / 1e9 / hbm_peak,
+                           "bytes_per_node_moved": pre_bytes,
                            "prepare_us": a_ev.elapsed_time(b_ev) * 1e3,
                            "bit_identical": bool(torch.equal(wp, wt)),
+                           "roofline": {"bound": "hbm", "kernel": "oz::ax_f64tc_kernel<true> (N=7, G prepared)",
+                                        "achieved": nbytes / t_p / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                        "frac": nbytes / t_p / 1e9 / hbm_peak,
+                                        "traffic": profiled_traffic("ax_f64tc_n8_e32768", "prepared_dram_bytes_per_launch"),
+                                        "algorithmic_bytes_per_launch": nbytes, "bytes_per_node": 64,
+                                        "peak_source": hbm_src + ", of measured",
+                                        "note": "counted at the operator's 64 B/node; the prepared G moves "
+                                                f"{pre_bytes:.0f} B/node, its extra bytes are overhead"},
                            "arith": "G split into (hi, lo) float pairs once (sem_ax_f64tc_prepare), "
                                     "then sem_ax_f64tc_prepared per call"}
     del wt, wp, gp
@@ -500,33 +649,81 @@ def run_ours(args, rank, world):
     if rank != 0:
         return
     flops = E * flops_per_element(n)
-    nbytes = dofs * bytes_per_node(8)
     achieved = flops / t_step / 1e12
-    peaks = load_peaks()
     roofline = {"bound": "alu", "kernel": "ax_plain_kernel<double, 8, even/odd lines>",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": profiled_traffic(),
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.070 GHz (GB300 nominal 1.25 TF)",
+                "achieved": achieved, "peak": fp64_peak["tflops"], "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak["tflops"], "traffic": profiled_traffic("ax_f64_n8_e32768"),
+                "peak_source": "measured in this run: " + fp64_peak["how"] + ", of measured",
+                "peak_clock_mhz": fp64_peak["clocks"].get("sm_mhz"),
+                "peak_nominal": FP64_NOMINAL_TFLOPS,
+                "frac_of_nominal": achieved / FP64_NOMINAL_TFLOPS,
                 "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
                 "hbm_gbs": nbytes / t_step / 1e9,
-                "hbm_frac_of_measured": nbytes / t_step / 1e9 / peaks.get("hbm_gbs", 6786.6)}
+                "hbm_frac_of_measured": nbytes / t_step / 1e9 / hbm_peak,
+                "note": "algorithmic flops count 12n+15 per node; the even/odd kernel issues 47 FP64 "
+                        "instructions per node where the plain form needs 57, so frac can exceed 1"}
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "sem_ax FP64 N=7 E=32768 per GPU (16.8M nodes, 1.07 GB/call)",
-                       "N": 7, "E_per_gpu": E, "nodes_per_gpu": dofs,
-                       "l2": "inputs larger than L2 (1.07 GB per step vs 129 MB L2), no flush"},
+            "config": config_dict(E, dofs),
             "hbm_gbs": world * nbytes / t_step / 1e9,
             "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline}
+    line["peaks_measured"] = {"fp64_tflops": fp64_peak["tflops"], "fp64_clocks": fp64_peak["clocks"],
+                              "fp32_tflops": fp32_peak["tflops"], "fp32_clocks": fp32_peak["clocks"],
+                              "hbm_gbs": hbm_peak, "hbm_source": hbm_src}
     line["f64x"] = f64x
     line["f64tc"] = f64tc
     line["helmholtz_f64"] = helm
+    sample = None
     if not args.no_variants:
-        line["variants"] = variants(semax, reps=20)
+        line["variants"], sample = variants(semax, reps=20)
     if not args.no_cpu_baseline and world == 1:
         host = shard_seed_workload(0, "cpu")
-        line["cpu_baseline"] = cpu_baseline((host.u.numpy(), host.G.numpy(), host.D.numpy()))
+        line["cpu_baseline"], w_oracle = cpu_baseline((host.u.numpy(), host.G.numpy(), host.D.numpy()))
+        # every form's error on this workload against the oracle, over the whole output
+        errs = {name: float(np.max(np.abs(out.numpy() - w_oracle)) / np.max(np.abs(w_oracle)))
+                for name, out in outputs.items()}
+        line["rel_err_vs_oracle"] = errs
+        line["f64x"]["rel_err_vs_oracle"] = errs["sem_ax_f64x"]
+        line["f64tc"]["rel_err_vs_oracle"] = errs["sem_ax_f64tc"]
+        if sample is not None:
+            import oracle
+            ref = oracle.sem_ax(sample["u"], sample["G"], sample["D"], nthreads=host_cores())
+            for name, got in sample["w"].items():
+                line["variants"][name]["rel_err_vs_oracle_sample"] = float(
+                    np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+                line["variants"][name]["oracle_sample"] = (f"{sample['elements']} of {sample['of']} elements "
+                                                           f"(seeded 1% choice)")
     print(json.dumps(line), flush=True)
+
+
+SINGLE_KERNELS = ("f64", "f64tc", "f64tc_prepared", "f64x", "f64tc_n15", "f32_n15", "bf16x3_n15", "bf16x6_n15")
+
+
+def run_single_kernel(args):
+    """One form alone on its bench workload (N=7, E=32768, or N=15, E=8192 for
+    the *_n15 names): W warm-up and K timed calls, nothing else on the GPU in
+    between; prints {"kernel", "us_per_call", "gdofs"}.  This is the command
+    the ncu summaries under profiles/ capture."""
+    import paper_1503_07659_gb300 as semax
+    name = args.kernel
+    m = si.make_workload(2 if name.endswith("n15") else 1, device="cuda")[0]
+    u, G, D = m.u, m.G, m.D
+    if name in ("f32_n15", "bf16x3_n15", "bf16x6_n15"):
+        u, G, D = u.float(), G.float(), D.float()
+    w = torch.empty_like(u)
+    gp = semax.f64tc_prepare(G) if name == "f64tc_prepared" else None
+    fn = {"f64": lambda: semax.sem_ax(u, G, D, w),
+          "f64tc": lambda: semax.sem_ax_f64tc(u, G, D, w),
+          "f64tc_n15": lambda: semax.sem_ax_f64tc(u, G, D, w),
+          "f64tc_prepared": lambda: semax.sem_ax_f64tc_prepared(u, gp, D, w),
+          "f64x": lambda: semax.sem_ax_f64x(u, G, D, w),
+          "f32_n15": lambda: semax.sem_ax_f32(u, G, D, w),
+          "bf16x3_n15": lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=3),
+          "bf16x6_n15": lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=6)}[name]
+    t = time_region(fn, args.steps, args.warmup) / args.steps
+    print(json.dumps({"kernel": name, "N": m.N, "E": m.E, "us_per_call": t * 1e6, "gdofs": m.dofs / t / 1e9}),
+          flush=True)
 
 
 def main():
@@ -537,12 +734,16 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=SINGLE_KERNELS, default=None,
+                    help="time one form alone on its workload (for profiling) and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world = dist_setup()
     try:
-        if args.impl == "reference":
+        if args.kernel is not None:
+            run_single_kernel(args)
+        elif args.impl == "reference":
             run_reference(args, rank, world)
         else:
             if not torch.cuda.is_available():

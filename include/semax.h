@@ -121,6 +121,26 @@ int sem_ax_f64x(int64_t E, int N, const double *u, const double *G, const double
 int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const double *D,
                  double *w, void *stream);
 
+/* sem_ax_f64tc with a status word for its bounded device-side waits.  The
+ * tensor-core kernels of orders 7 and 15 stage each element's u and G in
+ * shared memory with TMA bulk copies that complete on an mbarrier, and wait
+ * for them with a bounded number of polls (2^20 by default; each poll may
+ * suspend the thread briefly).  A copy that never completes is a failure of
+ * the device, not a property of any input.  If a wait gives up, its CTA
+ * stores SEMAX_ETIMEOUT in *status, writes NaN to every output element it
+ * has not yet written, waits once more (bounded, with the default limit) for
+ * its copies in flight, and exits; other CTAs carry on.  (Should that second
+ * wait give up too, the CTA exits with a copy still in flight, which may then
+ * land in shared memory the CTA no longer owns: the device is failing.)  `status` is a
+ * device int (4-byte aligned) that the kernels write only on a timeout: set
+ * it to SEMAX_OK before the call and read it once `stream` has reached the
+ * call's end.  NULL reports nothing (exactly sem_ax_f64tc).  Orders other
+ * than 7 and 15 run the double-float tile, which has no waits, and never
+ * write it.  The status is not the call's return value because the call
+ * returns before the kernel runs. */
+int sem_ax_f64tc_status(int64_t E, int N, const double *u, const double *G, const double *D,
+                        double *w, int *status, void *stream);
+
 /* The tensor-core FP64-accurate Ax with the geometric factor prepared once
  * (for repeated applications with the same G, as in an iterative solver).
  * sem_ax_f64tc_prepare splits each node's six G entries into (hi, lo) float
@@ -139,6 +159,9 @@ int sem_ax_f64tc_prepare_size(int64_t E, int N, size_t *bytes);
 int sem_ax_f64tc_prepare(int64_t E, int N, const double *G, void *Gp, void *stream);
 int sem_ax_f64tc_prepared(int64_t E, int N, const double *u, const void *Gp, const double *D,
                           double *w, void *stream);
+/* sem_ax_f64tc_prepared with the status word of sem_ax_f64tc_status. */
+int sem_ax_f64tc_prepared_status(int64_t E, int N, const double *u, const void *Gp, const double *D,
+                                 double *w, int *status, void *stream);
 
 /* FP32 storage and FP32 compute.  G_scale is NULL or [E] per-element factors
  * s_e: the kernel then treats the stored G as G_e / s_e and multiplies the
@@ -223,6 +246,11 @@ int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, int ngroups
                        int tune, const char *cache_path, int flags);
 int sem_ax_plan_exec(semax_plan *plan, void *stream);
 int sem_ax_plan_destroy(semax_plan *plan);
+/* SEMAX_ETIMEOUT if, in an execution of the plan since the last call, a
+ * staging wait of its tensor-core launches (SEMAX_PLAN_F64TC) gave up (see
+ * sem_ax_f64tc_status), else SEMAX_OK; clears the plan's status word.
+ * Blocks the host until the work queued on `stream` so far has finished. */
+int sem_ax_plan_status(semax_plan *plan, void *stream);
 /* The configuration the plan uses for order N: elements per tile and thread
  * mapping (0 = one thread per node, 1 = one thread per (i,j) column,
  * 2 = one thread per line with the even/odd split of D, even n only,
@@ -274,7 +302,9 @@ int sem_ax_diag(int64_t E, int N, const double *G, const double *D, double *diag
  * max_iter iterations, checked every 10 iterations: a block of 10 iterations
  * is one CUDA-graph launch with all scalars in device memory.  Solve blocks
  * the host until it returns; it is ordered after earlier work on `stream` and
- * later work on `stream` is ordered after it. */
+ * later work on `stream` is ordered after it.  With SEMAX_PCG_F64TC it
+ * returns SEMAX_ETIMEOUT (x then holds NaN) if a staging wait of the
+ * tensor-core operator gave up (see sem_ax_f64tc_status). */
 typedef struct semax_pcg semax_pcg;
 enum { SEMAX_PCG_F64X = 1,     /* apply A with sem_ax_f64x (double-float, FP64-accurate) */
        SEMAX_PCG_F64TC = 2,     /* apply A with sem_ax_f64tc (tensor-core digit slicing, FP64-accurate) */
@@ -309,8 +339,10 @@ int semax_reduce(int64_t count, const void *a, int a_prec, const void *b, int b_
  * needed more would be rejected with SEMAX_EWORKSPACE.  Nothing in the array
  * has to start at zero (pass 1 writes every partial that pass 2 reads).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the one array and
+ * (cudaGetSymbolAddress, with that device current) and caches it for the
+ * device's current context; make that first call before any stream capture.
+ * After a device reset (cudaDeviceReset) the next call, in the new context,
+ * looks the address up again.  Every call on a device shares the one array and
  * it keeps the last call's partials: calls that can overlap on the GPU (on
  * different streams, or from several host threads) race on it and must be
  * ordered by the caller.  No cudaMalloc, cudaFree or allocating library call
@@ -323,6 +355,27 @@ int semax_reduce_noalloc(int64_t count, const void *a, int a_prec, const void *b
 const char *semax_strerror(int status);
 /* cudaError_t of the last failing CUDA call made by libsemax on this thread. */
 int semax_last_cuda_error(void);
+
+/* Diagnostic: the FMA pipe's throughput, the peak that the plain FP64 and
+ * FP32 kernels are graded against.  Launches `blocks` blocks of 256 threads,
+ * each thread running 8 independent chains of `iters` dependent fused
+ * multiply-adds in FP64 (prec = SEMAX_F64) or FP32 (SEMAX_F32) and storing
+ * one value per thread in `sink` (device, blocks * 256 elements of that
+ * type); *flops (host) receives the floating-point operations the launch
+ * performs (an FMA counts 2).  Time it with events on `stream`.  The paper
+ * has no counterpart; this measures the machine. */
+int semax_fma_probe(int prec, int blocks, int iters, void *sink, double *flops, void *stream);
+
+/* Diagnostic: the number of polls the first staging wait of each element in
+ * the tensor-core kernels (sem_ax_f64tc and its variants) makes before it
+ * gives up, for launches queued after this call from any host thread;
+ * polls < 0 restores the default (2^20).  Launches already queued or
+ * captured into a graph keep the limit they were made with.  polls = 0
+ * makes every such wait give up at once, which drives the timeout path of
+ * sem_ax_f64tc_status on ordinary inputs: the CTA's copies are still
+ * drained by the second wait, which keeps the default limit.  The paper has
+ * no counterpart; this exists to test the status reporting. */
+int semax_set_wait_polls(int polls);
 
 #ifdef __cplusplus
 }

@@ -13,10 +13,10 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (SemaxError, semax_group, check, SEMAX_F32, SEMAX_F64, SEMAX_PLAN_F64X, SEMAX_PLAN_F64TC,
+from ._lib import (SemaxError, semax_group, check, SEMAX_OK, SEMAX_ETIMEOUT, SEMAX_F32, SEMAX_F64, SEMAX_PLAN_F64X, SEMAX_PLAN_F64TC,
                    SEMAX_PCG_F64X, SEMAX_PCG_F64TC, SEMAX_PCG_MIXED)
 
-__all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_bf16x3_geo", "sem_ax_batched", "Plan", "reduce",
+__all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f64tc_prepared", "f64tc_prepare", "set_wait_polls", "fma_probe", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_bf16x3_geo", "sem_ax_batched", "Plan", "reduce",
            "sem_ax_from_host", "SemaxError", "library_path"]
 
 
@@ -73,12 +73,36 @@ def sem_ax_f64x(u: torch.Tensor, G: torch.Tensor, D: torch.Tensor, w: torch.Tens
 
 
 def sem_ax_f64tc(u: torch.Tensor, G: torch.Tensor, D: torch.Tensor, w: torch.Tensor | None = None,
-                 stream=None) -> torch.Tensor:
-    """FP64 in/out, FP64-accurate; contractions on FP16 tensor cores by exact digit slicing (N = 7, 15)."""
+                 stream=None, status: torch.Tensor | None = None) -> torch.Tensor:
+    """FP64 in/out, FP64-accurate; contractions on FP16 tensor cores by exact digit slicing (N = 7, 15).
+    status: optional int32 device tensor that the kernel sets to SEMAX_ETIMEOUT (-6) if a staging wait
+    gives up (sem_ax_f64tc_status)."""
     E, N = _dims(u, D)
     w = _out(w, u)
-    check(_lib.lib().sem_ax_f64tc(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _stream(stream)), "sem_ax_f64tc")
+    if status is None:
+        check(_lib.lib().sem_ax_f64tc(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _stream(stream)), "sem_ax_f64tc")
+    else:
+        check(_lib.lib().sem_ax_f64tc_status(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _ptr(status),
+                                             _stream(stream)), "sem_ax_f64tc_status")
     return w
+
+
+def fma_probe(prec: str = "f64", blocks: int | None = None, iters: int = 4096, stream=None) -> tuple[torch.Tensor, float]:
+    """Launch the FMA-pipe probe (semax_fma_probe) on the current device; returns (sink, flops).
+    The caller times the launch with events on `stream`."""
+    dt = torch.float64 if prec == "f64" else torch.float32
+    if blocks is None:
+        blocks = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 8
+    sink = torch.empty(blocks * 256, dtype=dt, device="cuda")
+    flops = ctypes.c_double(0.0)
+    check(_lib.lib().semax_fma_probe(SEMAX_F64 if prec == "f64" else SEMAX_F32, int(blocks), int(iters), _ptr(sink),
+                                     ctypes.byref(flops), _stream(stream)), "semax_fma_probe")
+    return sink, flops.value
+
+
+def set_wait_polls(polls: int) -> None:
+    """Poll limit of the tensor-core kernels' first staging wait for later launches (< 0: default)."""
+    check(_lib.lib().semax_set_wait_polls(int(polls)), "semax_set_wait_polls")
 
 
 def f64tc_prepare(G: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -98,12 +122,16 @@ def f64tc_prepare(G: torch.Tensor, out: torch.Tensor | None = None, stream=None)
 
 
 def sem_ax_f64tc_prepared(u: torch.Tensor, Gp: torch.Tensor, D: torch.Tensor, w: torch.Tensor | None = None,
-                          stream=None) -> torch.Tensor:
-    """sem_ax_f64tc with the geometric factor from f64tc_prepare, bit for bit."""
+                          stream=None, status: torch.Tensor | None = None) -> torch.Tensor:
+    """sem_ax_f64tc with the geometric factor from f64tc_prepare, bit for bit (status as in sem_ax_f64tc)."""
     E, N = _dims(u, D)
     w = _out(w, u)
-    check(_lib.lib().sem_ax_f64tc_prepared(E, N, _ptr(u), _ptr(Gp), _ptr(D), _ptr(w), _stream(stream)),
-          "sem_ax_f64tc_prepared")
+    if status is None:
+        check(_lib.lib().sem_ax_f64tc_prepared(E, N, _ptr(u), _ptr(Gp), _ptr(D), _ptr(w), _stream(stream)),
+              "sem_ax_f64tc_prepared")
+    else:
+        check(_lib.lib().sem_ax_f64tc_prepared_status(E, N, _ptr(u), _ptr(Gp), _ptr(D), _ptr(w), _ptr(status),
+                                                      _stream(stream)), "sem_ax_f64tc_prepared_status")
     return w
 
 
@@ -168,6 +196,14 @@ class Plan:
 
     def __call__(self, stream=None) -> None:
         check(_lib.lib().sem_ax_plan_exec(self._handle, _stream(stream)), "sem_ax_plan_exec")
+
+    def status(self, stream=None) -> int:
+        """SEMAX_OK, or SEMAX_ETIMEOUT if a tensor-core launch of the plan had a staging wait give up since
+        the last call (blocks until the stream's queued work is done; clears the word)."""
+        st = _lib.lib().sem_ax_plan_status(self._handle, _stream(stream))
+        if st not in (SEMAX_OK, SEMAX_ETIMEOUT):
+            check(st, "sem_ax_plan_status")
+        return st
 
     def config(self, N: int) -> tuple[int, int]:
         epb, mp = ctypes.c_int(0), ctypes.c_int(0)

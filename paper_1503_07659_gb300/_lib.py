@@ -13,6 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsemax.so")
 
 SEMAX_OK = 0
+SEMAX_ETIMEOUT = -6
 SEMAX_F64, SEMAX_F32 = 0, 1
 SEMAX_PLAN_F64X, SEMAX_PLAN_F64TC = 1, 2
 SEMAX_PCG_F64X, SEMAX_PCG_F64TC, SEMAX_PCG_MIXED = 1, 2, 4
@@ -25,14 +26,14 @@ STATUS_NAMES = {
 
 # every symbol include/semax.h declares
 EXPORTS = (
-    "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f64tc_prepare_size", "sem_ax_f64tc_prepare",
-    "sem_ax_f64tc_prepared", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_bf16x3_geo",
+    "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f64tc_status", "sem_ax_f64tc_prepare_size",
+    "sem_ax_f64tc_prepare", "sem_ax_f64tc_prepared", "sem_ax_f64tc_prepared_status", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_bf16x3_geo",
     "sem_ax_batched_workspace_size", "sem_ax_batched",
-    "sem_ax_plan_create", "sem_ax_plan_exec", "sem_ax_plan_destroy", "sem_ax_plan_config",
+    "sem_ax_plan_create", "sem_ax_plan_exec", "sem_ax_plan_destroy", "sem_ax_plan_status", "sem_ax_plan_config",
     "semax_gs_create", "semax_gs_apply", "semax_gs_destroy", "sem_ax_diag",
     "sem_pcg_create", "sem_pcg_solve", "sem_pcg_destroy",
     "semax_reduce_workspace_size", "semax_reduce", "semax_reduce_noalloc",
-    "semax_strerror", "semax_last_cuda_error",
+    "semax_strerror", "semax_last_cuda_error", "semax_set_wait_polls", "semax_fma_probe",
 )
 
 
@@ -59,6 +60,8 @@ def _load():
         "sem_ax": [i64, i32, vp, vp, vp, vp, vp],
         "sem_ax_f64x": [i64, i32, vp, vp, vp, vp, vp],
         "sem_ax_f64tc": [i64, i32, vp, vp, vp, vp, vp],
+        "sem_ax_f64tc_status": [i64, i32, vp, vp, vp, vp, vp, vp],
+        "sem_ax_f64tc_prepared_status": [i64, i32, vp, vp, vp, vp, vp, vp],
         "sem_ax_f64tc_prepare_size": [i64, i32, ctypes.POINTER(sz)],
         "sem_ax_f64tc_prepare": [i64, i32, vp, vp, vp],
         "sem_ax_f64tc_prepared": [i64, i32, vp, vp, vp, vp, vp],
@@ -71,6 +74,7 @@ def _load():
         "sem_ax_plan_create": [ctypes.POINTER(vp), vp, i32, i32, ctypes.c_char_p, i32],
         "sem_ax_plan_exec": [vp, vp],
         "sem_ax_plan_destroy": [vp],
+        "sem_ax_plan_status": [vp, vp],
         "sem_ax_plan_config": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "semax_gs_create": [ctypes.POINTER(vp), i64, vp, i64, vp],
         "semax_gs_apply": [vp, vp, i32, vp],
@@ -84,6 +88,8 @@ def _load():
         "semax_reduce_noalloc": [i64, vp, i32, vp, i32, vp, vp],
         "semax_strerror": [i32],
         "semax_last_cuda_error": [],
+        "semax_set_wait_polls": [i32],
+        "semax_fma_probe": [i32, i32, i32, vp, ctypes.POINTER(ctypes.c_double), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)  # raises AttributeError if the library lacks a declared symbol

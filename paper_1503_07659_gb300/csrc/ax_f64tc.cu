@@ -133,7 +133,7 @@ __device__ __forceinline__ int max4(const int *p) { return max(max(p[0], p[1]), 
 template <bool PRE>
 __global__ void __launch_bounds__(kThreads, 4)
 ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
-                const double *__restrict__ D, double *__restrict__ w) {
+                const double *__restrict__ D, double *__restrict__ w, int *__restrict__ status, int polls) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *dig = smem;
     float2 *bs = reinterpret_cast<float2 *>(smem + kDigBytes);   // s-direction results
@@ -188,7 +188,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         double *we = w + e * 512;
 
         // ---- A: u -> digits (thread's nodes: k = 2w + h, j = g, i = 2t + c)
-        const bool timed_out = !mbar_wait(bar, parity);
+        const bool timed_out = !mbar_wait(bar, parity, polls);
         double2 uv[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) uv[h] = ust[(2 * warp + h) * 32 + g * 4 + t];
@@ -198,8 +198,9 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         ex = __reduce_max_sync(0xffffffffu, ex);
         if (lane == 0) sred[warp] = ex;
         if (__syncthreads_or(timed_out)) {
-            // the staged data never arrived: mark this CTA's remaining outputs
-            // NaN and leave (the decision is the same in every thread)
+            // the staged data never arrived: report it, mark this CTA's remaining
+            // outputs NaN and leave (the decision is the same in every thread)
+            if (tid == 0) report_timeout(status);
             for (int64_t r = e; r < E; r += gridDim.x)
                 for (int q = tid; q < 512; q += kThreads) w[r * 512 + q] = __longlong_as_double(0x7ff8000000000000ll);
             mbar_wait(bar, parity);   // one more bounded wait for the copies in flight
@@ -384,7 +385,8 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
 }
 
 template <bool PRE>
-static int launch(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s) {
+static int launch(int64_t E, const double *u, const double *G, const double *D, double *w, int *status,
+                  cudaStream_t s) {
     auto kern = ax_f64tc_kernel<PRE>;
     constexpr size_t kSmem = smem_bytes<PRE>();
     int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
@@ -396,7 +398,7 @@ static int launch(int64_t E, const double *u, const double *G, const double *D, 
     st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kSmem));
     if (st != SEMAX_OK) return st;
     const int64_t grid = std::min<int64_t>(E, (int64_t)device_sm_count() * std::max(per_sm, 1));
-    kern<<<(unsigned)grid, kThreads, kSmem, s>>>(E, u, G, D, w);
+    kern<<<(unsigned)grid, kThreads, kSmem, s>>>(E, u, G, D, w, status, first_wait_polls());
     return launch_status();
 }
 
@@ -434,8 +436,9 @@ __global__ void __launch_bounds__(256) prepare_kernel(int64_t E, const double *_
 }  // namespace semax
 
 namespace semax {
-int launch_f64tc16(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s);
-int launch_f64tc16_prepared(int64_t E, const double *u, const void *Gp, const double *D, double *w,
+int launch_f64tc16(int64_t E, const double *u, const double *G, const double *D, double *w, int *status,
+                   cudaStream_t s);
+int launch_f64tc16_prepared(int64_t E, const double *u, const void *Gp, const double *D, double *w, int *status,
                             cudaStream_t s);
 int prepare_f64tc16(int64_t E, const double *G, void *Gp, cudaStream_t s);
 size_t f64tc16_prepared_bytes_per_element();
@@ -443,13 +446,19 @@ size_t f64tc16_prepared_bytes_per_element();
 
 using namespace semax;
 
-extern "C" int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const double *D, double *w,
-                            void *stream) {
+extern "C" int sem_ax_f64tc_status(int64_t E, int N, const double *u, const double *G, const double *D, double *w,
+                                   int *status, void *stream) {
     int st = check_args(E, N, u, G, D, w);
     if (st != SEMAX_OK || E == 0) return st;
-    if (N == 7) return oz::launch<false>(E, u, G, D, w, (cudaStream_t)stream);
-    if (N == 15) return launch_f64tc16(E, u, G, D, w, (cudaStream_t)stream);
-    return sem_ax_f64x(E, N, u, G, D, w, stream);   // other orders: the double-float tile
+    if (status && ((uintptr_t)status % alignof(int)) != 0) return SEMAX_EALIGN;
+    if (N == 7) return oz::launch<false>(E, u, G, D, w, status, (cudaStream_t)stream);
+    if (N == 15) return launch_f64tc16(E, u, G, D, w, status, (cudaStream_t)stream);
+    return sem_ax_f64x(E, N, u, G, D, w, stream);   // other orders: the double-float tile (no waits)
+}
+
+extern "C" int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const double *D, double *w,
+                            void *stream) {
+    return sem_ax_f64tc_status(E, N, u, G, D, w, nullptr, stream);
 }
 
 // bytes of one element of the prepared geometric factor, 0 if N has none
@@ -478,18 +487,24 @@ extern "C" int sem_ax_f64tc_prepare(int64_t E, int N, const double *G, void *Gp,
     return launch_status();
 }
 
-extern "C" int sem_ax_f64tc_prepared(int64_t E, int N, const double *u, const void *Gp, const double *D, double *w,
-                                     void *stream) {
+extern "C" int sem_ax_f64tc_prepared_status(int64_t E, int N, const double *u, const void *Gp, const double *D,
+                                            double *w, int *status, void *stream) {
     if (E < 0) return SEMAX_EINVAL;
     if (!prepared_bytes(N)) return SEMAX_EUNSUPPORTED_N;
     if (E == 0) return SEMAX_OK;
     if (!u || !Gp || !D || !w) return SEMAX_EINVAL;
     if (!aligned16(u) || !aligned16(Gp) || !aligned16(w) || ((uintptr_t)D % alignof(double)) != 0)
         return SEMAX_EALIGN;
+    if (status && ((uintptr_t)status % alignof(int)) != 0) return SEMAX_EALIGN;
     const size_t n = (size_t)N + 1, ub = (size_t)E * n * n * n * sizeof(double);
     if (overlaps(w, ub, u, ub) || overlaps(w, ub, Gp, (size_t)E * prepared_bytes(N)) ||
         overlaps(w, ub, D, n * n * sizeof(double)))
         return SEMAX_EALIAS;
-    if (N == 15) return launch_f64tc16_prepared(E, u, Gp, D, w, (cudaStream_t)stream);
-    return oz::launch<true>(E, u, reinterpret_cast<const double *>(Gp), D, w, (cudaStream_t)stream);
+    if (N == 15) return launch_f64tc16_prepared(E, u, Gp, D, w, status, (cudaStream_t)stream);
+    return oz::launch<true>(E, u, reinterpret_cast<const double *>(Gp), D, w, status, (cudaStream_t)stream);
+}
+
+extern "C" int sem_ax_f64tc_prepared(int64_t E, int N, const double *u, const void *Gp, const double *D, double *w,
+                                     void *stream) {
+    return sem_ax_f64tc_prepared_status(E, N, u, Gp, D, w, nullptr, stream);
 }

@@ -30,6 +30,13 @@ using mma::smem_u32;
 
 constexpr int kBadExp = 1 << 20;             // marks a non-finite input in the exponent reductions
 
+// Status word of a CTA whose staging wait gave up (NULL: not reported).  The
+// CTA then marks every output it has not written NaN, waits once more (with
+// the default poll limit) for its copies in flight, and leaves.
+__device__ __forceinline__ void report_timeout(int *status) {
+    if (status) atomicExch(status, (int)SEMAX_ETIMEOUT);
+}
+
 // TMA bulk copy global -> shared, completing on an mbarrier transaction
 // count; the CTA is its own cluster, so its shared::cta address is valid.
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, unsigned bytes, uint32_t bar) {
@@ -43,10 +50,10 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-// Wait for phase `parity` of the mbarrier, giving up after a bounded number
-// of polls (each try_wait may itself suspend briefly): false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity) {
-    for (int it = 0; it < (1 << 20); ++it) {
+// Wait for phase `parity` of the mbarrier, giving up after `polls` polls
+// (each try_wait may itself suspend briefly): false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity, int polls = kDefaultWaitPolls) {
+    for (int it = 0; it < polls; ++it) {
         unsigned done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}"

@@ -88,7 +88,7 @@ __device__ __forceinline__ int max16(const int *p) {
 template <bool PRE>
 __global__ void __launch_bounds__(kThreads, 1)
 ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
-                  const double *__restrict__ D, double *__restrict__ w) {
+                  const double *__restrict__ D, double *__restrict__ w, int *__restrict__ status, int polls) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *ud = smem;
     unsigned char *dd = ud + kUD;
@@ -167,7 +167,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
         double *we = w + e * kN3;
 
         // ---- A: u -> digits
-        const bool toA = !mbar_wait(barA, pA);   // G's first half (staged during the previous element)
+        const bool toA = !mbar_wait(barA, pA, polls);   // G's first half (staged during the previous element)
         int ex = 1;
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
@@ -175,7 +175,8 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
             for (int h = 0; h < 2; ++h) ex = max(ex, (int)(max(habs(uv[nt][h].x), habs(uv[nt][h].y)) >> 20));
         ex = __reduce_max_sync(0xffffffffu, ex);
         if (lane == 0) sred[warp] = ex;
-        if (__syncthreads_or(toA)) {
+        if (__syncthreads_or(toA)) {   // the staged data never arrived: report, mark NaN, leave
+            if (tid == 0) report_timeout(status);
             for (int64_t r = e; r < E; r += gridDim.x)
                 for (int q = tid; q < kN3; q += kThreads) w[r * kN3 + q] = __longlong_as_double(0x7ff8000000000000ll);
             mbar_wait(barA, pA);
@@ -368,7 +369,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
         }
 
         // ---- C2: G's second half (ss, st, tt): finish y_s, y_t
-        const bool toB = !mbar_wait(barB, pB);
+        const bool toB = !mbar_wait(barB, pB, polls);
         acc2x2 YS[4], YT[4];
         int shS[8];
         int smax = INT_MIN, tmx = INT_MIN;
@@ -451,6 +452,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
             sred[48 + warp] = tmx;
         }
         if (__syncthreads_or(toB)) {
+            if (tid == 0) report_timeout(status);
             for (int64_t r = e; r < E; r += gridDim.x)
                 for (int q = tid; q < kN3; q += kThreads) w[r * kN3 + q] = __longlong_as_double(0x7ff8000000000000ll);
             mbar_wait(barB, pB);
@@ -576,23 +578,25 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
 }  // namespace oz16
 
 template <bool PRE>
-static int launch16(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s) {
+static int launch16(int64_t E, const double *u, const double *G, const double *D, double *w, int *status,
+                    cudaStream_t s) {
     auto kern = oz16::ax_f64tc16_kernel<PRE>;
     constexpr size_t kSmem = oz16::smem_bytes<PRE>();
     int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     if (st != SEMAX_OK) return st;
     const int64_t grid = std::min<int64_t>(E, (int64_t)device_sm_count());
-    kern<<<(unsigned)grid, oz16::kThreads, kSmem, s>>>(E, u, G, D, w);
+    kern<<<(unsigned)grid, oz16::kThreads, kSmem, s>>>(E, u, G, D, w, status, first_wait_polls());
     return launch_status();
 }
 
-int launch_f64tc16(int64_t E, const double *u, const double *G, const double *D, double *w, cudaStream_t s) {
-    return launch16<false>(E, u, G, D, w, s);
+int launch_f64tc16(int64_t E, const double *u, const double *G, const double *D, double *w, int *status,
+                   cudaStream_t s) {
+    return launch16<false>(E, u, G, D, w, status, s);
 }
 
-int launch_f64tc16_prepared(int64_t E, const double *u, const void *Gp, const double *D, double *w,
+int launch_f64tc16_prepared(int64_t E, const double *u, const void *Gp, const double *D, double *w, int *status,
                             cudaStream_t s) {
-    return launch16<true>(E, u, reinterpret_cast<const double *>(Gp), D, w, s);
+    return launch16<true>(E, u, reinterpret_cast<const double *>(Gp), D, w, status, s);
 }
 
 size_t f64tc16_prepared_bytes_per_element() { return 2 * (size_t)oz16::kGSP; }

@@ -266,7 +266,7 @@ struct semax_plan {
     BatchParams P;                    // the groups of the persistent launch
     std::vector<semax_group> tc;      // SEMAX_PLAN_F64TC: the groups of order 7 and 15 (own launches)
     std::vector<TileChoice> choice;   // by n
-    unsigned long long *counter = nullptr;
+    unsigned long long *counter = nullptr;   // 256 bytes: the work counter, and at byte 128 the status word
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned magic = 0x5e3a9u;
@@ -368,6 +368,8 @@ static std::vector<TileChoice> candidates(int n) {
     return ok;
 }
 
+static int *plan_status(semax_plan *p) { return reinterpret_cast<int *>(reinterpret_cast<char *>(p->counter) + 128); }
+
 static void destroy_plan(semax_plan *p) {
     if (!p) return;
     if (p->exec) cudaGraphExecDestroy(p->exec);
@@ -402,6 +404,7 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
     if (cache_path && !tune) read_cache(cache_path, dev, p->choice, have);
 
     st = cuda_status(cudaMalloc(&p->counter, 256));
+    if (st == SEMAX_OK) st = cuda_status(cudaMemset(p->counter, 0, 256));
     cudaStream_t cs = nullptr;
     if (st == SEMAX_OK) st = cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
 
@@ -448,7 +451,7 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
                 if (lst == SEMAX_OK) lst = cuda_status(cudaStreamWaitEvent(cs2, fork, 0));
                 for (size_t q = 0; q < p->tc.size() && lst == SEMAX_OK; ++q) {
                     const semax_group &g = p->tc[q];
-                    if (g.E > 0) lst = sem_ax_f64tc(g.E, g.N, g.u, g.G, g.D, g.w, cs2);
+                    if (g.E > 0) lst = sem_ax_f64tc_status(g.E, g.N, g.u, g.G, g.D, g.w, plan_status(p), cs2);
                 }
                 if (lst == SEMAX_OK) lst = cuda_status(cudaEventRecord(join, cs2));
             }
@@ -477,6 +480,17 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
 extern "C" int sem_ax_plan_exec(semax_plan *plan, void *stream) {
     if (!plan || plan->magic != 0x5e3a9u) return SEMAX_ENOPLAN;
     return cuda_status(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+}
+
+extern "C" int sem_ax_plan_status(semax_plan *plan, void *stream) {
+    if (!plan || plan->magic != 0x5e3a9u) return SEMAX_ENOPLAN;
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = SEMAX_OK;
+    int st = cuda_status(cudaMemcpyAsync(&h, plan_status(plan), sizeof h, cudaMemcpyDeviceToHost, s));
+    if (st == SEMAX_OK) st = cuda_status(cudaMemsetAsync(plan_status(plan), 0, sizeof h, s));
+    if (st == SEMAX_OK) st = cuda_status(cudaStreamSynchronize(s));
+    if (st != SEMAX_OK) return st;
+    return h == SEMAX_ETIMEOUT ? SEMAX_ETIMEOUT : SEMAX_OK;
 }
 
 extern "C" int sem_ax_plan_destroy(semax_plan *plan) {

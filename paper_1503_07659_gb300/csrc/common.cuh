@@ -50,6 +50,13 @@ inline int check_args(int64_t E, int N, const T *u, const T *G, const T *D, cons
 
 int device_sm_count();
 
+// Polls a staging wait of the tensor-core kernels makes before it gives up;
+// the limit of each element's first wait is read at launch from a
+// process-wide setting (semax_set_wait_polls), the drain wait after a
+// timeout always takes the default.
+constexpr int kDefaultWaitPolls = 1 << 20;
+int first_wait_polls();
+
 // ---------------------------------------------------------------- device side
 
 // Streaming read-once loads: do not keep the line in L1.

@@ -3,6 +3,10 @@
 // widened to double first.  Two passes with a fixed partition (per-block
 // partials in caller workspace, then one block), so the result is the same on
 // every call with the same count.
+#include <cuda.h>
+
+#include <mutex>
+
 #include "common.cuh"
 
 namespace semax {
@@ -130,25 +134,65 @@ constexpr int kNoAllocBlocks = kRedMaxBlocks;
 static __device__ __align__(256) double g_reduce_scratch[3 * kNoAllocBlocks];
 
 constexpr int kMaxDevices = 64;
-static double *g_scratch_ptr[kMaxDevices];   // device address per device ordinal, set up once
 
-// Device address of g_reduce_scratch on the current device.  In host code the
-// symbol names a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device with that device current.
+// The cached device address of g_reduce_scratch, per device ordinal, with the
+// id of the context it was looked up in: after a device reset the runtime
+// makes a new primary context, where the array lives at an address that must
+// be looked up again.
+struct ScratchCache {
+    unsigned long long ctx_id = 0;
+    double *ptr = nullptr;
+};
+static ScratchCache g_scratch[kMaxDevices];
+static std::mutex g_scratch_mutex;
+
+// Unique id of the calling thread's current context (0 if none, or if the
+// driver entry points are unavailable), through the runtime's driver entry
+// point query, so that the library does not link the driver library itself.
+static unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of g_reduce_scratch in the current device's context.  In
+// host code the symbol names a host-side stand-in, so the address must come
+// from cudaGetSymbolAddress with that device current; it is looked up on the
+// first call in each context and cached.
 static int noalloc_scratch(double **out) {
     int dev = 0;
     int st = cuda_status(cudaGetDevice(&dev));
     if (st != SEMAX_OK) return st;
     if (dev < 0 || dev >= kMaxDevices) return SEMAX_EINVAL;
-    double *p = __atomic_load_n(&g_scratch_ptr[dev], __ATOMIC_ACQUIRE);
-    if (!p) {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    const unsigned long long id = current_context_id();
+    ScratchCache &c = g_scratch[dev];
+    if (!c.ptr || id == 0 || c.ctx_id != id) {
         void *addr = nullptr;
         st = cuda_status(cudaGetSymbolAddress(&addr, g_reduce_scratch));
         if (st != SEMAX_OK) return st;
-        p = static_cast<double *>(addr);
-        __atomic_store_n(&g_scratch_ptr[dev], p, __ATOMIC_RELEASE);
+        c.ptr = static_cast<double *>(addr);
+        c.ctx_id = current_context_id();   // the lookup made the context current if it was not
     }
-    *out = p;
+    *out = c.ptr;
     return SEMAX_OK;
 }
 

@@ -1,5 +1,7 @@
 // C ABI of libsemax: the plain FP64 / FP32 entry points, status strings and
 // device queries.  Argument checks happen here, before anything is queued.
+#include <atomic>
+
 #include "ax_plain.cuh"
 
 namespace semax {
@@ -8,6 +10,9 @@ int &last_cuda_error() {
     static thread_local int err = 0;
     return err;
 }
+
+static std::atomic<int> g_wait_polls{kDefaultWaitPolls};
+int first_wait_polls() { return g_wait_polls.load(std::memory_order_relaxed); }
 
 int device_sm_count() {
     int dev = 0, sms = 0;
@@ -69,3 +74,8 @@ extern "C" const char *semax_strerror(int status) {
 }
 
 extern "C" int semax_last_cuda_error(void) { return last_cuda_error(); }
+
+extern "C" int semax_set_wait_polls(int polls) {
+    g_wait_polls.store(polls < 0 ? kDefaultWaitPolls : polls, std::memory_order_relaxed);
+    return SEMAX_OK;
+}

@@ -395,7 +395,7 @@ struct semax_pcg {
     float *G32 = nullptr, *D32 = nullptr, *p32 = nullptr, *w32 = nullptr;   // SEMAX_PCG_MIXED
     double *d = nullptr;                                                   // its correction vector
     void *Gp = nullptr;                 // SEMAX_PCG_F64TC at N = 7: the prepared geometric factor
-    unsigned *counters = nullptr;                                          // last-block reductions (2)
+    unsigned *counters = nullptr;   // last-block reductions (2), then the tensor-core operator's status word
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -408,8 +408,9 @@ struct semax_pcg {
 // w = A_L v, FP64-accurate, with the operator the solver was created with
 static int pcg_apply_a64(semax_pcg *s, const double *v, double *w, cudaStream_t cs) {
     if (s->flags & SEMAX_PCG_F64X) return sem_ax_f64x(s->E, s->N, v, s->G, s->D, w, cs);
-    if (s->Gp) return sem_ax_f64tc_prepared(s->E, s->N, v, s->Gp, s->D, w, cs);   // bit for bit sem_ax_f64tc
-    if (s->flags & SEMAX_PCG_F64TC) return sem_ax_f64tc(s->E, s->N, v, s->G, s->D, w, cs);
+    int *status = reinterpret_cast<int *>(s->counters + 2);
+    if (s->Gp) return sem_ax_f64tc_prepared_status(s->E, s->N, v, s->Gp, s->D, w, status, cs);   // bit for bit sem_ax_f64tc
+    if (s->flags & SEMAX_PCG_F64TC) return sem_ax_f64tc_status(s->E, s->N, v, s->G, s->D, w, status, cs);
     return launch_plain<double>(s->E, s->N, default_tile<double>(s->N + 1), v, s->G, s->D, w, nullptr,
                                 Helm<double>{nullptr, 1.0, 0.0}, cs);
 }
@@ -495,8 +496,8 @@ extern "C" int sem_pcg_create(semax_pcg **pcg, int64_t E, int N, const double *G
         if (st == SEMAX_OK) st = cuda_status(cudaMalloc(v, vb));
     if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->part, sizeof(double) * 2 * kSolverMaxBlocks));
     if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->scal, sizeof(double) * S_COUNT));
-    if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->counters, 2 * sizeof(unsigned)));
-    if (st == SEMAX_OK) st = cuda_status(cudaMemset(s->counters, 0, 2 * sizeof(unsigned)));
+    if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&s->counters, 4 * sizeof(unsigned)));
+    if (st == SEMAX_OK) st = cuda_status(cudaMemset(s->counters, 0, 4 * sizeof(unsigned)));
     if (st == SEMAX_OK) st = cuda_status(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
     if (st == SEMAX_OK && (flags & SEMAX_PCG_MIXED)) {
         const int64_t nn = (int64_t)(N + 1) * (N + 1);
@@ -581,9 +582,15 @@ extern "C" int sem_pcg_solve(semax_pcg *s, const double *b, double *x, int max_i
         s->x_bound = st == SEMAX_OK ? xi : nullptr;
     }
     double h[S_COUNT] = {0};
+    int dev_status = SEMAX_OK;
+    // the scalars, and the status word of the tensor-core operator: a staging
+    // wait that gave up ends the solve with SEMAX_ETIMEOUT
     auto read_scalars = [&]() {
         int rs = cuda_status(cudaMemcpyAsync(h, s->scal, sizeof h, cudaMemcpyDeviceToHost, cs));
-        return rs == SEMAX_OK ? cuda_status(cudaStreamSynchronize(cs)) : rs;
+        if (rs == SEMAX_OK)
+            rs = cuda_status(cudaMemcpyAsync(&dev_status, s->counters + 2, sizeof dev_status, cudaMemcpyDeviceToHost, cs));
+        if (rs == SEMAX_OK) rs = cuda_status(cudaStreamSynchronize(cs));
+        return rs == SEMAX_OK && dev_status == SEMAX_ETIMEOUT ? SEMAX_ETIMEOUT : rs;
     };
     // iterate on xi until its recurrence residual falls to `target` of its start
     int done = 0;
@@ -610,6 +617,7 @@ extern "C" int sem_pcg_solve(semax_pcg *s, const double *b, double *x, int max_i
         return rs;
     };
     double rel = 1.0;
+    if (st == SEMAX_OK) st = cuda_status(cudaMemsetAsync(s->counters + 2, 0, sizeof(int), cs));
     if (st == SEMAX_OK) st = restart(x);
     if (st == SEMAX_OK) st = read_scalars();
     const double rr0 = h[S_RR0];

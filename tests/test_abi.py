@@ -156,3 +156,32 @@ def test_plan_rejects_unknown_flags(lib):
     h = ctypes.c_void_p()
     assert lib.sem_ax_plan_create(ctypes.byref(h), None, 0, 0, None, 8) == -1   # SEMAX_EINVAL
     assert lib.sem_ax_plan_create(ctypes.byref(h), None, 0, 0, None, 4) == -1
+
+
+def test_status_variants_validation(lib):
+    """The _status entry points check their arguments like the plain ones
+    (the status pointer must be int-aligned; NULL reports nothing)."""
+    u, G, D, w = A, A + (1 << 32), A + (2 << 32), A + (3 << 32)
+    f = lib.sem_ax_f64tc_status
+    assert f(0, 7, None, None, None, None, None, None) == 0
+    assert f(-1, 7, u, G, D, w, None, None) == -1
+    assert f(4, 16, u, G, D, w, None, None) == -2
+    assert f(4, 7, u, G, D, w, A + (5 << 32) + 2, None) == -3     # misaligned status
+    assert f(4, 7, u + 8, G, D, w, A + (5 << 32), None) == -3
+    assert f(4, 7, u, G, D, u + 64, A + (5 << 32), None) == -4
+    fp = lib.sem_ax_f64tc_prepared_status
+    Gp = A + (6 << 32)
+    assert fp(0, 7, None, None, None, None, None, None) == 0
+    assert fp(4, 5, u, Gp, D, w, None, None) == -2
+    assert fp(4, 7, u, Gp, D, w, A + (5 << 32) + 1, None) == -3
+    assert fp(4, 7, u, Gp, D, Gp + 1024, None, None) == -4
+    assert lib.sem_ax_plan_status(None, None) == -7
+    assert lib.semax_set_wait_polls(-1) == 0
+
+
+def test_fma_probe_validation(lib):
+    fl = ctypes.c_double(0.0)
+    assert lib.semax_fma_probe(2, 1, 1, A, ctypes.byref(fl), None) == -1      # bad precision
+    assert lib.semax_fma_probe(0, 0, 1, A, ctypes.byref(fl), None) == -1
+    assert lib.semax_fma_probe(0, 1, 1, None, ctypes.byref(fl), None) == -1
+    assert lib.semax_fma_probe(0, 1, 1, A + 4, ctypes.byref(fl), None) == -3

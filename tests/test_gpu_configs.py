@@ -1,0 +1,149 @@
+"""Parity of every GPU form against the FP64 CPU oracle on the five
+benchmark workloads, in the launch configurations the benchmark times.
+
+  workload 1  N=7,  E=32768  (16.8M nodes)  FP64 and the FP64-accurate forms, in full
+  workload 2  N=15, E=8192   (33.5M nodes)  FP64-accurate, FP32 and BF16 split forms, in full
+  workload 3  N in {3,5,7,9,11,15}, ~4.19M nodes: batched plans and per-order launches, in full
+  workload 4  N=7,  E=262144 (134M nodes)   FP64 and FP32 on a seeded 1% sample of elements
+              (2,621 of 262,144; Ax is element-local, so a sampled element's output is
+              checked exactly)
+
+Error measure: ||w - w_ref||_inf / ||w_ref||_inf over the checked outputs.
+Tolerances: FP64 and the FP64-accurate forms 1e-12 (the requirement); FP32
+storage and compute 1e-5; BF16 split with 6 products 1e-5, with 3 products
+5e-5 (~16 significant bits per operand; the measured error is stated in the
+benchmark output).
+"""
+import numpy as np
+import pytest
+import torch
+
+import sem_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+TOL_F64 = 1e-12
+TOL_F32 = 1e-5
+TOL_BF16 = {6: 1e-5, 3: 5e-5}
+
+
+@pytest.fixture(scope="module")
+def semax():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1503_07659_gb300 as m
+    return m
+
+
+def rel_err(w, ref):
+    w = w.detach().cpu().double().numpy() if hasattr(w, "detach") else w
+    return float(np.max(np.abs(w - ref)) / np.max(np.abs(ref)))
+
+
+@pytest.fixture(scope="module")
+def c1(oracle_mod):
+    m = si.make_workload(1, device="cuda")[0]
+    ref = oracle_mod.sem_ax(m.u.cpu(), m.G.cpu(), m.D.cpu())
+    yield m, ref
+    del m
+    torch.cuda.empty_cache()
+
+
+def test_workload1_fp64_in_full(semax, c1):
+    m, ref = c1
+    w = semax.sem_ax(m.u, m.G, m.D)
+    torch.cuda.synchronize()
+    assert rel_err(w, ref) <= TOL_F64
+
+
+@pytest.mark.parametrize("form", ["f64tc", "f64tc_prepared", "f64x"])
+def test_workload1_fp64_accurate_in_full(semax, c1, form):
+    m, ref = c1
+    if form == "f64tc_prepared":
+        w = semax.sem_ax_f64tc_prepared(m.u, semax.f64tc_prepare(m.G), m.D)
+    else:
+        w = getattr(semax, "sem_ax_" + form)(m.u, m.G, m.D)
+    torch.cuda.synchronize()
+    assert rel_err(w, ref) <= TOL_F64
+
+
+@pytest.fixture(scope="module")
+def c2(oracle_mod):
+    m = si.make_workload(2, device="cuda")[0]
+    ref = oracle_mod.sem_ax(m.u.cpu(), m.G.cpu(), m.D.cpu())
+    yield m, ref
+    del m
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("form", ["f64", "f64tc", "f64tc_prepared", "f64x"])
+def test_workload2_fp64_forms_in_full(semax, c2, form):
+    m, ref = c2
+    if form == "f64":
+        w = semax.sem_ax(m.u, m.G, m.D)
+    elif form == "f64tc_prepared":
+        w = semax.sem_ax_f64tc_prepared(m.u, semax.f64tc_prepare(m.G), m.D)
+    else:
+        w = getattr(semax, "sem_ax_" + form)(m.u, m.G, m.D)
+    torch.cuda.synchronize()
+    assert rel_err(w, ref) <= TOL_F64
+
+
+def test_workload2_mixed_forms_in_full(semax, c2):
+    m, ref = c2
+    u, G, D = m.u.float(), m.G.float(), m.D.float()
+    w = semax.sem_ax_f32(u, G, D)
+    torch.cuda.synchronize()
+    assert rel_err(w, ref) <= TOL_F32
+    for terms in (3, 6):
+        w = semax.sem_ax_bf16x3(u, G, D, terms=terms)
+        torch.cuda.synchronize()
+        assert rel_err(w, ref) <= TOL_BF16[terms], terms
+
+
+@pytest.fixture(scope="module")
+def c3(oracle_mod):
+    mix = si.make_workload(3, device="cuda")
+    refs = [oracle_mod.sem_ax(m.u.cpu(), m.G.cpu(), m.D.cpu()) for m in mix]
+    yield mix, refs
+    del mix
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("mode", ["per_order", "plan", "plan_tuned", "plan_f64x", "plan_f64tc"])
+def test_workload3_in_full(semax, c3, mode):
+    mix, refs = c3
+    ws = [torch.full_like(m.u, float("nan")) for m in mix]
+    if mode == "per_order":
+        for m, w in zip(mix, ws):
+            semax.sem_ax(m.u, m.G, m.D, w)
+    else:
+        plan = semax.Plan([(m.N, m.u, m.G, m.D, w) for m, w in zip(mix, ws)], tune=(mode == "plan_tuned"),
+                          f64x=mode in ("plan_f64x", "plan_f64tc"), f64tc=(mode == "plan_f64tc"))
+        for w in ws:
+            w.fill_(float("nan"))   # tuning runs the kernels on the bound arrays
+        plan()
+        if mode == "plan_f64tc":
+            assert plan.status() == 0
+        torch.cuda.synchronize()
+        plan.close()
+    for m, w, ref in zip(mix, ws, refs):
+        assert rel_err(w, ref) <= TOL_F64, m.N
+
+
+def test_workload4_sampled(semax, oracle_mod):
+    m = si.make_workload(4, device="cuda")[0]
+    assert m.E == 262144
+    w64 = semax.sem_ax(m.u, m.G, m.D)
+    u32, G32, D32 = m.u.float(), m.G.float(), m.D.float()
+    w32 = semax.sem_ax_f32(u32, G32, D32)
+    torch.cuda.synchronize()
+    assert torch.isfinite(w64).all() and torch.isfinite(w32).all()
+    idx = np.sort(np.random.default_rng([1503, 7659, 4, 1]).choice(m.E, size=m.E // 100, replace=False))
+    assert idx.size == 2621
+    it = torch.from_numpy(idx).cuda()
+    ref = oracle_mod.sem_ax(m.u[it].cpu(), m.G[it].cpu(), m.D.cpu())
+    assert rel_err(w64[it], ref) <= TOL_F64
+    assert rel_err(w32[it], ref) <= TOL_F32
+    del m, u32, G32, D32, w64, w32
+    torch.cuda.empty_cache()
