@@ -54,6 +54,9 @@ WORKLOAD = dict(N=7, E=32768)
 # nominal FP64 pipe rate from unit counts and the maximum clock, for context
 # only: the roofline's peak is the probe's measurement in the same run
 FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk x flop x Hz
+# FP64 instructions per node of the order-7 even/odd tile: even/odd sums 6,
+# FMAs 24, recombination 6, direction sums 2, geometric factor 9
+FP64_INSTR_PER_NODE_N7 = 47
 # sources of the kernels whose ncu DRAM traffic is kept under profiles/ (the
 # traffic is used only while these still hash to what was profiled)
 KERNEL_SOURCES = {
@@ -333,7 +336,7 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- our arm
 
-def variants(semax, reps: int) -> dict:
+def variants(semax, reps: int, fp64_peak_tflops: float) -> dict:
     """Secondary forms, each on its own workload (timed with CUDA events)."""
     out = {}
 
@@ -368,10 +371,12 @@ def variants(semax, reps: int) -> dict:
     w = torch.empty_like(u)
     for name, fn in [("f32", lambda: semax.sem_ax_f32(u, G, D, w)),
                      ("bf16x3", lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=3)),
-                     ("bf16x6", lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=6))]:
+                     ("bf16x6", lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=6)),
+                     ("f16x3", lambda: semax.sem_ax_f16x3(u, G, D, w))]:
         r = rate(fn, dofs, dofs * bytes_per_node(4))
         r["rel_err_vs_f64"] = rel_err_gpu(semax, w, ref)
         r["energy_rel_err"] = energy_rel_gpu(semax, u64, w, ref)
+        r["hbm_frac_of_measured"] = r["hbm_gbs"] / load_peaks().get("hbm_gbs", 6800.0)
         out[f"{name}_N15_E8192"] = r
     # geometric factor recomputed from the vertices: 8 B/node + 96 B/element
     for name, terms in (("bf16x3_geo", 3), ("bf16x6_geo", 6)):
@@ -411,10 +416,19 @@ def variants(semax, reps: int) -> dict:
     r = rate(plan, dofs, dofs * bytes_per_node(8))
     r["tuned"] = {x.N: plan.config(x.N) for x in mix}
     r["l2_flushed"] = flushed(plan, dofs, dofs * bytes_per_node(8))["l2_flushed"]
+    # the FP64 plan is bound by the FP64 pipe like the plain kernel: its
+    # algorithmic flops against the FMA-pipe peak measured in this run
+    mix_flops = sum(x.E * flops_per_element(x.n) for x in mix)
+    r["roofline"] = {"bound": "alu", "algorithmic_flops": mix_flops,
+                     "achieved_tflops": mix_flops / (r["us_per_call"] * 1e-6) / 1e12,
+                     "peak_tflops": fp64_peak_tflops,
+                     "frac": mix_flops / (r["us_per_call"] * 1e-6) / 1e12 / fp64_peak_tflops,
+                     "peak_source": "semax_fma_probe FP64, measured in this run"}
     out["batched_plan_mix"] = r
     per_order = lambda: [semax.sem_ax(x.u, x.G, x.D, w) for x, w in zip(mix, ws)]  # noqa: E731
     r = rate(per_order, dofs, dofs * bytes_per_node(8))
     r["l2_flushed"] = flushed(per_order, dofs, dofs * bytes_per_node(8))["l2_flushed"]
+    r["roofline_frac"] = mix_flops / (r["us_per_call"] * 1e-6) / 1e12 / fp64_peak_tflops
     out["per_order_launches_mix"] = r
     ref_ws = [w.clone() for w in ws]
     planx = semax.Plan([(x.N, x.u, x.G, x.D, w) for x, w in zip(mix, ws)], f64x=True)
@@ -498,7 +512,7 @@ def variants(semax, reps: int) -> dict:
 
 
 def probe_peak(semax, prec: str, iters: int, launches: int, dev_index: int) -> dict:
-    """The FMA pipe's measured throughput (semax_fma_probe: 8 chains of
+    """The FMA pipe's measured throughput (semax_fma_probe: 4 (FP64) or 8 (FP32) chains of
     dependent FMAs per thread, 8 blocks of 256 threads per SM), CUDA events
     around `launches` back-to-back launches, clocks sampled meanwhile."""
     semax.fma_probe(prec, iters=iters)              # warm-up
@@ -516,7 +530,7 @@ def probe_peak(semax, prec: str, iters: int, launches: int, dev_index: int) -> d
     clk = clocks.stop()
     t = a.elapsed_time(b) / 1e3
     return {"tflops": flops / t / 1e12, "seconds": t, "clocks": clk,
-            "how": f"semax_fma_probe {prec}: 8 independent FMA chains x {iters} steps per thread, "
+            "how": f"semax_fma_probe {prec}: {4 if prec == 'f64' else 8} independent FMA chains x {iters} steps per thread, "
                    f"8 x 256 threads per SM, {launches} launches between CUDA events"}
 
 
@@ -660,8 +674,12 @@ def run_ours(args, rank, world):
                 "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
                 "hbm_gbs": nbytes / t_step / 1e9,
                 "hbm_frac_of_measured": nbytes / t_step / 1e9 / hbm_peak,
+                "fp64_instructions_per_node": FP64_INSTR_PER_NODE_N7,
+                "fp64_pipe_frac": FP64_INSTR_PER_NODE_N7 * dofs / t_step / (fp64_peak["tflops"] * 1e12 / 2),
                 "note": "algorithmic flops count 12n+15 per node; the even/odd kernel issues 47 FP64 "
-                        "instructions per node where the plain form needs 57, so frac can exceed 1"}
+                        "instructions per node where the plain form needs 57, so frac can exceed 1; "
+                        "fp64_pipe_frac compares the FP64 instructions it issues per second with the "
+                        "probe's FMA rate"}
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -676,7 +694,7 @@ def run_ours(args, rank, world):
     line["helmholtz_f64"] = helm
     sample = None
     if not args.no_variants:
-        line["variants"], sample = variants(semax, reps=20)
+        line["variants"], sample = variants(semax, reps=20, fp64_peak_tflops=fp64_peak["tflops"])
     if not args.no_cpu_baseline and world == 1:
         host = shard_seed_workload(0, "cpu")
         line["cpu_baseline"], w_oracle = cpu_baseline((host.u.numpy(), host.G.numpy(), host.D.numpy()))
@@ -697,7 +715,8 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-SINGLE_KERNELS = ("f64", "f64tc", "f64tc_prepared", "f64x", "f64tc_n15", "f32_n15", "bf16x3_n15", "bf16x6_n15")
+SINGLE_KERNELS = ("f64", "f64tc", "f64tc_prepared", "f64x", "f64tc_n15", "f32_n15", "bf16x3_n15", "bf16x6_n15",
+                  "f16x3_n15")
 
 
 def run_single_kernel(args):
@@ -709,7 +728,7 @@ def run_single_kernel(args):
     name = args.kernel
     m = si.make_workload(2 if name.endswith("n15") else 1, device="cuda")[0]
     u, G, D = m.u, m.G, m.D
-    if name in ("f32_n15", "bf16x3_n15", "bf16x6_n15"):
+    if name in ("f32_n15", "bf16x3_n15", "bf16x6_n15", "f16x3_n15"):
         u, G, D = u.float(), G.float(), D.float()
     w = torch.empty_like(u)
     gp = semax.f64tc_prepare(G) if name == "f64tc_prepared" else None
@@ -720,7 +739,8 @@ def run_single_kernel(args):
           "f64x": lambda: semax.sem_ax_f64x(u, G, D, w),
           "f32_n15": lambda: semax.sem_ax_f32(u, G, D, w),
           "bf16x3_n15": lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=3),
-          "bf16x6_n15": lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=6)}[name]
+          "bf16x6_n15": lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=6),
+          "f16x3_n15": lambda: semax.sem_ax_f16x3(u, G, D, w)}[name]
     t = time_region(fn, args.steps, args.warmup) / args.steps
     print(json.dumps({"kernel": name, "N": m.N, "E": m.E, "us_per_call": t * 1e6, "gdofs": m.dofs / t / 1e9}),
           flush=True)

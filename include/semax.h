@@ -143,18 +143,23 @@ int sem_ax_f64tc_status(int64_t E, int N, const double *u, const double *G, cons
 
 /* The tensor-core FP64-accurate Ax with the geometric factor prepared once
  * (for repeated applications with the same G, as in an iterative solver).
- * sem_ax_f64tc_prepare splits each node's six G entries into (hi, lo) float
- * pairs after the per-node power-of-two scale, exactly as sem_ax_f64tc does
- * on every call, and keeps each node's largest biased exponent (at N = 15
- * for each half (rr, rs, rt) and (ss, st, tt) of G, as that kernel splits
- * them): per element 6 n^3 float pairs and n^3 (N = 15: 2 n^3) int32,
- * E * 26624 bytes at N = 7 and E * 229376 at N = 15
- * (sem_ax_f64tc_prepare_size), 4 to 8 bytes per node more HBM traffic per
- * call than FP64 G.  sem_ax_f64tc_prepared then computes, bit for bit, what
- * sem_ax_f64tc computes from G, without the split.  N = 7 and N = 15
- * (SEMAX_EUNSUPPORTED_N otherwise).  Gp: device memory, 16-byte aligned,
- * owned by the caller, not overlapping G or w, and prepared for the same E
- * and N (its size is not checked, like G's in sem_ax). */
+ * sem_ax_f64tc_prepare splits G's entries into (hi, lo) float pairs after a
+ * power-of-two scale, as sem_ax_f64tc does on every call: at N = 7 against
+ * one scale per element (kept in a 16-byte tail after the element's
+ * 6 n^3 float pairs: E * 24592 bytes, 64 bytes per node plus 16 per element,
+ * the same HBM traffic per call as FP64 G), at N = 15 against one scale per
+ * node for each half (rr, rs, rt) and (ss, st, tt) of G, as that kernel
+ * splits them, keeping each node's largest biased exponent per half
+ * (E * 229376 bytes, 8 bytes per node more than FP64 G); see
+ * sem_ax_f64tc_prepare_size.  sem_ax_f64tc_prepared then computes, bit for
+ * bit, what sem_ax_f64tc computes from G, without the split (at N = 7
+ * sem_ax_f64tc scales per node: the two agree bit for bit unless an
+ * element's G entries span more than about 2^100, far beyond any mesh, where
+ * the per-element split flushes entries below 2^-126 of the element's
+ * largest to zero).  N = 7 and N = 15 (SEMAX_EUNSUPPORTED_N otherwise).  Gp:
+ * device memory, 16-byte aligned, owned by the caller, not overlapping G or
+ * w, and prepared for the same E and N (its size is not checked, like G's in
+ * sem_ax). */
 int sem_ax_f64tc_prepare_size(int64_t E, int N, size_t *bytes);
 int sem_ax_f64tc_prepare(int64_t E, int N, const double *G, void *Gp, void *stream);
 int sem_ax_f64tc_prepared(int64_t E, int N, const double *u, const void *Gp, const double *D,
@@ -179,6 +184,21 @@ int sem_ax_f32(int64_t E, int N, const float *u, const float *G, const float *D,
  * SEMAX_EUNSUPPORTED_N. */
 int sem_ax_bf16x3(int64_t E, int N, const float *u, const float *G, const float *D,
                   float *w, const float *G_scale, int terms, void *stream);
+
+/* The split tensor-core form with FP16 pieces and three products: each
+ * operand x is scaled by a power of two s (exact) and split as x s = x0 + x1,
+ * x0 = fp16(x s), x1 = fp16(x s - x0), ~22 significant bits against BF16's
+ * 16, and the products x0 y0 + x0 y1 + x1 y0 are accumulated in FP32 on the
+ * tensor cores.  FP16's exponent range is narrow, so the scales are chosen
+ * to put each group's largest magnitude in [1, 2): u and the intermediate wt
+ * per element, D once, wr and ws per plane of the element (their
+ * contractions stay inside a plane); they are undone on the output.  Values
+ * more than 2^24 below their group's largest keep an absolute accuracy of
+ * 2^-25 of it.  The geometric factor multiply is FP32; G_scale as in
+ * sem_ax_f32.  Error against the FP64 definition ~1e-6 of ||w||_inf.
+ * Order N = 15 only (other orders: SEMAX_EUNSUPPORTED_N). */
+int sem_ax_f16x3(int64_t E, int N, const float *u, const float *G, const float *D, float *w,
+                 const float *G_scale, void *stream);
 
 /* The BF16-split tensor-core form with the geometric factor recomputed at
  * every node instead of read: X [E][8][3] holds each element's vertices
@@ -287,7 +307,7 @@ int sem_ax_diag(int64_t E, int N, const double *G, const double *D, double *diag
  * G, D and gs stay bound to the solver; flags = 0 applies A with the FP64
  * kernel of sem_ax, SEMAX_PCG_F64X with that of sem_ax_f64x, SEMAX_PCG_F64TC
  * with that of sem_ax_f64tc (at most one of the two flags; at N = 7 from G
- * prepared once at create, sem_ax_f64tc_prepared, E * 26624 bytes more
+ * prepared once at create, sem_ax_f64tc_prepared, E * 24592 bytes more
  * device memory, the same results bit for bit).  SEMAX_PCG_MIXED
  * (combinable with either) is mixed-precision iterative refinement: each
  * outer step computes the true residual r = b - A x with the FP64-accurate
@@ -358,11 +378,11 @@ int semax_last_cuda_error(void);
 
 /* Diagnostic: the FMA pipe's throughput, the peak that the plain FP64 and
  * FP32 kernels are graded against.  Launches `blocks` blocks of 256 threads,
- * each thread running 8 independent chains of `iters` dependent fused
- * multiply-adds in FP64 (prec = SEMAX_F64) or FP32 (SEMAX_F32) and storing
- * one value per thread in `sink` (device, blocks * 256 elements of that
- * type); *flops (host) receives the floating-point operations the launch
- * performs (an FMA counts 2).  Time it with events on `stream`.  The paper
+ * each thread running 4 (FP64, prec = SEMAX_F64) or 8 (FP32, SEMAX_F32)
+ * independent chains of `iters` (a multiple of 4, else SEMAX_EINVAL)
+ * dependent fused multiply-adds and storing one value per thread in `sink`
+ * (device, blocks * 256 elements of that type); *flops (host) receives the
+ * floating-point operations the launch performs (an FMA counts 2).  Time it with events on `stream`.  The paper
  * has no counterpart; this measures the machine. */
 int semax_fma_probe(int prec, int blocks, int iters, void *sink, double *flops, void *stream);
 

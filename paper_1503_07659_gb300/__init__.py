@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (SemaxError, semax_group, check, SEMAX_OK, SEMAX_ETIMEOUT, SEMAX_F32, SEMAX_F64, SEMAX_PLAN_F64X, SEMAX_PLAN_F64TC,
                    SEMAX_PCG_F64X, SEMAX_PCG_F64TC, SEMAX_PCG_MIXED)
 
-__all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f64tc_prepared", "f64tc_prepare", "set_wait_polls", "fma_probe", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_bf16x3_geo", "sem_ax_batched", "Plan", "reduce",
+__all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f64tc_prepared", "f64tc_prepare", "set_wait_polls", "fma_probe", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_f16x3", "sem_ax_bf16x3_geo", "sem_ax_batched", "Plan", "reduce",
            "sem_ax_from_host", "SemaxError", "library_path"]
 
 
@@ -107,7 +107,7 @@ def set_wait_polls(polls: int) -> None:
 
 def f64tc_prepare(G: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """The prepared geometric factor of sem_ax_f64tc_prepared (order 7): a
-    uint8 device tensor of E * 26624 bytes."""
+    uint8 device tensor of E * 24592 bytes (E * 229376 at order 15)."""
     if G.dim() != 5 or G.shape[1] != 6:
         raise ValueError("f64tc_prepare: G must be [E, 6, n, n, n]")
     E, N = G.shape[0], G.shape[2] - 1
@@ -150,6 +150,16 @@ def sem_ax_bf16x3(u, G, D, w=None, G_scale=None, terms: int = 3, stream=None) ->
     w = _out(w, u)
     check(_lib.lib().sem_ax_bf16x3(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _ptr(G_scale),
                                    int(terms), _stream(stream)), "sem_ax_bf16x3")
+    return w
+
+
+def sem_ax_f16x3(u, G, D, w=None, G_scale=None, stream=None) -> torch.Tensor:
+    """FP32 storage; contractions on tensor cores with FP16 operand splits (3 products) after
+    power-of-two scaling of each operand group."""
+    E, N = _dims(u, D)
+    w = _out(w, u)
+    check(_lib.lib().sem_ax_f16x3(E, N, _ptr(u), _ptr(G), _ptr(D), _ptr(w), _ptr(G_scale), _stream(stream)),
+          "sem_ax_f16x3")
     return w
 
 

@@ -25,7 +25,18 @@
 //          movmatrix transpose; w_rs = wr D + D^T ws -> W (same plane);
 //   pass T' warp w owns rows j again: w_t = D^T (x) I (x) I wt on tensor cores,
 //          w = (w_rs + w_t) * s_e, stored to global memory.
+//
+// FP16 pieces (F16 = true, 3 products): FP16 keeps 11 significant bits per
+// piece against BF16's 8, so two pieces hold ~22 bits, but its exponent range
+// is narrow.  Every operand is therefore scaled by a power of two first (an
+// exact operation): u and wt per element, D once, and wr, ws per plane (their
+// contractions stay inside the plane), each so that its largest magnitude
+// lies in [1, 2); the scales are undone on the outputs.  Values more than
+// 2^-24 below their scale's maximum keep an absolute accuracy of 2^-25 of
+// it (FP16 subnormals).  wt is kept raw in FP32 until every plane's maximum
+// is known and split when pass T' loads it.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "mma_sync.cuh"
@@ -38,6 +49,10 @@ constexpr int kThreads = 256;
 constexpr int kPieceBytes = 4096 * 2;      // one BF16 copy of an element
 constexpr int kWRow = 24, kWPlane = 392;   // padded FP32 plane (words)
 constexpr int kWBytes = kN * kWPlane * 4;
+constexpr int kRawPlane = 260;             // FP16 pieces: raw FP32 wt [l][j][i], padded plane (words)
+// bytes of the wt region: its pieces, or raw FP32 wt for the FP16 pieces
+template <int NP, bool F16>
+constexpr int wt_bytes() { return F16 ? kN * kRawPlane * 4 : NP * kPieceBytes; }
 
 // byte offset of BF16 element (k, j, i) inside one piece buffer
 __device__ __forceinline__ uint32_t swz(int k, int j, int i) {
@@ -54,29 +69,49 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return mma::smem_
 __device__ __forceinline__ void ldsm_x4(uint32_t a, uint32_t (&r)[4]) { mma::ldsm_x4(a, r[0], r[1], r[2], r[3]); }
 __device__ __forceinline__ void ldsm_x4_t(uint32_t a, uint32_t (&r)[4]) { mma::ldsm_x4_t(a, r[0], r[1], r[2], r[3]); }
 using mma::movm_t;
+template <bool F16>
 __device__ __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    mma::bf16_16816(c, a[0], a[1], a[2], a[3], b0, b1);
+    if (F16)
+        mma::f16_16816(c, a[0], a[1], a[2], a[3], b0, b1);
+    else
+        mma::bf16_16816(c, a[0], a[1], a[2], a[3], b0, b1);
 }
 
 __device__ __forceinline__ uint32_t pack(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t *>(&h); }
+__device__ __forceinline__ uint32_t pack(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
 
-// Split the pair (x, y) into NP BF16 pieces, packed (x in the low half).
-template <int NP>
+// Split the pair (x, y) into NP BF16 (F16: FP16) pieces, packed (x in the low half).
+template <int NP, bool F16 = false>
 __device__ __forceinline__ void split2(float x, float y, uint32_t (&out)[NP]) {
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
-        out[p] = pack(h);
-        x -= __low2float(h);
-        y -= __high2float(h);
+        if (F16) {
+            const __half2 h = __floats2half2_rn(x, y);
+            out[p] = pack(h);
+            x -= __low2float(h);
+            y -= __high2float(h);
+        } else {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+            out[p] = pack(h);
+            x -= __low2float(h);
+            y -= __high2float(h);
+        }
     }
 }
 
+// 2^-e for the largest magnitude m of a group (as float bits), e its
+// exponent, so that the group scaled by it lies below 2 in magnitude:
+// clamped to [2^-126, 2^127] (a zero group keeps any scale).
+__device__ __forceinline__ float inv_pow2_of(unsigned mbits) {
+    const int eb = (int)((mbits >> 23) & 0xffu);
+    return __uint_as_float((unsigned)min(max(254 - eb, 1), 254) << 23);
+}
+
 // piece p of a scalar (for the constant D fragments)
-template <int NP>
+template <int NP, bool F16 = false>
 __device__ __forceinline__ uint32_t piece_pair(float x, float y, int p) {
     uint32_t o[NP];
-    split2<NP>(x, y, o);
+    split2<NP, F16>(x, y, o);
     uint32_t r = o[0];
 #pragma unroll
     for (int q = 1; q < NP; ++q)
@@ -85,7 +120,7 @@ __device__ __forceinline__ uint32_t piece_pair(float x, float y, int p) {
 }
 
 // acc += sum over piece pairs (pa, pb), pa + pb <= NP - 1, smallest first
-template <int NP>
+template <int NP, bool F16>
 __device__ __forceinline__ void mma_split(float (&c)[4], const uint32_t (&a)[NP][4],
                                           const uint32_t (&b)[NP][2]) {
 #pragma unroll
@@ -93,7 +128,7 @@ __device__ __forceinline__ void mma_split(float (&c)[4], const uint32_t (&a)[NP]
 #pragma unroll
         for (int pa = s; pa >= 0; --pa) {
             const int pb = s - pa;
-            mma(c, a[pa], b[pb][0], b[pb][1]);
+            mma<F16>(c, a[pa], b[pb][0], b[pb][1]);
         }
 }
 
@@ -105,29 +140,39 @@ struct DFrag {
     uint32_t BDt[NP][2][2];  // B(l, i) = D[l][i], per n-tile
 };
 
-template <int NP>
-__device__ __forceinline__ void load_dfrag(const float *__restrict__ D, DFrag<NP> &f) {
+// The D fragments, of D * sD (sD = 1 for BF16; for FP16 the power of two
+// that puts max |D sD| in [1, 2), returned).
+template <int NP, bool F16>
+__device__ __forceinline__ float load_dfrag(const float *__restrict__ D, DFrag<NP> &f) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    auto d = [&](int r, int c) { return D[r * kN + c]; };
+    float sD = 1.0f;
+    if (F16) {
+        unsigned m = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) m = max(m, __float_as_uint(D[lane + 32 * q]) & 0x7fffffffu);
+        sD = inv_pow2_of(__reduce_max_sync(0xffffffffu, m));
+    }
+    auto d = [&](int r, int c) { return D[r * kN + c] * sD; };
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        f.AD[p][0] = piece_pair<NP>(d(g, 2 * t), d(g, 2 * t + 1), p);
-        f.AD[p][1] = piece_pair<NP>(d(g + 8, 2 * t), d(g + 8, 2 * t + 1), p);
-        f.AD[p][2] = piece_pair<NP>(d(g, 2 * t + 8), d(g, 2 * t + 9), p);
-        f.AD[p][3] = piece_pair<NP>(d(g + 8, 2 * t + 8), d(g + 8, 2 * t + 9), p);
-        f.ADt[p][0] = piece_pair<NP>(d(2 * t, g), d(2 * t + 1, g), p);
-        f.ADt[p][1] = piece_pair<NP>(d(2 * t, g + 8), d(2 * t + 1, g + 8), p);
-        f.ADt[p][2] = piece_pair<NP>(d(2 * t + 8, g), d(2 * t + 9, g), p);
-        f.ADt[p][3] = piece_pair<NP>(d(2 * t + 8, g + 8), d(2 * t + 9, g + 8), p);
+        f.AD[p][0] = piece_pair<NP, F16>(d(g, 2 * t), d(g, 2 * t + 1), p);
+        f.AD[p][1] = piece_pair<NP, F16>(d(g + 8, 2 * t), d(g + 8, 2 * t + 1), p);
+        f.AD[p][2] = piece_pair<NP, F16>(d(g, 2 * t + 8), d(g, 2 * t + 9), p);
+        f.AD[p][3] = piece_pair<NP, F16>(d(g + 8, 2 * t + 8), d(g + 8, 2 * t + 9), p);
+        f.ADt[p][0] = piece_pair<NP, F16>(d(2 * t, g), d(2 * t + 1, g), p);
+        f.ADt[p][1] = piece_pair<NP, F16>(d(2 * t, g + 8), d(2 * t + 1, g + 8), p);
+        f.ADt[p][2] = piece_pair<NP, F16>(d(2 * t + 8, g), d(2 * t + 9, g), p);
+        f.ADt[p][3] = piece_pair<NP, F16>(d(2 * t + 8, g + 8), d(2 * t + 9, g + 8), p);
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt) {
             const int i = g + 8 * nt;
-            f.BD[p][nt][0] = piece_pair<NP>(d(i, 2 * t), d(i, 2 * t + 1), p);
-            f.BD[p][nt][1] = piece_pair<NP>(d(i, 2 * t + 8), d(i, 2 * t + 9), p);
-            f.BDt[p][nt][0] = piece_pair<NP>(d(2 * t, i), d(2 * t + 1, i), p);
-            f.BDt[p][nt][1] = piece_pair<NP>(d(2 * t + 8, i), d(2 * t + 9, i), p);
+            f.BD[p][nt][0] = piece_pair<NP, F16>(d(i, 2 * t), d(i, 2 * t + 1), p);
+            f.BD[p][nt][1] = piece_pair<NP, F16>(d(i, 2 * t + 8), d(i, 2 * t + 9), p);
+            f.BDt[p][nt][0] = piece_pair<NP, F16>(d(2 * t, i), d(2 * t + 1, i), p);
+            f.BDt[p][nt][1] = piece_pair<NP, F16>(d(2 * t + 8, i), d(2 * t + 9, i), p);
         }
     }
+    return sD;
 }
 
 // G = wq adj(J) adj(J)^T / det(J), components (rr, rs, rt, ss, st, tt), for
@@ -155,16 +200,18 @@ __device__ __forceinline__ void geo_from_jacobian(const float (&J)[3][3], float 
 // GEO = true:  G is the element vertices [E][8][3] (FP32) and xq = (GLL nodes
 // [16], GLL weights [16]); the factor is recomputed at every node from the
 // trilinear map (96 bytes per element read instead of 96 KB).
-template <int NP, bool GEO>
+template <int NP, bool GEO, bool F16>
 __global__ void __launch_bounds__(kThreads, 2)
 ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__ G,
                const float *__restrict__ D, float *__restrict__ w, const float *__restrict__ scale,
                const float *__restrict__ xq) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *upc = smem;                                // NP pieces of u
-    unsigned char *wpc = smem + NP * kPieceBytes;             // NP pieces of wt
-    float *W = reinterpret_cast<float *>(smem + 2 * NP * kPieceBytes);
+    unsigned char *wpc = smem + NP * kPieceBytes;             // NP pieces of wt (F16: raw FP32 wt)
+    float *wraw = reinterpret_cast<float *>(wpc);
+    float *W = reinterpret_cast<float *>(smem + NP * kPieceBytes + wt_bytes<NP, F16>());
     float *sgeo = W + kWBytes / 4;                            // GEO: map coefficients [3][8], xi [16], wq [16]
+    unsigned *smax = reinterpret_cast<unsigned *>(W + kWBytes / 4);   // F16: per-warp maxima of |u| and |wt|
     const uint32_t upc_s = smem_addr(upc), wpc_s = smem_addr(wpc);
     if (GEO && threadIdx.x < 32) sgeo[24 + threadIdx.x] = xq[threadIdx.x];
 
@@ -173,7 +220,7 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
     const int lm = lane >> 3, lr = lane & 7;  // ldmatrix: matrix id, row id
 
     DFrag<NP> f;
-    load_dfrag<NP>(D, f);
+    const float sD = load_dfrag<NP, F16>(D, f);
 
     // u of the CTA's first element, raw FP32, into the u-piece region: each
     // thread copies (and later reads back) its own four 16-byte chunks
@@ -210,15 +257,31 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
         float4 vr[4];
 #pragma unroll
         for (int it = 0; it < 4; ++it) vr[it] = reinterpret_cast<const float4 *>(upc)[tid + it * kThreads];
+        if (F16) {   // the element's largest |u|, per warp
+            unsigned m = 0;
+#pragma unroll
+            for (int it = 0; it < 4; ++it)
+                m = max(max(m, max(__float_as_uint(vr[it].x), __float_as_uint(vr[it].y)) & 0x7fffffffu),
+                        max(__float_as_uint(vr[it].z), __float_as_uint(vr[it].w)) & 0x7fffffffu);
+            m = __reduce_max_sync(0xffffffffu, m);
+            if (lane == 0) smax[warp] = m;
+        }
         __syncthreads();   // every thread has its raw values before pieces overwrite the region
+        float su = 1.0f;   // F16: u's power-of-two scale
+        if (F16) {
+            unsigned m = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) m = max(m, smax[q]);
+            su = inv_pow2_of(m);
+        }
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
             const int q = tid + it * kThreads;  // float4 index, 0..1023
             const float4 v = vr[it];
             const int k = q >> 6, j = (q >> 2) & 15, i = (q & 3) << 2;
             uint32_t lo[NP], hi[NP];
-            split2<NP>(v.x, v.y, lo);
-            split2<NP>(v.z, v.w, hi);
+            split2<NP, F16>(v.x * su, v.y * su, lo);
+            split2<NP, F16>(v.z * su, v.w * su, hi);
             const uint32_t off = swz(k, j, i);
 #pragma unroll
             for (int p = 0; p < NP; ++p)
@@ -240,7 +303,7 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
 #pragma unroll
                 for (int p = 0; p < NP; ++p) { bb[p][0] = b[p][2 * nt]; bb[p][1] = b[p][2 * nt + 1]; }
                 float c[4] = {0.f, 0.f, 0.f, 0.f};
-                mma_split<NP>(c, f.AD, bb);
+                mma_split<NP, F16>(c, f.AD, bb);
                 const int i = 8 * nt + 2 * t;
                 *reinterpret_cast<float2 *>(W + widx(g, j, i)) = make_float2(c[0], c[1]);
                 *reinterpret_cast<float2 *>(W + widx(g + 8, j, i)) = make_float2(c[2], c[3]);
@@ -249,6 +312,7 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
         __syncthreads();
 
         // ---- pass P: planes k = 2*warp, 2*warp+1
+        unsigned tmax = 0;   // F16: the warp's largest |wt| (float bits)
 #pragma unroll 1
         for (int kk = 0; kk < 2; ++kk) {
             const int k = 2 * warp + kk;
@@ -316,6 +380,8 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
             float wacc[2][4];
             uint32_t awr[NP][4];   // wr as A operand (C -> A reuse)
             uint32_t bws[NP][2][2];
+            float wrv[2][4], wsv[2][4];   // F16: wr, ws of the plane until its scale is known
+            unsigned pmax = 0;
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
                 float ur[4] = {0.f, 0.f, 0.f, 0.f}, us[4] = {0.f, 0.f, 0.f, 0.f};
@@ -331,8 +397,8 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
 #pragma unroll
                 for (int s = NP - 1; s >= 0; --s)
 #pragma unroll
-                    for (int pa = s; pa >= 0; --pa) mma(ur, au[s - pa], bd[pa][0], bd[pa][1]);
-                mma_split<NP>(us, f.AD, bb);
+                    for (int pa = s; pa >= 0; --pa) mma<F16>(ur, au[s - pa], bd[pa][0], bd[pa][1]);
+                mma_split<NP, F16>(us, f.AD, bb);
                 const int i = 8 * nt + 2 * t;
                 float wr[4], ws[4], wt[4];
 #pragma unroll
@@ -353,6 +419,20 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
                         ws[q] = __fmaf_rn(gst, tt, __fmaf_rn(gss, s, grs * r));
                         wt[q] = __fmaf_rn(gtt, tt, __fmaf_rn(gst, s, grt * r));
                     }
+                }
+                if (F16) {
+                    // wt raw (FP32) -> shared, split in pass T' once every plane's
+                    // maximum is known; wr and ws wait for the plane's scale
+                    *reinterpret_cast<float2 *>(wraw + k * kRawPlane + g * kN + i) = make_float2(wt[0], wt[1]);
+                    *reinterpret_cast<float2 *>(wraw + k * kRawPlane + (g + 8) * kN + i) = make_float2(wt[2], wt[3]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        tmax = max(tmax, __float_as_uint(wt[q]) & 0x7fffffffu);
+                        pmax = max(pmax, max(__float_as_uint(wr[q]), __float_as_uint(ws[q])) & 0x7fffffffu);
+                        wrv[nt][q] = wr[q];
+                        wsv[nt][q] = ws[q];
+                    }
+                    continue;
                 }
                 // wt pieces -> shared (for pass T')
                 uint32_t p0[NP], p1[NP];
@@ -380,6 +460,29 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
                     bws[p][nt][1] = movm_t(p1[p]);
                 }
             }
+            float inv_sk = 1.0f;   // F16: undoes the plane's scale on w_rs
+            if (F16) {
+                const float sk = inv_pow2_of(__reduce_max_sync(0xffffffffu, pmax));
+                inv_sk = __frcp_rn(sk);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    uint32_t p0[NP], p1[NP];
+                    split2<NP, true>(wrv[nt][0] * sk, wrv[nt][1] * sk, p0);
+                    split2<NP, true>(wrv[nt][2] * sk, wrv[nt][3] * sk, p1);
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        awr[p][2 * nt] = p0[p];
+                        awr[p][2 * nt + 1] = p1[p];
+                    }
+                    split2<NP, true>(wsv[nt][0] * sk, wsv[nt][1] * sk, p0);
+                    split2<NP, true>(wsv[nt][2] * sk, wsv[nt][3] * sk, p1);
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        bws[p][nt][0] = movm_t(p0[p]);
+                        bws[p][nt][1] = movm_t(p1[p]);
+                    }
+                }
+            }
             // w_rs = wr D + D^T ws
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
@@ -392,38 +495,67 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
                     bw[p][0] = bws[p][nt][0];
                     bw[p][1] = bws[p][nt][1];
                 }
-                mma_split<NP>(wacc[nt], awr, bdt);
-                mma_split<NP>(wacc[nt], f.ADt, bw);
+                mma_split<NP, F16>(wacc[nt], awr, bdt);
+                mma_split<NP, F16>(wacc[nt], f.ADt, bw);
                 const int i = 8 * nt + 2 * t;
-                *reinterpret_cast<float2 *>(W + widx(k, g, i)) = make_float2(wacc[nt][0], wacc[nt][1]);
-                *reinterpret_cast<float2 *>(W + widx(k, g + 8, i)) = make_float2(wacc[nt][2], wacc[nt][3]);
+                *reinterpret_cast<float2 *>(W + widx(k, g, i)) = make_float2(wacc[nt][0] * inv_sk, wacc[nt][1] * inv_sk);
+                *reinterpret_cast<float2 *>(W + widx(k, g + 8, i)) = make_float2(wacc[nt][2] * inv_sk, wacc[nt][3] * inv_sk);
             }
+        }
+        if (F16) {
+            tmax = __reduce_max_sync(0xffffffffu, tmax);
+            if (lane == 0) smax[8 + warp] = tmax;
         }
         __syncthreads();
         if (e + gridDim.x < E) prefetch_u(e + gridDim.x);   // the u pieces are dead from here on
 
         // ---- pass T': w += sum_l D[l][k] wt[l][j][i]; store
-        const float sc = scale ? scale[e] : 1.f;
+        float sc = scale ? scale[e] : 1.f;
+        float st = 1.0f, inv_st = 1.0f;   // F16: wt's scale, and its inverse
+        if (F16) {
+            unsigned m = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) m = max(m, smax[8 + q]);
+            st = inv_pow2_of(m);
+            inv_st = __frcp_rn(st);
+            sc = sc * __frcp_rn(su * sD * sD);   // W and the t-part are in units of su sD^2
+        }
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
             const int j = 2 * warp + jj;
             uint32_t b[NP][4];
-            const uint32_t a_off = swz(lr + 8 * (lm & 1), j, 8 * (lm >> 1));
+            if (F16) {   // B fragments (rows l = 2t, 2t+1 (+8), column i = g (+8)) split from the raw wt
 #pragma unroll
-            for (int p = 0; p < NP; ++p) ldsm_x4_t(wpc_s + p * kPieceBytes + a_off, b[p]);
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int kh = 0; kh < 2; ++kh) {
+                        const int l = 2 * t + 8 * kh, i = 8 * nt + g;
+                        uint32_t pc[NP];
+                        split2<NP, true>(wraw[l * kRawPlane + j * kN + i] * st, wraw[(l + 1) * kRawPlane + j * kN + i] * st,
+                                         pc);
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) b[p][2 * nt + kh] = pc[p];
+                    }
+            } else {
+                const uint32_t a_off = swz(lr + 8 * (lm & 1), j, 8 * (lm >> 1));
+#pragma unroll
+                for (int p = 0; p < NP; ++p) ldsm_x4_t(wpc_s + p * kPieceBytes + a_off, b[p]);
+            }
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
                 uint32_t bb[NP][2];
 #pragma unroll
                 for (int p = 0; p < NP; ++p) { bb[p][0] = b[p][2 * nt]; bb[p][1] = b[p][2 * nt + 1]; }
                 float c[4] = {0.f, 0.f, 0.f, 0.f};
-                mma_split<NP>(c, f.ADt, bb);
+                mma_split<NP, F16>(c, f.ADt, bb);
                 const int i = 8 * nt + 2 * t;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int k = g + 8 * h;
                     const float2 prev = *reinterpret_cast<const float2 *>(W + widx(k, j, i));
-                    float2 out = make_float2((prev.x + c[2 * h]) * sc, (prev.y + c[2 * h + 1]) * sc);
+                    float2 out = F16 ? make_float2(__fmaf_rn(c[2 * h], inv_st, prev.x) * sc,
+                                                   __fmaf_rn(c[2 * h + 1], inv_st, prev.y) * sc)
+                                     : make_float2((prev.x + c[2 * h]) * sc, (prev.y + c[2 * h + 1]) * sc);
                     *reinterpret_cast<float2 *>(we + k * 256 + j * 16 + i) = out;
                 }
             }
@@ -432,11 +564,12 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
     }
 }
 
-template <int NP, bool GEO>
+template <int NP, bool GEO, bool F16 = false>
 static int launch(int64_t E, const float *u, const float *G, const float *D, float *w, const float *scale,
                   const float *xq, cudaStream_t s) {
-    const size_t smem = 2 * NP * kPieceBytes + kWBytes + (GEO ? 64 * sizeof(float) : 0);
-    auto kern = ax_bf16_kernel<NP, GEO>;
+    const size_t smem = NP * kPieceBytes + wt_bytes<NP, F16>() + kWBytes + (GEO ? 64 * sizeof(float) : 0) +
+                        (F16 ? 16 * sizeof(unsigned) : 0);
+    auto kern = ax_bf16_kernel<NP, GEO, F16>;
     int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (st != SEMAX_OK) return st;
     int per_sm = 0;
@@ -464,6 +597,16 @@ extern "C" int sem_ax_bf16x3(int64_t E, int N, const float *u, const float *G, c
         return SEMAX_EALIAS;
     if (terms == 3) return tc::launch<2, false>(E, u, G, D, w, G_scale, nullptr, (cudaStream_t)stream);
     return tc::launch<3, false>(E, u, G, D, w, G_scale, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int sem_ax_f16x3(int64_t E, int N, const float *u, const float *G, const float *D, float *w,
+                            const float *G_scale, void *stream) {
+    int st = check_args(E, N, u, G, D, w);
+    if (st != SEMAX_OK || E == 0) return st;
+    if (N != 15) return SEMAX_EUNSUPPORTED_N;
+    if (G_scale && overlaps(w, (size_t)E * 4096 * sizeof(float), G_scale, (size_t)E * sizeof(float)))
+        return SEMAX_EALIAS;
+    return tc::launch<2, false, true>(E, u, G, D, w, G_scale, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" int sem_ax_bf16x3_geo(int64_t E, int N, const float *u, const float *X, const float *xi_wq,

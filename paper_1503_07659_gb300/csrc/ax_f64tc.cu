@@ -16,19 +16,25 @@
 // weigh less than 2^-48 of the element's scale.  The five level sums of an
 // output are combined in double-float (an unevaluated sum of two floats).
 //
-// Per element (one CTA of 4 warps; warp w owns the planes k = 2w, 2w+1 for
-// every pointwise step, in the layout of the m16n8 accumulator of the
-// r-direction tile; u and G of the CTA's next element are fetched by TMA
-// bulk copies into shared memory while the current one finishes):
+// Per element (one CTA of 4 warps, five CTAs per SM with G prepared and four
+// with FP64 G; warp w owns the planes k = 2w, 2w+1 for every pointwise step,
+// in the layout of the m16n8 accumulator of the r-direction tile; u and G of
+// the CTA's next element are fetched by TMA bulk copies into shared memory
+// while the current one finishes):
 //   A  u (FP64) -> per-element scale -> 5 FP16 digit planes in shared memory;
 //   B  ur, us, ut on tensor cores (B operand: the digits of D^T, held in
 //      registers for the CTA's lifetime); ur stays in registers, us and ut
-//      go through two swizzled double-float buffers;
-//   C  y = G [ur us ut] in double-float with G split hi + lo by bit
-//      operations after a per-node power-of-two scale; per-element scale of
-//      y; 3 x 5 digit planes;
-//   D  w_r, w_s, w_t on tensor cores (B operand: the digits of D);
-//   E  w = (w_r + w_s + w_t) * 2^(scales) in FP64, stored.
+//      go through two swizzled double-float buffers (the r- and
+//      s-contractions read only the warp's own planes and start before the
+//      CTA barrier that the t-contraction needs);
+//   C  y = G [ur us ut] in double-float, G split hi + lo by bit operations
+//      after a power-of-two scale (per node from FP64 G, per element in the
+//      prepared form); per-element scale of y; 5 digits of each component:
+//      those of y_r stay in registers as A fragments, those of y_s too after
+//      a movmatrix transpose, those of y_t go to shared memory;
+//   D  w_r + w_s on tensor cores into one set of level accumulators (the
+//      s-part through a block-diagonal A, below), w_t from the shared digits;
+//   E  w = (w_rs + w_t) * 2^(scales) in FP64, stored.
 // The only FP64 instruction is the final add of each node.
 // Inputs with Inf or NaN make their element's output NaN.
 #include "ax_f64tc.cuh"
@@ -39,12 +45,12 @@ namespace oz {
 constexpr int kThreads = 128;                // one element per CTA pass
 constexpr int kPlane = 128;                  // bytes per 8 x 8 FP16 plane (rows XOR-swizzled)
 constexpr int kSlice = 8 * kPlane;           // one digit of an 8^3 operand
-constexpr int kDigBytes = 3 * kS10 * kSlice; // digits of wr, ws, wt (u reuses the first five)
+constexpr int kDigBytes = kS10 * kSlice;     // digits of u, later of wt (wr and ws stay in registers)
 constexpr int kBufBytes = 512 * 8;           // one double-float per node
 constexpr int kGBytes = 6 * 512 * 8;         // one element's G (FP64), staged
 constexpr int kUBytes = 512 * 8;             // one element's u (FP64), staged
-constexpr int kEgBytes = 512 * 4;            // prepared form: each node's largest G exponent, after G
-constexpr int kPreBytes = kGBytes + kEgBytes; // one element of the prepared geometric factor (26 KB)
+constexpr int kTailBytes = 16;               // prepared form: the element's largest G exponent (and padding)
+constexpr int kPreBytes = kGBytes + kTailBytes;   // one element of the prepared geometric factor
 // + mbarrier in the last 8 of the reduction slots
 template <bool PRE>
 constexpr size_t smem_bytes() { return kDigBytes + 2 * kBufBytes + (PRE ? kPreBytes : kGBytes) + kUBytes + 16 * sizeof(int); }
@@ -99,6 +105,27 @@ __device__ __forceinline__ void contract(uint32_t base, int warp, int lane, cons
 #undef OZ_K16
 }
 
+// The same with the A fragments in registers: a[q][h] holds digit q of the
+// rows of plane 2w + h (DIR 0: rows j, columns i; DIR 1: rows i, columns j).
+__device__ __forceinline__ void contract_regs(const uint32_t (&a)[kS10][2], const uint32_t (&Bf)[kS10],
+                                              float (&acc)[kS10][4]) {
+#pragma unroll
+    for (int l = 0; l < kS10; ++l) acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = 0.0f;
+#define OZ_K8(L, p, q) mma::f16_1688(acc[L], a[q][0], a[q][1], Bf[p])
+#define OZ_K16(L, p1, q1, p2, q2) mma::f16_16816(acc[L], a[q1][0], a[q1][1], a[q2][0], a[q2][1], Bf[p1], Bf[p2])
+    OZ_K8(0, 0, 0);
+    OZ_K16(1, 0, 1, 1, 0);
+    OZ_K16(2, 0, 2, 1, 1);
+    OZ_K16(3, 0, 3, 1, 2);
+    OZ_K16(4, 0, 4, 1, 3);
+    OZ_K8(2, 2, 0);
+    OZ_K16(3, 2, 1, 3, 0);
+    OZ_K16(4, 2, 2, 3, 1);
+    OZ_K8(4, 4, 0);
+#undef OZ_K8
+#undef OZ_K16
+}
+
 // Double-float buffers of the s- and t-direction results (one float2 per
 // node), XOR-swizzled so that the accumulator-layout writes and the
 // pointwise reads are both free of bank conflicts:
@@ -128,10 +155,11 @@ __device__ __forceinline__ void store_tile(float2 *buf, const float (&acc)[kS10]
 __device__ __forceinline__ int max4(const int *p) { return max(max(p[0], p[1]), max(p[2], p[3])); }
 
 // PRE = false: G is FP64 [E][6][512]; PRE = true: G points at the prepared
-// form, per element 6 x 512 (hi, lo) float pairs (G split as below) and 512
-// ints (each node's largest biased exponent of G).
+// form, per element 6 x 512 (hi, lo) float pairs (G split against the
+// element's scale) and a 16-byte tail whose first int is the element's
+// largest biased exponent of G.
 template <bool PRE>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, PRE ? 5 : 4)
 ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
                 const double *__restrict__ D, double *__restrict__ w, int *__restrict__ status, int polls) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -140,7 +168,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
     float2 *bt = bs + 512;                                         // t-direction results
     const double2 *gst = reinterpret_cast<const double2 *>(bt + 512);   // staged G [6][256 node pairs]
     const float4 *gpre = reinterpret_cast<const float4 *>(gst);         // prepared: [6][256 node pairs] (hi, lo) x 2
-    const int2 *egst = reinterpret_cast<const int2 *>(reinterpret_cast<const unsigned char *>(gst) + kGBytes);
+    const int *egst = reinterpret_cast<const int *>(reinterpret_cast<const unsigned char *>(gst) + kGBytes);
     const double2 *ust = reinterpret_cast<const double2 *>(reinterpret_cast<const unsigned char *>(gst) +
                                                            (PRE ? kPreBytes : kGBytes));   // staged u [256 node pairs]
     int *sred = reinterpret_cast<int *>(smem + kDigBytes + 2 * kBufBytes + (PRE ? kPreBytes : kGBytes) + kUBytes);   // [0, 4) u, [4, 8) y exponents
@@ -222,7 +250,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
 #pragma unroll
             for (int q = 0; q < kS10; ++q) *reinterpret_cast<uint32_t *>(p + q * kSlice) = pack_f16(d0[q], d1[q]);
         }
-        __syncthreads();
+        __syncwarp();   // the r- and s-contractions read only this warp's planes
 
         // ---- B: gradient on tensor cores
         df vr[4];
@@ -237,6 +265,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
             contract<1>(dig_s, warp, lane, fg, acc);
             store_tile<1>(bs, acc, warp, g, t);
         }
+        __syncthreads();   // the t-contraction reads every warp's planes
         {
             float acc[kS10][4];
             contract<2>(dig_s, warp, lane, fg, acc);
@@ -245,19 +274,21 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         __syncthreads();
 
         // ---- C: y = G grad in double-float; per-element scale; digits
+        // G is split against a power-of-two scale 2^sh: per node for FP64 G,
+        // per element in the prepared form (the same digits unless the
+        // element's G entries span more than ~2^100)
         acc2 y[4][3];
         int shn[4];
         int tmax = INT_MIN;
+        const int egE = PRE ? egst[0] : 0;   // prepared: the element's largest biased G exponent
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = 2 * warp + h, nb = k * 64 + g * 8 + 2 * t;
             double2 gv[6];
             float4 gp[6];
-            int2 eg2;
             if (PRE) {
 #pragma unroll
                 for (int a = 0; a < 6; ++a) gp[a] = gpre[a * 256 + (nb >> 1)];
-                eg2 = egst[nb >> 1];
             } else {
 #pragma unroll
                 for (int a = 0; a < 6; ++a) gv[a] = gst[a * 256 + (nb >> 1)];
@@ -270,11 +301,10 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 const df Vs{sv.x, sv.y};
                 const df Vt = c ? df{tv.z, tv.w} : df{tv.x, tv.y};
                 df Gh[6];
-                int eg;   // largest biased exponent of the node's G
+                int sh = 0;
                 if (PRE) {
 #pragma unroll
                     for (int a = 0; a < 6; ++a) Gh[a] = c ? df{gp[a].z, gp[a].w} : df{gp[a].x, gp[a].y};
-                    eg = c ? eg2.y : eg2.x;
                 } else {
                     double Gc[6];
                     unsigned hws[6], hmax = 0;
@@ -284,13 +314,13 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                         hws[a] = habs(Gc[a]);
                         hmax = max(hmax, hws[a]);
                     }
-                    eg = (int)(hmax >> 20);
-                    const int sh = max(eg, 1) - 1023;
+                    const int eg = (int)(hmax >> 20);   // largest biased exponent of the node's G
+                    sh = max(eg, 1) - 1023;             // G * 2^-sh has magnitude < 2
                     const unsigned K = (unsigned)(896 + sh) << 23;
 #pragma unroll
                     for (int a = 0; a < 6; ++a) Gh[a] = split_g(Gc[a], hws[a], K, (unsigned)max(897 + sh, 1) << 20);
+                    if (eg == 0x7ff) tmax = kBadExp;
                 }
-                const int sh = max(eg, 1) - 1023;   // G * 2^-sh has magnitude < 2
                 y[q][0] = dot3(Gh[0], Gh[1], Gh[2], vr[q], Vs, Vt);
                 y[q][1] = dot3(Gh[1], Gh[3], Gh[4], vr[q], Vs, Vt);
                 y[q][2] = dot3(Gh[2], Gh[4], Gh[5], vr[q], Vs, Vt);
@@ -302,7 +332,6 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 const float ym = fmaxf(fabsf(y[q][0].s), fmaxf(fabsf(y[q][1].s), fabsf(y[q][2].s)));
                 const int ev = (int)(__float_as_uint(ym) >> 23);
                 if (ev) tmax = max(tmax, ev + sh);
-                if (eg == 0x7ff) tmax = kBadExp;
             }
         }
         tmax = __reduce_max_sync(0xffffffffu, tmax);
@@ -310,8 +339,13 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
         __syncthreads();
         if (tid == 0 && e + gridDim.x < E) prefetch(e + gridDim.x);   // every thread has read this element's G
         const int eWraw = max4(sred + 4);
-        const bool bad = eU == 0x7ff || eD == 0x7ff || eWraw >= kBadExp;
+        const bool bad = eU == 0x7ff || eD == 0x7ff || eWraw >= kBadExp || egE == 0x7ff;
         const int eW = eWraw == INT_MIN ? 0 : min(eWraw, kBadExp);   // y == 0 everywhere: any scale
+        const int shE = PRE ? max(egE, 1) - 1023 : 0;                 // prepared: the element's G scale
+        // digits of y_r and y_s stay in registers as A fragments (y_s transposed
+        // by movmatrix); those of y_t, which the t-contraction reads across
+        // warps, go to shared memory
+        uint32_t yr[kS10][2], ys[kS10][2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             unsigned char *p = dig + prow(2 * warp + h, g) + 4 * t;
@@ -324,35 +358,47 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                 digits10_df2_neg(make_float2(y[2 * h][a].s, y[2 * h + 1][a].s), make_float2(y[2 * h][a].c, y[2 * h + 1][a].c),
                                  make_float2(m0, m1), make_float2(m0s, m1s), d0, d1);
 #pragma unroll
-                for (int q = 0; q < kS10; ++q)
-                    *reinterpret_cast<uint32_t *>(p + (a * kS10 + q) * kSlice) = pack_f16(d0[q], d1[q]);
+                for (int q = 0; q < kS10; ++q) {
+                    const uint32_t v = pack_f16(d0[q], d1[q]);
+                    if (a == 0)
+                        yr[q][h] = v;
+                    else if (a == 1)
+                        ys[q][h] = mma::movm_t(v);
+                    else
+                        *reinterpret_cast<uint32_t *>(p + q * kSlice) = v;
+                }
             }
         }
-        __syncthreads();
 
-        // ---- D: transposed contractions on tensor cores
+        // ---- D: transposed contractions on tensor cores.  The s-part lands in
+        // the r-part's accumulators: with K = (plane, l) and the block-diagonal
+        // A = diag(D^T, D^T) over the warp's two planes, the product of A with
+        // the B fragments of y_s (planes 2w, 2w + 1) has rows (k, j) and
+        // columns i, the layout of the r-part.  The level sums then collect
+        // twice the products (levels 0..2 stay below 2^24 and exact; levels 3
+        // and 4 may round by a unit at weights 2^-30 and 2^-40).
         df vo[4];
         {
             float acc[kS10][4];
-            contract<0>(dig_s, warp, lane, ft, acc);
+            contract_regs(yr, ft, acc);
 #pragma unroll
-            for (int q = 0; q < 4; q += 2) combine5_k8x2(acc, q, vo[q], vo[q + 1]);
+            for (int a = 0; a < kS10; ++a)
+#pragma unroll
+                for (int L = a; L < kS10; ++L) mma::f16_16816(acc[L], ft[a], 0u, 0u, ft[a], ys[L - a][0], ys[L - a][1]);
+#pragma unroll
+            for (int q = 0; q < 4; q += 2) combine5x2(acc, q, vo[q], vo[q + 1]);
         }
+        __syncthreads();   // y_t's digits of every warp
         {
             float acc[kS10][4];
-            contract<1>(dig_s + kS10 * kSlice, warp, lane, ft, acc);
-            store_tile<1>(bs, acc, warp, g, t);
-        }
-        {
-            float acc[kS10][4];
-            contract<2>(dig_s + 2 * kS10 * kSlice, warp, lane, ft, acc);
+            contract<2>(dig_s, warp, lane, ft, acc);
             store_tile<2>(bt, acc, warp, g, t);
         }
         __syncthreads();
 
         // ---- E: sum, undo the scales, store
         // w = 2^((eU - 1022) + 2 (eD - 1022) + (eW - 126) - 36) V_out
-        const int SH = (eU - 1022) + 2 * (eD - 1022) + (eW - 126) - 36;
+        const int SH = (eU - 1022) + 2 * (eD - 1022) + (eW + shE - 126) - 36;
         const bool fastSH = SH >= -896 && SH <= 896;   // the same for the whole element
         const unsigned cSH = (unsigned)(896 + SH) << 20;
 #pragma unroll
@@ -362,11 +408,9 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
             double o[2];
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                const float2 sv = bs[sidx(k, g, 2 * t + c)];
                 const float th = c ? tv.z : tv.x, tl = c ? tv.w : tv.y;
-                const df a = dfx::two_sum(vo[2 * h + c].hi, sv.x);
-                const df b = dfx::two_sum(a.hi, th);
-                const float lo = __fadd_rn(__fadd_rn(__fadd_rn(vo[2 * h + c].lo, sv.y), tl), __fadd_rn(a.lo, b.lo));
+                const df b = dfx::two_sum(vo[2 * h + c].hi, th);
+                const float lo = __fadd_rn(__fadd_rn(vo[2 * h + c].lo, tl), b.lo);
                 // bit-level conversions with the scale in the exponent field: one FP64 add
                 double dh, dl;
                 if (fastSH)
@@ -402,33 +446,43 @@ static int launch(int64_t E, const double *u, const double *G, const double *D, 
     return launch_status();
 }
 
-// The prepared geometric factor: per node, G's six entries split hi + lo
-// exactly as ax_f64tc_kernel<false> splits them, and the largest biased
-// exponent of the six.  One thread per node, coalesced in both layouts.
+// The prepared geometric factor: G's entries split hi + lo against one
+// power-of-two scale per element (from the element's largest biased exponent,
+// stored after the 6 x 512 float pairs).  One block of 256 threads per
+// element, two nodes per thread.
 __global__ void __launch_bounds__(256) prepare_kernel(int64_t E, const double *__restrict__ G,
                                                       unsigned char *__restrict__ Gp) {
-    const int64_t total = E * 512, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
-        const int64_t e = p >> 9;
-        const int q = (int)(p & 511);
-        const double *Ge = G + e * 3072 + q;
-        double Gc[6];
-        unsigned hws[6], hmax = 0;
+    __shared__ unsigned wmax[8];
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const double *Ge = G + e * 3072;
+        double Gc[2][6];
+        unsigned hws[2][6], hmax = 0;
 #pragma unroll
-        for (int a = 0; a < 6; ++a) {
-            Gc[a] = ld_stream(Ge + a * 512);
-            hws[a] = habs(Gc[a]);
-            hmax = max(hmax, hws[a]);
-        }
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                Gc[x][a] = ld_stream(Ge + a * 512 + threadIdx.x + 256 * x);
+                hws[x][a] = habs(Gc[x][a]);
+                hmax = max(hmax, hws[x][a]);
+            }
+        hmax = __reduce_max_sync(0xffffffffu, hmax);
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = hmax;
+        __syncthreads();
+        hmax = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) hmax = max(hmax, wmax[q]);
         const int eg = (int)(hmax >> 20), sh = max(eg, 1) - 1023;
         const unsigned K = (unsigned)(896 + sh) << 23, mw = (unsigned)max(897 + sh, 1) << 20;
         float2 *out = reinterpret_cast<float2 *>(Gp + e * kPreBytes);
 #pragma unroll
-        for (int a = 0; a < 6; ++a) {
-            const df d = split_g(Gc[a], hws[a], K, mw);
-            out[a * 512 + q] = make_float2(d.hi, d.lo);
-        }
-        reinterpret_cast<int *>(Gp + e * kPreBytes + kGBytes)[q] = eg;
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                const df d = split_g(Gc[x][a], hws[x][a], K, mw);
+                out[a * 512 + threadIdx.x + 256 * x] = make_float2(d.hi, d.lo);
+            }
+        if (threadIdx.x == 0) *reinterpret_cast<int4 *>(Gp + e * kPreBytes + kGBytes) = make_int4(eg, 0, 0, 0);
+        __syncthreads();   // wmax is reused by the next element
     }
 }
 
@@ -482,7 +536,7 @@ extern "C" int sem_ax_f64tc_prepare(int64_t E, int N, const double *G, void *Gp,
     const size_t n3 = (size_t)(N + 1) * (N + 1) * (N + 1);
     if (overlaps(G, (size_t)E * 6 * n3 * sizeof(double), Gp, (size_t)E * prepared_bytes(N))) return SEMAX_EALIAS;
     if (N == 15) return prepare_f64tc16(E, G, Gp, (cudaStream_t)stream);
-    const int64_t blocks = std::min<int64_t>((E * 512 + 255) / 256, (int64_t)device_sm_count() * 8);
+    const int64_t blocks = std::min<int64_t>(E, (int64_t)device_sm_count() * 8);
     oz::prepare_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(E, G, (unsigned char *)Gp);
     return launch_status();
 }

@@ -1,5 +1,5 @@
 // Arithmetic-pipe probe for the roofline of the plain kernels: every thread
-// runs CH independent chains of dependent fused multiply-adds (FP64 or FP32)
+// runs independent chains of dependent fused multiply-adds (FP64 or FP32)
 // for `iters` steps and writes one sum, so the measured rate is the FMA
 // pipe's sustained throughput with latency hidden by the chains and warps.
 // Not part of the operator.
@@ -7,20 +7,31 @@
 
 namespace semax {
 
-constexpr int kProbeChains = 8;
+// Chains per thread, each with its own multiplier and addend registers: four
+// ran fastest on GB300 in FP64 (eight, or operands shared by all chains, ran
+// 10-15 % slower), eight in FP32 (four reached two-thirds of the FP32 rate).
+template <typename T>
+__host__ __device__ constexpr int probe_chains() { return sizeof(T) == 8 ? 4 : 8; }
 
 template <typename T>
 __global__ void __launch_bounds__(256) fma_probe_kernel(int iters, T b, T c, T *__restrict__ sink) {
-    T a[kProbeChains];
+    constexpr int CH = probe_chains<T>();
+    T a[CH], bq[CH], cq[CH];
 #pragma unroll
-    for (int q = 0; q < kProbeChains; ++q) a[q] = (T)(threadIdx.x + q) * c;
-    for (int it = 0; it < iters; ++it) {
+    for (int q = 0; q < CH; ++q) {
+        a[q] = (T)(threadIdx.x + q) * c;
+        bq[q] = b - (T)q * (T)1e-6 * (T)(1 - b);   // distinct registers, each < 1
+        cq[q] = c * (T)(q + 1);
+    }
+    for (int it = 0; it < iters; it += 4) {
 #pragma unroll
-        for (int q = 0; q < kProbeChains; ++q) a[q] = fma(a[q], b, c);
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < CH; ++q) a[q] = fma(a[q], bq[q], cq[q]);
     }
     T s = 0;
 #pragma unroll
-    for (int q = 0; q < kProbeChains; ++q) s += a[q];
+    for (int q = 0; q < CH; ++q) s += a[q];
     sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
@@ -29,7 +40,7 @@ __global__ void __launch_bounds__(256) fma_probe_kernel(int iters, T b, T c, T *
 using namespace semax;
 
 extern "C" int semax_fma_probe(int prec, int blocks, int iters, void *sink, double *flops, void *stream) {
-    if ((prec != SEMAX_F64 && prec != SEMAX_F32) || blocks <= 0 || iters <= 0 || !sink || !flops)
+    if ((prec != SEMAX_F64 && prec != SEMAX_F32) || blocks <= 0 || iters <= 0 || (iters & 3) || !sink || !flops)
         return SEMAX_EINVAL;
     if (((uintptr_t)sink % (prec == SEMAX_F64 ? 8u : 4u)) != 0) return SEMAX_EALIGN;
     cudaStream_t s = (cudaStream_t)stream;
@@ -37,6 +48,7 @@ extern "C" int semax_fma_probe(int prec, int blocks, int iters, void *sink, doub
         fma_probe_kernel<double><<<blocks, 256, 0, s>>>(iters, 0.9999999999, 1e-9, (double *)sink);
     else
         fma_probe_kernel<float><<<blocks, 256, 0, s>>>(iters, 0.9999999f, 1e-7f, (float *)sink);
-    *flops = 2.0 * kProbeChains * (double)iters * 256.0 * (double)blocks;
+    const int chains = prec == SEMAX_F64 ? probe_chains<double>() : probe_chains<float>();
+    *flops = 2.0 * chains * (double)iters * 256.0 * (double)blocks;
     return launch_status();
 }

@@ -41,13 +41,14 @@ def test_strerror_covers_every_status(lib):
 A = 1 << 40
 
 
-@pytest.mark.parametrize("fn", ["sem_ax", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f32", "sem_ax_bf16x3"])
+@pytest.mark.parametrize("fn", ["sem_ax", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f32", "sem_ax_bf16x3",
+                                "sem_ax_f16x3"])
 def test_argument_validation(lib, fn):
     f = getattr(lib, fn)
 
     def call(E, N, u=A, G=A + (1 << 32), D=A + (2 << 32), w=A + (3 << 32)):
         extra = {"sem_ax": (), "sem_ax_f64x": (), "sem_ax_f64tc": (), "sem_ax_f32": (None,),
-                 "sem_ax_bf16x3": (None, 3)}[fn]
+                 "sem_ax_bf16x3": (None, 3), "sem_ax_f16x3": (None,)}[fn]
         return f(E, N, u, G, D, w, *extra, None)
 
     assert call(0, 7) == 0                      # empty: no-op, nothing inspected
@@ -64,7 +65,7 @@ def test_argument_validation(lib, fn):
 
 def test_prepared_f64tc_validation(lib):
     size = ctypes.c_size_t(0)
-    assert lib.sem_ax_f64tc_prepare_size(10, 7, ctypes.byref(size)) == 0 and size.value == 10 * 26624
+    assert lib.sem_ax_f64tc_prepare_size(10, 7, ctypes.byref(size)) == 0 and size.value == 10 * 24592
     assert lib.sem_ax_f64tc_prepare_size(10, 15, ctypes.byref(size)) == 0 and size.value == 10 * 229376
     assert lib.sem_ax_f64tc_prepare_size(10, 5, ctypes.byref(size)) == -2      # orders 7 and 15 only
     assert lib.sem_ax_f64tc_prepare_size(-1, 7, ctypes.byref(size)) == -1
@@ -181,7 +182,8 @@ def test_status_variants_validation(lib):
 
 def test_fma_probe_validation(lib):
     fl = ctypes.c_double(0.0)
-    assert lib.semax_fma_probe(2, 1, 1, A, ctypes.byref(fl), None) == -1      # bad precision
-    assert lib.semax_fma_probe(0, 0, 1, A, ctypes.byref(fl), None) == -1
-    assert lib.semax_fma_probe(0, 1, 1, None, ctypes.byref(fl), None) == -1
-    assert lib.semax_fma_probe(0, 1, 1, A + 4, ctypes.byref(fl), None) == -3
+    assert lib.semax_fma_probe(2, 1, 4, A, ctypes.byref(fl), None) == -1      # bad precision
+    assert lib.semax_fma_probe(0, 0, 4, A, ctypes.byref(fl), None) == -1
+    assert lib.semax_fma_probe(0, 1, 4, None, ctypes.byref(fl), None) == -1
+    assert lib.semax_fma_probe(0, 1, 3, A, ctypes.byref(fl), None) == -1       # iters not a multiple of 4
+    assert lib.semax_fma_probe(0, 1, 4, A + 4, ctypes.byref(fl), None) == -3

@@ -282,6 +282,66 @@ def test_bf16_split_scaled_matches_unscaled(semax, terms):
     assert torch.equal(w0, w1)
 
 
+# ---------------------------------------------------------------- FP16 splits (3 products) on tensor cores
+#
+# Tolerance: two FP16 pieces keep ~22 bits of each scaled operand (x - x0 -
+# x1 <= 2^-22 |x|, and 2^-25 of the group's largest absolute below FP16's
+# normal range), the dropped product x1 y1 weighs <= 2^-22, and the FP32
+# accumulation and the FP32 geometric-factor multiply add ~2^-24 per step:
+# about 1e-6 of ||w||_inf after the cancellation of the Laplacian's terms.
+# The test holds it to TOL_F16 = 1e-5 (the bar the split forms are held to)
+# and the typical error to 3e-6.
+
+TOL_F16, TYPICAL_F16 = 1e-5, 3e-6
+
+
+@pytest.mark.parametrize("E", [1, 7, 300])
+def test_f16_split_against_f64_oracle(semax, oracle_mod, E):
+    m = si.make_mesh(np.random.default_rng(1300 + E), E, 15)
+    ref = oracle_mod.sem_ax(m.u, m.G, m.D)
+    u, G, D = to_dev(m, torch.float32)
+    w = semax.sem_ax_f16x3(u, G, D)
+    torch.cuda.synchronize()
+    err = rel_err(w, ref)
+    assert err <= TOL_F16 and err <= TYPICAL_F16, err
+
+
+@pytest.mark.parametrize("us,gs", [(2.0 ** 40, 1.0), (2.0 ** -50, 1.0), (1.0, 2.0 ** 30), (2.0 ** -20, 2.0 ** -25)])
+def test_f16_split_is_scale_invariant(semax, us, gs):
+    """Power-of-two scales of u and G scale the result exactly: the operands
+    are rescaled to [1, 2) before the FP16 split, so the pieces are the same."""
+    m = si.make_mesh(np.random.default_rng(1350), 9, 15, device="cuda")
+    u, G, D = (x.float() for x in (m.u, m.G, m.D))
+    w0 = semax.sem_ax_f16x3(u, G, D)
+    w1 = semax.sem_ax_f16x3((u * us).contiguous(), (G * gs).contiguous(), D)
+    torch.cuda.synchronize()
+    assert torch.equal(w1, w0 * (us * gs))
+
+
+def test_f16_split_zero_and_scaled_g(semax, oracle_mod):
+    """An all-zero element, an element with zero u in one plane, and the
+    per-element G scale give the unscaled result bit for bit."""
+    m = si.make_mesh(np.random.default_rng(1360), 11, 15)
+    u = m.u.clone()
+    u[2] = 0.0
+    u[4, 7] = 0.0
+    ref = oracle_mod.sem_ax(u, m.G, m.D)
+    ud, G, D = u.float().cuda(), m.G.float().cuda(), m.D.float().cuda()
+    w0 = semax.sem_ax_f16x3(ud, G, D)
+    s = si.per_element_g_scale(G).float()
+    w1 = semax.sem_ax_f16x3(ud, (G / s.view(-1, 1, 1, 1, 1)).contiguous(), D, G_scale=s)
+    torch.cuda.synchronize()
+    assert torch.equal(w0, w1)
+    assert bool((w0[2] == 0).all())
+    assert rel_err(w0, ref) <= TYPICAL_F16
+
+
+def test_f16_split_rejects_other_orders(semax):
+    m = si.make_mesh(np.random.default_rng(1370), 2, 7, device="cuda")
+    with pytest.raises(semax.SemaxError):
+        semax.sem_ax_f16x3(m.u.float(), m.G.float(), m.D.float())
+
+
 def _geo_inputs(m):
     X = torch.from_numpy(m.X).float().cuda().contiguous()
     xq = torch.cat([torch.from_numpy(si.gll_nodes(m.N)), torch.from_numpy(si.gll_weights(m.N))]).float().cuda()

@@ -18,7 +18,7 @@ def semax():
 def test_fma_probe_runs_and_counts(semax, prec):
     sink, flops = semax.fma_probe(prec, blocks=40, iters=64)
     torch.cuda.synchronize()
-    assert flops == 2 * 8 * 64 * 256 * 40
+    assert flops == 2 * (4 if prec == "f64" else 8) * 64 * 256 * 40
     assert sink.numel() == 40 * 256 and bool(torch.isfinite(sink).all())
-    # thread t's chains start at (t + q) c; after 64 steps of a -> a b + c they are positive
+    # thread t's chains start at (t + q) c; after 64 steps of a -> a b_q + c_q they are positive
     assert bool((sink > 0).all())
