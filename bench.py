@@ -358,9 +358,11 @@ def variants(semax, reps: int, fp64_peak_tflops: float) -> dict:
         out[f"{name}_N15_E8192"] = r
     gp = semax.f64tc_prepare(m.G)
     wp = torch.empty_like(w64)
-    r = rate(lambda: semax.sem_ax_f64tc_prepared(m.u, gp, m.D, wp), dofs, dofs * 72)
+    r = rate(lambda: semax.sem_ax_f64tc_prepared(m.u, gp, m.D, wp), dofs, dofs * bytes_per_node(8))
     r["bit_identical_to_f64tc"] = bool(torch.equal(wp, w64))
-    r["arith"] = "G split into float pairs once (sem_ax_f64tc_prepare), 72 B per node"
+    r["hbm_frac_of_measured"] = r["hbm_gbs"] / load_peaks().get("hbm_gbs", 6800.0)
+    r["arith"] = ("G split into float pairs once (sem_ax_f64tc_prepare), 64 B per node + 16 B per element; "
+                  "GB/s counted at the operator's 64 B per node")
     out["f64tc_prepared_N15_E8192"] = r
     del w64, wp, gp
     u, G, D = m.u.float(), m.G.float(), m.D.float()
@@ -715,8 +717,8 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-SINGLE_KERNELS = ("f64", "f64tc", "f64tc_prepared", "f64x", "f64tc_n15", "f32_n15", "bf16x3_n15", "bf16x6_n15",
-                  "f16x3_n15")
+SINGLE_KERNELS = ("f64", "f64tc", "f64tc_prepared", "f64x", "f64tc_n15", "f64tc_prepared_n15", "f32_n15",
+                  "bf16x3_n15", "bf16x6_n15", "f16x3_n15")
 
 
 def run_single_kernel(args):
@@ -731,11 +733,12 @@ def run_single_kernel(args):
     if name in ("f32_n15", "bf16x3_n15", "bf16x6_n15", "f16x3_n15"):
         u, G, D = u.float(), G.float(), D.float()
     w = torch.empty_like(u)
-    gp = semax.f64tc_prepare(G) if name == "f64tc_prepared" else None
+    gp = semax.f64tc_prepare(G) if name.startswith("f64tc_prepared") else None
     fn = {"f64": lambda: semax.sem_ax(u, G, D, w),
           "f64tc": lambda: semax.sem_ax_f64tc(u, G, D, w),
           "f64tc_n15": lambda: semax.sem_ax_f64tc(u, G, D, w),
           "f64tc_prepared": lambda: semax.sem_ax_f64tc_prepared(u, gp, D, w),
+          "f64tc_prepared_n15": lambda: semax.sem_ax_f64tc_prepared(u, gp, D, w),
           "f64x": lambda: semax.sem_ax_f64x(u, G, D, w),
           "f32_n15": lambda: semax.sem_ax_f32(u, G, D, w),
           "bf16x3_n15": lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=3),

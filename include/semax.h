@@ -143,23 +143,19 @@ int sem_ax_f64tc_status(int64_t E, int N, const double *u, const double *G, cons
 
 /* The tensor-core FP64-accurate Ax with the geometric factor prepared once
  * (for repeated applications with the same G, as in an iterative solver).
- * sem_ax_f64tc_prepare splits G's entries into (hi, lo) float pairs after a
- * power-of-two scale, as sem_ax_f64tc does on every call: at N = 7 against
- * one scale per element (kept in a 16-byte tail after the element's
- * 6 n^3 float pairs: E * 24592 bytes, 64 bytes per node plus 16 per element,
- * the same HBM traffic per call as FP64 G), at N = 15 against one scale per
- * node for each half (rr, rs, rt) and (ss, st, tt) of G, as that kernel
- * splits them, keeping each node's largest biased exponent per half
- * (E * 229376 bytes, 8 bytes per node more than FP64 G); see
- * sem_ax_f64tc_prepare_size.  sem_ax_f64tc_prepared then computes, bit for
- * bit, what sem_ax_f64tc computes from G, without the split (at N = 7
- * sem_ax_f64tc scales per node: the two agree bit for bit unless an
- * element's G entries span more than about 2^100, far beyond any mesh, where
- * the per-element split flushes entries below 2^-126 of the element's
- * largest to zero).  N = 7 and N = 15 (SEMAX_EUNSUPPORTED_N otherwise).  Gp:
- * device memory, 16-byte aligned, owned by the caller, not overlapping G or
- * w, and prepared for the same E and N (its size is not checked, like G's in
- * sem_ax). */
+ * sem_ax_f64tc_prepare splits G's entries into (hi, lo) float pairs against
+ * one power-of-two scale per element, kept in a 16-byte record with the
+ * element's split pairs: E * 24592 bytes at N = 7 (64 bytes per node plus 16
+ * per element, the same HBM traffic per call as FP64 G) and E * 196624 at
+ * N = 15 (sem_ax_f64tc_prepare_size).  sem_ax_f64tc_prepared then computes,
+ * bit for bit, what sem_ax_f64tc computes from G, without the split:
+ * sem_ax_f64tc splits per node (at N = 15 per node and half of G), which
+ * gives the same digits unless an element's G entries span more than about
+ * 2^100, far beyond any mesh, where the per-element split flushes entries
+ * below 2^-126 of the element's largest to zero.  N = 7 and N = 15
+ * (SEMAX_EUNSUPPORTED_N otherwise).  Gp: device memory, 16-byte aligned,
+ * owned by the caller, not overlapping G or w, and prepared for the same E
+ * and N (its size is not checked, like G's in sem_ax). */
 int sem_ax_f64tc_prepare_size(int64_t E, int N, size_t *bytes);
 int sem_ax_f64tc_prepare(int64_t E, int N, const double *G, void *Gp, void *stream);
 int sem_ax_f64tc_prepared(int64_t E, int N, const double *u, const void *Gp, const double *D,

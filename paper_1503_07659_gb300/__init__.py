@@ -107,7 +107,7 @@ def set_wait_polls(polls: int) -> None:
 
 def f64tc_prepare(G: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """The prepared geometric factor of sem_ax_f64tc_prepared (order 7): a
-    uint8 device tensor of E * 24592 bytes (E * 229376 at order 15)."""
+    uint8 device tensor of E * 24592 bytes (E * 196624 at order 15)."""
     if G.dim() != 5 or G.shape[1] != 6:
         raise ValueError("f64tc_prepare: G must be [E, 6, n, n, n]")
     E, N = G.shape[0], G.shape[2] - 1

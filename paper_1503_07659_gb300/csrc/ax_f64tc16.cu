@@ -44,10 +44,10 @@ constexpr int kTB = kN3 * 8;                 // double-float per node: t-directi
 constexpr int kSB = kN3 * 8;                 // double-float per node: the s-gradient, parked (32 KB)
 constexpr int kGS = 3 * kN3 * 8;             // half of an element's G (96 KB)
 constexpr int kRed = 64 * 4;                 // reduction slots
-constexpr int kEgB = kN3 * 4;                // prepared form: each node's largest exponent of the half (16 KB)
-constexpr int kGSP = kGS + kEgB;             // prepared form: one half of an element (112 KB)
+constexpr int kTail = 16;                    // prepared form: the element's largest G exponent, before its halves
+constexpr int kPreElem = kTail + 2 * kGS;    // prepared form: one element (192 KB + 16 B)
 template <bool PRE>
-constexpr size_t smem_bytes() { return kUD + kDD + kTB + kSB + (PRE ? kGSP : kGS) + kRed + 16; }   // + two mbarriers
+constexpr size_t smem_bytes() { return kUD + kDD + kTB + kSB + kTail + kGS + kRed + 16; }   // + two mbarriers
 
 // Byte offset of (row r, 16-byte chunk c) of the 16 x 16 BF16 plane p: the
 // 32 chunks of a plane are permuted by p and by bit 2 of r, so that ldmatrix
@@ -82,9 +82,10 @@ __device__ __forceinline__ int max16(const int *p) {
 }
 
 // PRE = false: G is FP64 [E][6][4096]; PRE = true: G points at the prepared
-// form, per element two halves (rr, rs, rt) and (ss, st, tt), each 3 x 4096
-// (hi, lo) float pairs (split as below, against the half's per-node scale)
-// followed by 4096 ints (each node's largest biased exponent in the half).
+// form, per element a 16-byte tail whose first int is the element's largest
+// biased exponent of G, then the halves (rr, rs, rt) and (ss, st, tt), each
+// 3 x 4096 (hi, lo) float pairs split against that one scale (so the halves
+// need no alignment; FP64 G is split per node and half, below).
 template <bool PRE>
 __global__ void __launch_bounds__(kThreads, 1)
 ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
@@ -94,10 +95,10 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
     unsigned char *dd = ud + kUD;
     float4 *tb = reinterpret_cast<float4 *>(dd + kDD);                 // [2048] node pairs
     float2 *sb = reinterpret_cast<float2 *>(dd + kDD + kTB);           // [8][512] per-thread slots
-    const double2 *gs = reinterpret_cast<const double2 *>(dd + kDD + kTB + kSB);   // [3][2048]
+    const int *tail = reinterpret_cast<const int *>(dd + kDD + kTB + kSB);            // prepared: the element's exponent
+    const double2 *gs = reinterpret_cast<const double2 *>(dd + kDD + kTB + kSB + kTail);   // [3][2048]
     const float4 *gsp = reinterpret_cast<const float4 *>(gs);                       // prepared: [3][2048] pairs x 2
-    const int2 *egs = reinterpret_cast<const int2 *>(dd + kDD + kTB + kSB + kGS);   // prepared: [2048]
-    int *sred = reinterpret_cast<int *>(dd + kDD + kTB + kSB + (PRE ? kGSP : kGS));   // 4 x 16 slots
+    int *sred = reinterpret_cast<int *>(dd + kDD + kTB + kSB + kTail + kGS);         // 4 x 16 slots
     const uint32_t ud_s = smem_u32(ud), dd_s = smem_u32(dd), gs_s = smem_u32(gs);
     const uint32_t barA = smem_u32(sred + 64), barB = barA + 8;
 
@@ -113,9 +114,15 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
     // half h (0: rr, rs, rt; 1: ss, st, tt) of element ep into the staging buffer
     auto stage = [&](uint32_t bar, int64_t ep, int h) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (PRE) {
-            mbar_expect_tx(bar, kGSP);
-            bulk_g2s(gs_s, reinterpret_cast<const unsigned char *>(G) + (2 * ep + h) * (int64_t)kGSP, kGSP, bar);
+        if (PRE) {   // the first half with the element's tail in front of it
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(G) + ep * (int64_t)kPreElem;
+            if (h == 0) {
+                mbar_expect_tx(bar, kTail + kGS);
+                bulk_g2s(gs_s - kTail, src, kTail + kGS, bar);
+            } else {
+                mbar_expect_tx(bar, kGS);
+                bulk_g2s(gs_s, src + kTail + kGS, kGS, bar);
+            }
         } else {
             mbar_expect_tx(bar, kGS);
             bulk_g2s(gs_s, G + (2 * ep + h) * 3 * kN3, kGS, bar);
@@ -183,6 +190,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
             return;
         }
         const int eU = max16(sred);
+        const int egE = PRE ? tail[0] : 0;   // prepared: the element's largest biased G exponent
         {
             const unsigned Ku = (unsigned)(eU - 127) << 23, mw = (unsigned)max(eU - 126, 1) << 20;
 #pragma unroll
@@ -279,11 +287,9 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 const float4 tv = tb[tslot(k, j, 4 * nt + t)];
                 double2 gv[3];
                 float4 gp[3];
-                int2 eg2;
                 if (PRE) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) gp[a] = gsp[a * 2048 + nd2];
-                    eg2 = egs[nd2];
                 } else {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) gv[a] = gs[a * 2048 + nd2];
@@ -298,8 +304,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
                         Gh[a] = df2{make_float2(gp[a].x, gp[a].z), make_float2(gp[a].y, gp[a].w)};
-                    eg0 = eg2.x;
-                    eg1 = eg2.y;
+                    eg0 = eg1 = egE;
                 } else {
                     unsigned hw0[3], hw1[3], hm0 = 0, hm1 = 0;
 #pragma unroll
@@ -381,11 +386,9 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 const float4 tv = tb[tslot(k, j, 4 * nt + t)];
                 double2 gv[3];
                 float4 gp[3];
-                int2 eg2;
                 if (PRE) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) gp[a] = gsp[a * 2048 + nd2];
-                    eg2 = egs[nd2];
                 } else {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) gv[a] = gs[a * 2048 + nd2];
@@ -399,8 +402,7 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
                         Gh[a] = df2{make_float2(gp[a].x, gp[a].z), make_float2(gp[a].y, gp[a].w)};
-                    eg0 = eg2.x;
-                    eg1 = eg2.y;
+                    eg0 = eg1 = egE;
                 } else {
                     unsigned hw0[3], hw1[3], hm0 = 0, hm1 = 0;
 #pragma unroll
@@ -424,12 +426,19 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 dot2_step2(bs, Gh[1], Vt);
                 acc2x2 bt = prod2(Gh[1], Vs);
                 dot2_step2(bt, Gh[2], Vt);
-                // align the two halves' sums to the larger of their scales
+                // align the two halves' sums to the larger of their scales (the
+                // prepared form has one scale per element: nothing to align)
                 const int sm0 = max(shA[q0], sh0), sm1 = max(shA[q0 + 1], sh1);
-                const float2 fa = make_float2(pow2f_or_zero(shA[q0] - sm0), pow2f_or_zero(shA[q0 + 1] - sm1));
-                const float2 fb = make_float2(pow2f_or_zero(sh0 - sm0), pow2f_or_zero(sh1 - sm1));
-                const df2 xs{__fmul2_rn(YSP[p].s, fa), __fmul2_rn(YSP[p].c, fa)}, zs{__fmul2_rn(bs.s, fb), __fmul2_rn(bs.c, fb)};
-                const df2 xt{__fmul2_rn(YTP[p].s, fa), __fmul2_rn(YTP[p].c, fa)}, zt{__fmul2_rn(bt.s, fb), __fmul2_rn(bt.c, fb)};
+                df2 xs, zs, xt, zt;
+                if (PRE) {
+                    xs = df2{YSP[p].s, YSP[p].c}, zs = df2{bs.s, bs.c};
+                    xt = df2{YTP[p].s, YTP[p].c}, zt = df2{bt.s, bt.c};
+                } else {
+                    const float2 fa = make_float2(pow2f_or_zero(shA[q0] - sm0), pow2f_or_zero(shA[q0 + 1] - sm1));
+                    const float2 fb = make_float2(pow2f_or_zero(sh0 - sm0), pow2f_or_zero(sh1 - sm1));
+                    xs = df2{__fmul2_rn(YSP[p].s, fa), __fmul2_rn(YSP[p].c, fa)}, zs = df2{__fmul2_rn(bs.s, fb), __fmul2_rn(bs.c, fb)};
+                    xt = df2{__fmul2_rn(YTP[p].s, fa), __fmul2_rn(YTP[p].c, fa)}, zt = df2{__fmul2_rn(bt.s, fb), __fmul2_rn(bt.c, fb)};
+                }
                 const df2 ts = two_sum2(xs.hi, zs.hi), tt = two_sum2(xt.hi, zt.hi);
                 const df2 sn = two_sum2(ts.hi, __fadd2_rn(__fadd2_rn(xs.lo, zs.lo), ts.lo));
                 const df2 tn = two_sum2(tt.hi, __fadd2_rn(__fadd2_rn(xt.lo, zt.lo), tt.lo));
@@ -599,46 +608,43 @@ int launch_f64tc16_prepared(int64_t E, const double *u, const void *Gp, const do
     return launch16<true>(E, u, reinterpret_cast<const double *>(Gp), D, w, status, s);
 }
 
-size_t f64tc16_prepared_bytes_per_element() { return 2 * (size_t)oz16::kGSP; }
+size_t f64tc16_prepared_bytes_per_element() { return (size_t)oz16::kPreElem; }
 
 namespace oz16 {
-// The prepared geometric factor of order 15: per node and half, the three
-// entries split hi + lo exactly as ax_f64tc16_kernel<false> splits them, and
-// the half's largest biased exponent.  One thread per node.
+// The prepared geometric factor of order 15: the element's 6 x 4096 entries
+// split hi + lo against one power-of-two scale, from the element's largest
+// biased exponent (stored in the 16-byte tail in front of the halves).  One
+// block per element: a pass for the exponent, a pass for the split.
 __global__ void __launch_bounds__(256) prepare16_kernel(int64_t E, const double *__restrict__ G,
                                                         unsigned char *__restrict__ Gp) {
-    const int64_t total = E * kN3, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
-        const int64_t e = p >> 12;
-        const int q = (int)(p & (kN3 - 1));
+    __shared__ unsigned wmax[8];
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const double *Ge = G + e * 6 * kN3;
+        unsigned hmax = 0;
+        for (int q = threadIdx.x; q < 6 * kN3; q += blockDim.x) hmax = max(hmax, habs(ld_stream(Ge + q)));
+        hmax = __reduce_max_sync(0xffffffffu, hmax);
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = hmax;
+        __syncthreads();
+        hmax = 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const double *Gh = G + (2 * e + h) * 3 * kN3 + q;
-            double Gc[3];
-            unsigned hws[3], hmax = 0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                Gc[a] = ld_stream(Gh + a * kN3);
-                hws[a] = habs(Gc[a]);
-                hmax = max(hmax, hws[a]);
-            }
-            const int eg = (int)(hmax >> 20), sh = max(eg, 1) - 1023;
-            const unsigned K = (unsigned)(896 + sh) << 23, mw = (unsigned)max(897 + sh, 1) << 20;
-            unsigned char *half = Gp + (2 * e + h) * (int64_t)kGSP;
-            float2 *out = reinterpret_cast<float2 *>(half);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const df d = split_g(Gc[a], hws[a], K, mw);
-                out[a * kN3 + q] = make_float2(d.hi, d.lo);
-            }
-            reinterpret_cast<int *>(half + kGS)[q] = eg;
+        for (int q = 0; q < 8; ++q) hmax = max(hmax, wmax[q]);
+        const int eg = (int)(hmax >> 20), sh = max(eg, 1) - 1023;
+        const unsigned K = (unsigned)(896 + sh) << 23, mw = (unsigned)max(897 + sh, 1) << 20;
+        unsigned char *pe = Gp + e * (int64_t)kPreElem;
+        float2 *out = reinterpret_cast<float2 *>(pe + kTail);   // [6][4096]: the two halves in order
+        for (int q = threadIdx.x; q < 6 * kN3; q += blockDim.x) {
+            const double x = ld_stream(Ge + q);
+            const df d = split_g(x, habs(x), K, mw);
+            out[q] = make_float2(d.hi, d.lo);
         }
+        if (threadIdx.x == 0) *reinterpret_cast<int4 *>(pe) = make_int4(eg, 0, 0, 0);
+        __syncthreads();   // wmax is reused by the next element
     }
 }
 }  // namespace oz16
 
 int prepare_f64tc16(int64_t E, const double *G, void *Gp, cudaStream_t s) {
-    const int64_t blocks = std::min<int64_t>((E * oz16::kN3 + 255) / 256, (int64_t)device_sm_count() * 8);
+    const int64_t blocks = std::min<int64_t>(E, (int64_t)device_sm_count() * 8);
     oz16::prepare16_kernel<<<(unsigned)blocks, 256, 0, s>>>(E, G, (unsigned char *)Gp);
     return launch_status();
 }

@@ -7,21 +7,23 @@
 
 namespace semax {
 
-// Chains per thread, each with its own multiplier and addend registers: four
-// ran fastest on GB300 in FP64 (eight, or operands shared by all chains, ran
-// 10-15 % slower), eight in FP32 (four reached two-thirds of the FP32 rate).
+// Chains per thread: four in FP64, each with its own multiplier and addend
+// registers (eight chains, or operands shared by all chains, ran 10-15 %
+// slower on GB300); eight in FP32 sharing one multiplier and addend (own
+// operands per chain ran a third slower there).
 template <typename T>
 __host__ __device__ constexpr int probe_chains() { return sizeof(T) == 8 ? 4 : 8; }
 
 template <typename T>
 __global__ void __launch_bounds__(256) fma_probe_kernel(int iters, T b, T c, T *__restrict__ sink) {
     constexpr int CH = probe_chains<T>();
+    constexpr bool kOwn = sizeof(T) == 8;   // per-chain operand registers
     T a[CH], bq[CH], cq[CH];
 #pragma unroll
     for (int q = 0; q < CH; ++q) {
         a[q] = (T)(threadIdx.x + q) * c;
-        bq[q] = b - (T)q * (T)1e-6 * (T)(1 - b);   // distinct registers, each < 1
-        cq[q] = c * (T)(q + 1);
+        bq[q] = kOwn ? b - (T)q * (T)1e-6 * (T)(1 - b) : b;   // each < 1
+        cq[q] = kOwn ? c * (T)(q + 1) : c;
     }
     for (int it = 0; it < iters; it += 4) {
 #pragma unroll

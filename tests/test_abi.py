@@ -66,7 +66,7 @@ def test_argument_validation(lib, fn):
 def test_prepared_f64tc_validation(lib):
     size = ctypes.c_size_t(0)
     assert lib.sem_ax_f64tc_prepare_size(10, 7, ctypes.byref(size)) == 0 and size.value == 10 * 24592
-    assert lib.sem_ax_f64tc_prepare_size(10, 15, ctypes.byref(size)) == 0 and size.value == 10 * 229376
+    assert lib.sem_ax_f64tc_prepare_size(10, 15, ctypes.byref(size)) == 0 and size.value == 10 * 196624
     assert lib.sem_ax_f64tc_prepare_size(10, 5, ctypes.byref(size)) == -2      # orders 7 and 15 only
     assert lib.sem_ax_f64tc_prepare_size(-1, 7, ctypes.byref(size)) == -1
     assert lib.sem_ax_f64tc_prepare_size(10, 7, None) == -1

@@ -323,7 +323,7 @@ def test_f64tc_prepared_order15_equals_f64tc_bit_for_bit(semax, oracle_mod):
     G[8, 5, 1, 2, 3] = float("nan")
     for GG in (m.G, G):
         Gp = semax.f64tc_prepare(GG)
-        assert Gp.numel() == 21 * 229376
+        assert Gp.numel() == 21 * 196624
         w = semax.sem_ax_f64tc_prepared(m.u, Gp, m.D)
         ref = semax.sem_ax_f64tc(m.u, GG, m.D)
         keep = torch.arange(21, device=w.device) != (8 if GG is G else -1)
