@@ -717,7 +717,7 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-SINGLE_KERNELS = ("f64", "f64tc", "f64tc_prepared", "f64x", "f64tc_n15", "f64tc_prepared_n15", "f32_n15",
+SINGLE_KERNELS = ("f64", "f64tc", "f64tc_prepared", "f64x", "f32", "f64tc_n15", "f64tc_prepared_n15", "f32_n15",
                   "bf16x3_n15", "bf16x6_n15", "f16x3_n15")
 
 
@@ -730,7 +730,7 @@ def run_single_kernel(args):
     name = args.kernel
     m = si.make_workload(2 if name.endswith("n15") else 1, device="cuda")[0]
     u, G, D = m.u, m.G, m.D
-    if name in ("f32_n15", "bf16x3_n15", "bf16x6_n15", "f16x3_n15"):
+    if name in ("f32", "f32_n15", "bf16x3_n15", "bf16x6_n15", "f16x3_n15"):
         u, G, D = u.float(), G.float(), D.float()
     w = torch.empty_like(u)
     gp = semax.f64tc_prepare(G) if name.startswith("f64tc_prepared") else None
@@ -740,6 +740,7 @@ def run_single_kernel(args):
           "f64tc_prepared": lambda: semax.sem_ax_f64tc_prepared(u, gp, D, w),
           "f64tc_prepared_n15": lambda: semax.sem_ax_f64tc_prepared(u, gp, D, w),
           "f64x": lambda: semax.sem_ax_f64x(u, G, D, w),
+          "f32": lambda: semax.sem_ax_f32(u, G, D, w),
           "f32_n15": lambda: semax.sem_ax_f32(u, G, D, w),
           "bf16x3_n15": lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=3),
           "bf16x6_n15": lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=6),

@@ -247,6 +247,23 @@ def test_f32_against_f64_oracle(semax, oracle_mod, N, E):
     assert rel_err(w, ref) <= TOL_F32
 
 
+@pytest.mark.parametrize("E", [1, 5, 37, 1000, 5000])
+def test_f32_order7_against_oracle(semax, oracle_mod, E):
+    """Order 7 in FP32: ragged counts, more elements than one wave of CTAs,
+    and a general D that is not centro-antisymmetric (the generic tile)."""
+    m = si.make_mesh(np.random.default_rng(1400 + E), E, 7)
+    ref = oracle_mod.sem_ax(m.u, m.G, m.D)
+    u, G, D = to_dev(m, torch.float32)
+    w = semax.sem_ax_f32(u, G, D)
+    torch.cuda.synchronize()
+    assert rel_err(w, ref) <= TOL_F32
+    Dg = m.D + 0.05 * torch.from_numpy(np.random.default_rng(1401).standard_normal((8, 8)))
+    refg = oracle_mod.sem_ax(m.u, m.G, Dg)
+    wg = semax.sem_ax_f32(u, G, Dg.float().cuda())
+    torch.cuda.synchronize()
+    assert rel_err(wg, refg) <= TOL_F32
+
+
 def test_f32_power_of_two_scale_is_exact(semax):
     m = si.make_mesh(np.random.default_rng(5), 40, 7, device="cuda")
     u, G, D = (x.float() for x in (m.u, m.G, m.D))
