@@ -508,6 +508,13 @@ def variants(semax, reps: int, fp64_peak_tflops: float) -> dict:
     r["energy_rel_err"] = energy_rel_gpu(semax, u, w32, w64)
     out["f32_N7_E262144"] = r
     sample["w"] = {"f64_N7_E262144": w64[it].cpu().numpy(), "f32_N7_E262144": w32[it].double().cpu().numpy()}
+    # FP32 storage, FP16 split with three products on tensor cores
+    r = rate(lambda: semax.sem_ax_f16x3(u, G, D, w32), dofs, dofs * bytes_per_node(4), 10)
+    r["rel_err_vs_f64"] = rel_err_gpu(semax, w32, w64)
+    r["energy_rel_err"] = energy_rel_gpu(semax, u, w32, w64)
+    r["hbm_frac_of_measured"] = r["hbm_gbs"] / load_peaks().get("hbm_gbs", 6800.0)
+    out["f16x3_N7_E262144"] = r
+    sample["w"]["f16x3_N7_E262144"] = w32[it].double().cpu().numpy()
     del u, G, D, w32, w64
     torch.cuda.empty_cache()
     return out, sample
@@ -717,7 +724,7 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-SINGLE_KERNELS = ("f64", "f64tc", "f64tc_prepared", "f64x", "f32", "f64tc_n15", "f64tc_prepared_n15", "f32_n15",
+SINGLE_KERNELS = ("f64", "f64tc", "f64tc_prepared", "f64x", "f32", "f16x3", "f64tc_n15", "f64tc_prepared_n15", "f32_n15",
                   "bf16x3_n15", "bf16x6_n15", "f16x3_n15")
 
 
@@ -730,7 +737,7 @@ def run_single_kernel(args):
     name = args.kernel
     m = si.make_workload(2 if name.endswith("n15") else 1, device="cuda")[0]
     u, G, D = m.u, m.G, m.D
-    if name in ("f32", "f32_n15", "bf16x3_n15", "bf16x6_n15", "f16x3_n15"):
+    if name in ("f32", "f16x3", "f32_n15", "bf16x3_n15", "bf16x6_n15", "f16x3_n15"):
         u, G, D = u.float(), G.float(), D.float()
     w = torch.empty_like(u)
     gp = semax.f64tc_prepare(G) if name.startswith("f64tc_prepared") else None
@@ -741,6 +748,7 @@ def run_single_kernel(args):
           "f64tc_prepared_n15": lambda: semax.sem_ax_f64tc_prepared(u, gp, D, w),
           "f64x": lambda: semax.sem_ax_f64x(u, G, D, w),
           "f32": lambda: semax.sem_ax_f32(u, G, D, w),
+          "f16x3": lambda: semax.sem_ax_f16x3(u, G, D, w),
           "f32_n15": lambda: semax.sem_ax_f32(u, G, D, w),
           "bf16x3_n15": lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=3),
           "bf16x6_n15": lambda: semax.sem_ax_bf16x3(u, G, D, w, terms=6),

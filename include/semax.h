@@ -192,7 +192,8 @@ int sem_ax_bf16x3(int64_t E, int N, const float *u, const float *G, const float 
  * more than 2^24 below their group's largest keep an absolute accuracy of
  * 2^-25 of it.  The geometric factor multiply is FP32; G_scale as in
  * sem_ax_f32.  Error against the FP64 definition ~1e-6 of ||w||_inf.
- * Order N = 15 only (other orders: SEMAX_EUNSUPPORTED_N). */
+ * Orders N = 7 and N = 15 (others: SEMAX_EUNSUPPORTED_N); at N = 7 wr and
+ * ws are scaled per pair of planes (the planes a warp owns). */
 int sem_ax_f16x3(int64_t E, int N, const float *u, const float *G, const float *D, float *w,
                  const float *G_scale, void *stream);
 

@@ -599,11 +599,21 @@ extern "C" int sem_ax_bf16x3(int64_t E, int N, const float *u, const float *G, c
     return tc::launch<3, false>(E, u, G, D, w, G_scale, nullptr, (cudaStream_t)stream);
 }
 
+namespace semax {
+int launch_f16x3_n8(int64_t E, const float *u, const float *G, const float *D, float *w, const float *scale,
+                    cudaStream_t s);
+}
+
 extern "C" int sem_ax_f16x3(int64_t E, int N, const float *u, const float *G, const float *D, float *w,
                             const float *G_scale, void *stream) {
     int st = check_args(E, N, u, G, D, w);
     if (st != SEMAX_OK || E == 0) return st;
-    if (N != 15) return SEMAX_EUNSUPPORTED_N;
+    if (N != 7 && N != 15) return SEMAX_EUNSUPPORTED_N;
+    if (N == 7) {
+        if (G_scale && overlaps(w, (size_t)E * 512 * sizeof(float), G_scale, (size_t)E * sizeof(float)))
+            return SEMAX_EALIAS;
+        return launch_f16x3_n8(E, u, G, D, w, G_scale, (cudaStream_t)stream);
+    }
     if (G_scale && overlaps(w, (size_t)E * 4096 * sizeof(float), G_scale, (size_t)E * sizeof(float)))
         return SEMAX_EALIAS;
     return tc::launch<2, false, true>(E, u, G, D, w, G_scale, nullptr, (cudaStream_t)stream);

@@ -312,9 +312,9 @@ def test_bf16_split_scaled_matches_unscaled(semax, terms):
 TOL_F16, TYPICAL_F16 = 1e-5, 3e-6
 
 
-@pytest.mark.parametrize("E", [1, 7, 300])
-def test_f16_split_against_f64_oracle(semax, oracle_mod, E):
-    m = si.make_mesh(np.random.default_rng(1300 + E), E, 15)
+@pytest.mark.parametrize("N,E", [(15, 1), (15, 7), (15, 300), (7, 1), (7, 37), (7, 5000)])
+def test_f16_split_against_f64_oracle(semax, oracle_mod, N, E):
+    m = si.make_mesh(np.random.default_rng(1300 + E + N), E, N)
     ref = oracle_mod.sem_ax(m.u, m.G, m.D)
     u, G, D = to_dev(m, torch.float32)
     w = semax.sem_ax_f16x3(u, G, D)
@@ -323,11 +323,12 @@ def test_f16_split_against_f64_oracle(semax, oracle_mod, E):
     assert err <= TOL_F16 and err <= TYPICAL_F16, err
 
 
+@pytest.mark.parametrize("N", [7, 15])
 @pytest.mark.parametrize("us,gs", [(2.0 ** 40, 1.0), (2.0 ** -50, 1.0), (1.0, 2.0 ** 30), (2.0 ** -20, 2.0 ** -25)])
-def test_f16_split_is_scale_invariant(semax, us, gs):
+def test_f16_split_is_scale_invariant(semax, N, us, gs):
     """Power-of-two scales of u and G scale the result exactly: the operands
     are rescaled to [1, 2) before the FP16 split, so the pieces are the same."""
-    m = si.make_mesh(np.random.default_rng(1350), 9, 15, device="cuda")
+    m = si.make_mesh(np.random.default_rng(1350), 9, N, device="cuda")
     u, G, D = (x.float() for x in (m.u, m.G, m.D))
     w0 = semax.sem_ax_f16x3(u, G, D)
     w1 = semax.sem_ax_f16x3((u * us).contiguous(), (G * gs).contiguous(), D)
@@ -335,10 +336,11 @@ def test_f16_split_is_scale_invariant(semax, us, gs):
     assert torch.equal(w1, w0 * (us * gs))
 
 
-def test_f16_split_zero_and_scaled_g(semax, oracle_mod):
+@pytest.mark.parametrize("N", [7, 15])
+def test_f16_split_zero_and_scaled_g(semax, oracle_mod, N):
     """An all-zero element, an element with zero u in one plane, and the
     per-element G scale give the unscaled result bit for bit."""
-    m = si.make_mesh(np.random.default_rng(1360), 11, 15)
+    m = si.make_mesh(np.random.default_rng(1360), 11, N)
     u = m.u.clone()
     u[2] = 0.0
     u[4, 7] = 0.0
@@ -353,8 +355,18 @@ def test_f16_split_zero_and_scaled_g(semax, oracle_mod):
     assert rel_err(w0, ref) <= TYPICAL_F16
 
 
+def test_f16_split_general_d_order7(semax, oracle_mod):
+    """The order-7 form takes any D (no symmetry is used)."""
+    m = si.make_mesh(np.random.default_rng(1365), 40, 7)
+    Dg = m.D + 0.05 * torch.from_numpy(np.random.default_rng(1366).standard_normal((8, 8)))
+    ref = oracle_mod.sem_ax(m.u, m.G, Dg)
+    w = semax.sem_ax_f16x3(m.u.float().cuda(), m.G.float().cuda(), Dg.float().cuda())
+    torch.cuda.synchronize()
+    assert rel_err(w, ref) <= TOL_F16
+
+
 def test_f16_split_rejects_other_orders(semax):
-    m = si.make_mesh(np.random.default_rng(1370), 2, 7, device="cuda")
+    m = si.make_mesh(np.random.default_rng(1370), 2, 5, device="cuda")
     with pytest.raises(semax.SemaxError):
         semax.sem_ax_f16x3(m.u.float(), m.G.float(), m.D.float())
 
