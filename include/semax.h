@@ -34,9 +34,11 @@
  *     the device at the address given: device memory, or host memory pinned
  *     with cudaHostAlloc/cudaHostRegister (on NVLink-C2C systems such as
  *     GB300 the kernel then streams the arrays over the coherent link with no
- *     staging copy).  The library never allocates, frees or synchronises
- *     inside sem_ax* calls; work is queued on `stream` (a cudaStream_t,
- *     NULL = legacy default stream) and the call returns before it finishes.
+ *     staging copy).  The operator calls (sem_ax, sem_ax_* apart from the
+ *     plan functions) never allocate, free or synchronise; work is queued
+ *     on `stream` (a cudaStream_t, NULL = legacy default stream) and the
+ *     call returns before it finishes.  Plans, the gather-scatter and the
+ *     PCG solver state what they allocate or wait for.
  *   - 1 <= N <= 15 (n <= 16), else SEMAX_EUNSUPPORTED_N.
  *   - E == 0 is a no-op returning SEMAX_OK (pointers are not inspected).
  *     E < 0 or a NULL pointer with E > 0 returns SEMAX_EINVAL.

@@ -40,6 +40,8 @@ def test_entry_points_capture_into_a_cuda_graph(semax):
     m15 = si.make_mesh(rng, 3, 15, device="cuda")
     gp7, gp15 = semax.f64tc_prepare(m7.G), semax.f64tc_prepare(m15.G)
     u32, G32, D32 = m15.u.float(), m15.G.float(), m15.D.float()
+    u7, G7, D7 = m7.u.float(), m7.G.float(), m7.D.float()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
     cases = {
         "sem_ax": (lambda w: semax.sem_ax(m7.u, m7.G, m7.D, w), m7.u),
         "sem_ax_f64x": (lambda w: semax.sem_ax_f64x(m7.u, m7.G, m7.D, w), m7.u),
@@ -49,9 +51,15 @@ def test_entry_points_capture_into_a_cuda_graph(semax):
         "sem_ax_f64tc_prepared N=15": (lambda w: semax.sem_ax_f64tc_prepared(m15.u, gp15, m15.D, w), m15.u),
         "sem_ax_f32": (lambda w: semax.sem_ax_f32(u32, G32, D32, w), u32),
         "sem_ax_bf16x3": (lambda w: semax.sem_ax_bf16x3(u32, G32, D32, w, terms=6), u32),
+        "sem_ax_f16x3 N=15": (lambda w: semax.sem_ax_f16x3(u32, G32, D32, w), u32),
+        "sem_ax_f16x3 N=7": (lambda w: semax.sem_ax_f16x3(u7, G7, D7, w), u7),
+        "sem_ax_f64tc_status N=7": (lambda w: semax.sem_ax_f64tc(m7.u, m7.G, m7.D, w, status=st), m7.u),
+        "sem_ax_f64tc_prepared_status N=15": (lambda w: semax.sem_ax_f64tc_prepared(m15.u, gp15, m15.D, w, status=st),
+                                              m15.u),
     }
     for name, (fn, like) in cases.items():
         assert _captured_equals_eager(fn, like), name
+    assert int(st.item()) == 0
 
 
 def test_batched_and_reduce_capture_with_preallocated_workspaces(semax):
