@@ -667,7 +667,14 @@ def run_ours(args, rank, world):
     t_h = time_region(lambda: semax.sem_ax_helmholtz(mesh.u, mesh.G, Bm, mesh.D, 1.0, 0.1, wh), args.steps,
                       args.warmup, world) / args.steps
     helm = {"gdofs": world * dofs / t_h / 1e9, "hbm_gbs": world * dofs * 72 / t_h / 1e9, "us_per_call": t_h * 1e6}
-    del wh, Bm
+    # the same with A u FP64-accurate on tensor cores
+    whc = torch.empty_like(w)
+    t_hc = time_region(lambda: semax.sem_ax_helmholtz_f64tc(mesh.u, mesh.G, Bm, mesh.D, 1.0, 0.1, whc), args.steps,
+                       args.warmup, world) / args.steps
+    helm["f64tc"] = {"gdofs": world * dofs / t_hc / 1e9, "hbm_gbs": world * dofs * 72 / t_hc / 1e9,
+                     "hbm_frac_of_measured": dofs * 72 / t_hc / 1e9 / hbm_peak,
+                     "us_per_call": t_hc * 1e6, "rel_err_vs_f64": rel_err_gpu(semax, whc, wh)}
+    del wh, whc, Bm
 
     if rank != 0:
         return

@@ -123,6 +123,14 @@ int sem_ax_f64x(int64_t E, int N, const double *u, const double *G, const double
 int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const double *D,
                  double *w, void *stream);
 
+/* The Helmholtz form w = h1 A u + h2 B u (as sem_ax_helmholtz) with A u
+ * computed FP64-accurately on tensor cores as in sem_ax_f64tc and the mass
+ * term added in FP64: 72 bytes per node moved, like the FP64 form, without
+ * its FP64-pipe limit.  N = 7 on tensor cores; other orders are computed by
+ * sem_ax_helmholtz.  B follows the alignment and aliasing rules of G. */
+int sem_ax_helmholtz_f64tc(int64_t E, int N, const double *u, const double *G, const double *B,
+                           const double *D, double h1, double h2, double *w, void *stream);
+
 /* sem_ax_f64tc with a status word for its bounded device-side waits.  The
  * tensor-core kernels of orders 7 and 15 stage each element's u and G in
  * shared memory with TMA bulk copies that complete on an mbarrier, and wait

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (SemaxError, semax_group, check, SEMAX_OK, SEMAX_ETIMEOUT, SEMAX_F32, SEMAX_F64, SEMAX_PLAN_F64X, SEMAX_PLAN_F64TC,
                    SEMAX_PCG_F64X, SEMAX_PCG_F64TC, SEMAX_PCG_MIXED)
 
-__all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f64tc_prepared", "f64tc_prepare", "set_wait_polls", "fma_probe", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_f16x3", "sem_ax_bf16x3_geo", "sem_ax_batched", "Plan", "reduce",
+__all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_helmholtz_f64tc", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f64tc_prepared", "f64tc_prepare", "set_wait_polls", "fma_probe", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_f16x3", "sem_ax_bf16x3_geo", "sem_ax_batched", "Plan", "reduce",
            "sem_ax_from_host", "SemaxError", "library_path"]
 
 
@@ -60,6 +60,16 @@ def sem_ax_helmholtz(u: torch.Tensor, G: torch.Tensor, B: torch.Tensor, D: torch
     w = _out(w, u)
     check(_lib.lib().sem_ax_helmholtz(E, N, _ptr(u), _ptr(G), _ptr(B), _ptr(D), float(h1), float(h2), _ptr(w),
                                       _stream(stream)), "sem_ax_helmholtz")
+    return w
+
+
+def sem_ax_helmholtz_f64tc(u: torch.Tensor, G: torch.Tensor, B: torch.Tensor, D: torch.Tensor, h1: float,
+                           h2: float, w: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """w = h1 A u + h2 B u with A u FP64-accurate on tensor cores (N = 7; FP64 otherwise)."""
+    E, N = _dims(u, D)
+    w = _out(w, u)
+    check(_lib.lib().sem_ax_helmholtz_f64tc(E, N, _ptr(u), _ptr(G), _ptr(B), _ptr(D), float(h1), float(h2), _ptr(w),
+                                            _stream(stream)), "sem_ax_helmholtz_f64tc")
     return w
 
 

@@ -26,7 +26,7 @@ STATUS_NAMES = {
 
 # every symbol include/semax.h declares
 EXPORTS = (
-    "sem_ax", "sem_ax_helmholtz", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f64tc_status", "sem_ax_f64tc_prepare_size",
+    "sem_ax", "sem_ax_helmholtz", "sem_ax_helmholtz_f64tc", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f64tc_status", "sem_ax_f64tc_prepare_size",
     "sem_ax_f64tc_prepare", "sem_ax_f64tc_prepared", "sem_ax_f64tc_prepared_status", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_f16x3", "sem_ax_bf16x3_geo",
     "sem_ax_batched_workspace_size", "sem_ax_batched",
     "sem_ax_plan_create", "sem_ax_plan_exec", "sem_ax_plan_destroy", "sem_ax_plan_status", "sem_ax_plan_config",
@@ -66,6 +66,7 @@ def _load():
         "sem_ax_f64tc_prepare": [i64, i32, vp, vp, vp],
         "sem_ax_f64tc_prepared": [i64, i32, vp, vp, vp, vp, vp],
         "sem_ax_helmholtz": [i64, i32, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp],
+        "sem_ax_helmholtz_f64tc": [i64, i32, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp],
         "sem_ax_f32": [i64, i32, vp, vp, vp, vp, vp, vp],
         "sem_ax_bf16x3": [i64, i32, vp, vp, vp, vp, vp, i32, vp],
         "sem_ax_f16x3": [i64, i32, vp, vp, vp, vp, vp, vp],

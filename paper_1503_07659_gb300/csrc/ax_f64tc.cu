@@ -154,14 +154,22 @@ __device__ __forceinline__ void store_tile(float2 *buf, const float (&acc)[kS10]
 
 __device__ __forceinline__ int max4(const int *p) { return max(max(p[0], p[1]), max(p[2], p[3])); }
 
+// The Helmholtz form's mass term: w = h1 (A u) + h2 B u, B [E][512].
+struct HelmArgs {
+    const double *B;
+    double h1, h2;
+};
+
 // PRE = false: G is FP64 [E][6][512]; PRE = true: G points at the prepared
 // form, per element 6 x 512 (hi, lo) float pairs (G split against the
 // element's scale) and a 16-byte tail whose first int is the element's
-// largest biased exponent of G.
-template <bool PRE>
+// largest biased exponent of G.  HELM: w = h1 (A u) + h2 B u, the mass term
+// added in FP64 to the FP64 output of A u (three FP64 operations per node).
+template <bool PRE, bool HELM = false>
 __global__ void __launch_bounds__(kThreads, PRE ? 5 : 4)
 ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
-                const double *__restrict__ D, double *__restrict__ w, int *__restrict__ status, int polls) {
+                const double *__restrict__ D, double *__restrict__ w, int *__restrict__ status, int polls,
+                HelmArgs hm) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *dig = smem;
     float2 *bs = reinterpret_cast<float2 *>(smem + kDigBytes);   // s-direction results
@@ -406,6 +414,10 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
             const int k = 2 * warp + h, nb = k * 64 + g * 8 + 2 * t;
             const float4 tv = *reinterpret_cast<const float4 *>(bt + tidx(k, g, 2 * t));
             double o[2];
+            double2 bv = make_double2(0.0, 0.0);
+            if (HELM)
+                asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];"
+                             : "=d"(bv.x), "=d"(bv.y) : "l"(hm.B + e * 512 + nb));
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const float th = c ? tv.z : tv.x, tl = c ? tv.w : tv.y;
@@ -419,6 +431,10 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                     o[c] = dh + dl;
                 else
                     o[c] = scale2(dfx::f2d(b.hi) + dfx::f2d(lo), SH);
+                if (HELM) {   // u of this node is still in uv from phase A
+                    const double uu = c ? uv[h].y : uv[h].x, bb = c ? bv.y : bv.x;
+                    o[c] = __fma_rn(hm.h2 * bb, uu, hm.h1 * o[c]);
+                }
                 if (bad) o[c] = __longlong_as_double(0x7ff8000000000000ll);
             }
             *reinterpret_cast<double2 *>(we + nb) = make_double2(o[0], o[1]);
@@ -428,10 +444,10 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
     if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-template <bool PRE>
+template <bool PRE, bool HELM = false>
 static int launch(int64_t E, const double *u, const double *G, const double *D, double *w, int *status,
-                  cudaStream_t s) {
-    auto kern = ax_f64tc_kernel<PRE>;
+                  cudaStream_t s, HelmArgs hm = HelmArgs{nullptr, 1.0, 0.0}) {
+    auto kern = ax_f64tc_kernel<PRE, HELM>;
     constexpr size_t kSmem = smem_bytes<PRE>();
     int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     if (st != SEMAX_OK) return st;
@@ -442,7 +458,7 @@ static int launch(int64_t E, const double *u, const double *G, const double *D, 
     st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kSmem));
     if (st != SEMAX_OK) return st;
     const int64_t grid = std::min<int64_t>(E, (int64_t)device_sm_count() * std::max(per_sm, 1));
-    kern<<<(unsigned)grid, kThreads, kSmem, s>>>(E, u, G, D, w, status, first_wait_polls());
+    kern<<<(unsigned)grid, kThreads, kSmem, s>>>(E, u, G, D, w, status, first_wait_polls(), hm);
     return launch_status();
 }
 
@@ -508,6 +524,17 @@ extern "C" int sem_ax_f64tc_status(int64_t E, int N, const double *u, const doub
     if (N == 7) return oz::launch<false>(E, u, G, D, w, status, (cudaStream_t)stream);
     if (N == 15) return launch_f64tc16(E, u, G, D, w, status, (cudaStream_t)stream);
     return sem_ax_f64x(E, N, u, G, D, w, stream);   // other orders: the double-float tile (no waits)
+}
+
+extern "C" int sem_ax_helmholtz_f64tc(int64_t E, int N, const double *u, const double *G, const double *B,
+                                      const double *D, double h1, double h2, double *w, void *stream) {
+    if (N != 7) return sem_ax_helmholtz(E, N, u, G, B, D, h1, h2, w, stream);
+    int st = check_args(E, N, u, G, D, w);
+    if (st != SEMAX_OK || E == 0) return st;
+    if (!B) return SEMAX_EINVAL;
+    if (!aligned16(B)) return SEMAX_EALIGN;
+    if (overlaps(w, (size_t)E * 512 * sizeof(double), B, (size_t)E * 512 * sizeof(double))) return SEMAX_EALIAS;
+    return oz::launch<false, true>(E, u, G, D, w, nullptr, (cudaStream_t)stream, oz::HelmArgs{B, h1, h2});
 }
 
 extern "C" int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const double *D, double *w,

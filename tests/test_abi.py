@@ -119,9 +119,10 @@ def test_reduce_validation(lib):
     assert lib.semax_reduce(100, A, 0, A + 4096, 0, A + 8192, None, 0, None) == -8
 
 
-def test_helmholtz_validation(lib):
+@pytest.mark.parametrize("fn", ["sem_ax_helmholtz", "sem_ax_helmholtz_f64tc"])
+def test_helmholtz_validation(lib, fn):
     import ctypes as C
-    f = lib.sem_ax_helmholtz
+    f = getattr(lib, fn)
     u, G, B, D, w = A, A + (1 << 32), A + (4 << 32), A + (2 << 32), A + (3 << 32)
     assert f(0, 7, None, None, None, None, C.c_double(1.0), C.c_double(0.0), None, None) == 0
     assert f(4, 7, u, G, None, D, C.c_double(1.0), C.c_double(0.0), w, None) == -1       # B missing

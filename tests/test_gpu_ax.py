@@ -169,6 +169,49 @@ def test_helmholtz_full_size_sampled(semax, oracle_mod):
     assert rel_err(w[it], ref) <= TOL_F64
 
 
+@pytest.mark.parametrize("N,E", [(7, 1), (7, 37), (7, 3000), (5, 20)])
+def test_helmholtz_f64tc_against_oracle(semax, oracle_mod, N, E):
+    """A u on tensor cores (N = 7; the FP64 form otherwise), the mass term in FP64."""
+    m = si.make_mesh(np.random.default_rng(620 + N + E), E, N)
+    B = si.mass_diagonal(m.X, N)
+    h1, h2 = 0.625, 7.25
+    ref = oracle_mod.sem_helmholtz(m.u, m.G, B, m.D, h1, h2)
+    u, G, D = to_dev(m)
+    w = semax.sem_ax_helmholtz_f64tc(u, G, B.cuda(), D, h1, h2)
+    torch.cuda.synchronize()
+    assert rel_err(w, ref) <= TOL_F64
+
+
+def test_helmholtz_f64tc_reduces_to_f64tc_and_mass(semax):
+    m = si.make_mesh(np.random.default_rng(630), 40, 7, device="cuda")
+    B = si.mass_diagonal(m.X, 7, device="cuda")
+    w_ax = semax.sem_ax_f64tc(m.u, m.G, m.D)
+    w_h = semax.sem_ax_helmholtz_f64tc(m.u, m.G, B, m.D, 1.0, 0.0)
+    one = torch.ones_like(m.u)
+    w_1 = semax.sem_ax_f64tc(one, m.G, m.D)
+    w_m = semax.sem_ax_helmholtz_f64tc(one, m.G, B, m.D, 3.0, 2.0)
+    w_b = semax.sem_ax_helmholtz_f64tc(one, m.G, B, m.D, 0.0, 2.0)
+    torch.cuda.synchronize()
+    assert torch.equal(w_ax, w_h)                  # h1 = 1, h2 = 0: the tensor-core Ax bit for bit
+    assert torch.equal(w_b, 2.0 * B)               # h1 = 0: the mass term alone, exact
+    # one fused multiply-add per node: h2 B u + h1 (A u) with a single rounding, and here
+    # h2 B u = 2 B is exact, so it equals the two-step sum bit for bit
+    assert torch.equal(w_m, 3.0 * w_1 + 2.0 * B)
+    # A annihilates constants (D applied to a constant is zero): what is left is rounding
+    assert w_1.abs().max().item() <= 1e-12 * semax.sem_ax_f64tc(m.u, m.G, m.D).abs().max().item()
+
+
+def test_helmholtz_f64tc_full_size_sampled(semax, oracle_mod):
+    m = si.make_workload(1, device="cuda")[0]
+    B = si.mass_diagonal(m.X, m.N, device="cuda")
+    w = semax.sem_ax_helmholtz_f64tc(m.u, m.G, B, m.D, 1.0, 0.1)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(18).choice(m.E, size=m.E // 50, replace=False))
+    it = torch.from_numpy(idx).cuda()
+    ref = oracle_mod.sem_helmholtz(m.u[it].cpu(), m.G[it].cpu(), B[it].cpu(), m.D.cpu(), 1.0, 0.1)
+    assert rel_err(w[it], ref) <= TOL_F64
+
+
 # ---------------------------------------------------------------- FP64-accurate double-float form
 
 @pytest.mark.parametrize("N", list(range(1, 16)))
