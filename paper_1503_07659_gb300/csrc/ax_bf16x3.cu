@@ -238,6 +238,12 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
 
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         const float *Ge = G + e * (GEO ? 24 : 6 * 4096);
+        if (!GEO) {   // the element's stored G into L2 (three 128-byte lines per thread) ahead of pass P
+            const char *src = reinterpret_cast<const char *>(Ge);
+#pragma unroll
+            for (int it = 0; it < 3; ++it)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(src + 128 * (tid + it * kThreads)));
+        }
         float *we = w + e * 4096;
         if (GEO && tid < 24) {   // trilinear map coefficients of this element
             const int c = tid >> 3, m = tid & 7;

@@ -47,6 +47,15 @@ ax_plain_kernel(int64_t E, int epb, const T *__restrict__ u, const T *__restrict
     T *buf = sD + d_slots<T>(n);
     const int64_t e0 = (int64_t)blockIdx.x * epb;
     const int cnt = (int)(E - e0 < epb ? E - e0 : epb);
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the tile's G into L2 first, so that the column pass's loads of
+        // it wait on L2 rather than on HBM
+        const char *src = reinterpret_cast<const char *>(G + e0 * 6 * n3);
+        const int lines = (int)(((size_t)cnt * 6 * n3 * sizeof(T)) / 128);
+#pragma unroll 1
+        for (int q = threadIdx.x; q < lines; q += blockDim.x)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(src + 128 * (size_t)q));
+    }
     load_D<T, n>(D, sD);
     if constexpr (HELM) helm.B += e0 * n3;
     ax_tile<T, n, MAP, HELM>(cnt, u + e0 * n3, G + e0 * 6 * n3, w + e0 * n3,
