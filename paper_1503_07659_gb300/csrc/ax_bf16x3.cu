@@ -238,7 +238,9 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
 
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         const float *Ge = G + e * (GEO ? 24 : 6 * 4096);
-        if (!GEO) {   // the element's stored G into L2 (three 128-byte lines per thread) ahead of pass P
+        // the element's stored G into L2 ahead of pass P (three 128-byte lines
+        // per thread); two-piece forms only, the three-piece form measured slower
+        if (!GEO && NP == 2) {
             const char *src = reinterpret_cast<const char *>(Ge);
 #pragma unroll
             for (int it = 0; it < 3; ++it)
