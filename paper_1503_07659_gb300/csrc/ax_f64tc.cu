@@ -200,6 +200,10 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
     };
     if (tid == 0) mbar_init(bar, 1);
     __syncthreads();
+    // launched as a programmatic dependent of the previous kernel in the
+    // stream: this CTA may already be resident while that kernel finishes;
+    // no global memory is read before it has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (tid == 0) prefetch(blockIdx.x);
 
     // D digits, once per CTA: B fragments of D^T (gradient) and D (transposed)
@@ -222,6 +226,8 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
     unsigned parity = 0;
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x, parity ^= 1u) {
         double *we = w + e * 512;
+        // the CTA's last element: a dependent launch may start taking SMs
+        if (e + gridDim.x >= E) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
         // ---- A: u -> digits (thread's nodes: k = 2w + h, j = g, i = 2t + c)
         const bool timed_out = !mbar_wait(bar, parity, polls);
@@ -458,7 +464,18 @@ static int launch(int64_t E, const double *u, const double *G, const double *D, 
     st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kSmem));
     if (st != SEMAX_OK) return st;
     const int64_t grid = std::min<int64_t>(E, (int64_t)device_sm_count() * std::max(per_sm, 1));
-    kern<<<(unsigned)grid, kThreads, kSmem, s>>>(E, u, G, D, w, status, first_wait_polls(), hm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    st = cuda_status(cudaLaunchKernelEx(&cfg, kern, E, u, G, D, w, status, first_wait_polls(), hm));
+    if (st != SEMAX_OK) return st;
     return launch_status();
 }
 
