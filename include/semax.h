@@ -119,7 +119,11 @@ int sem_ax_f64x(int64_t E, int N, const double *u, const double *G, const double
  * precision.  An element with an Inf or NaN input returns NaN in every
  * entry.  Orders N = 7 (n = 8) and N = 15 (n = 16) on tensor cores, any
  * D; other orders are computed by sem_ax_f64x.  N = 15 launches one
- * persistent 512-thread block per SM with 207 KB of shared memory. */
+ * persistent 512-thread block per SM with 207 KB of shared memory.  N = 7
+ * is launched as a programmatic dependent of the previous kernel in the
+ * stream (its blocks may become resident while that kernel finishes), and
+ * reads no global memory before that kernel has completed, so stream order
+ * holds as for any launch. */
 int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const double *D,
                  double *w, void *stream);
 

@@ -346,3 +346,40 @@ def test_energy_norm_on_the_gpu(semax, oracle_mod):
         w = fn(u, m.G.cuda(), m.D.cuda())
         e = float(semax.reduce(u.reshape(-1), w.reshape(-1)).cpu().numpy()[2])
         assert abs(e - e_ref) <= 1e-12 * e_ref
+
+
+def test_f64tc_back_to_back_calls_read_the_previous_output(semax):
+    """The order-7 kernel starts as a programmatic dependent of the previous
+    kernel in its stream (its CTAs may be resident during that kernel's last
+    wave) and reads no global memory before that kernel has completed.  A
+    chain of calls, each reading the previous call's output, issued with no
+    synchronisation in between, must give what the same chain gives with a
+    synchronisation after every call; also alternating with the prepared
+    form and with a torch kernel that rewrites the input in between."""
+    m = si.make_workload(1, device="cuda")[0]   # N = 7, E = 32768: many waves per call
+    Gp = semax.f64tc_prepare(m.G)
+    scale = 1.0 / 64.0                          # an exact rescaling between calls
+    bufs = [m.u.clone()] + [torch.empty_like(m.u) for _ in range(4)]
+    torch.cuda.synchronize()
+    for q in range(4):                          # unsynchronised chain, one call straight after another
+        if q % 2 == 0:
+            semax.sem_ax_f64tc(bufs[q], m.G, m.D, bufs[q + 1])
+        else:
+            semax.sem_ax_f64tc_prepared(bufs[q], Gp, m.D, bufs[q + 1])
+    torch.cuda.synchronize()
+    x = m.u.clone()
+    for q in range(4):                          # the same chain, synchronised
+        x = semax.sem_ax_f64tc(x, m.G, m.D) if q % 2 == 0 else semax.sem_ax_f64tc_prepared(x, Gp, m.D)
+        torch.cuda.synchronize()
+        assert torch.equal(bufs[q + 1], x), q
+    # w = A u then u overwritten in place by A's output in the same stream
+    u = m.u.clone()
+    for _ in range(3):
+        semax.sem_ax_f64tc_prepared(u, Gp, m.D, bufs[0])
+        u.copy_(bufs[0]).mul_(scale)
+    torch.cuda.synchronize()
+    x = m.u.clone()
+    for _ in range(3):
+        x = semax.sem_ax_f64tc_prepared(x, Gp, m.D) * scale
+        torch.cuda.synchronize()
+    assert torch.equal(u, x)
