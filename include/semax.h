@@ -252,8 +252,8 @@ int sem_ax_batched(const semax_group *groups, int ngroups, void *workspace,
 
 /* A plan owns a device work counter and a captured CUDA graph that resets the
  * counter and launches the persistent kernel (and, with SEMAX_PLAN_F64TC,
- * the tensor-core kernels beside it on a forked stream, joined before the
- * graph ends).  Creating a plan allocates device memory; executing it does
+ * the groups launched apart beside it, on up to eight forked streams joined
+ * before the graph ends, longest first).  Creating a plan allocates device memory; executing it does
  * not.
  *   tune = 0: use the tuning cache entry if present, else defaults;
  *   tune = 1: time the candidate (elements per tile, thread mapping) pairs for
@@ -265,13 +265,15 @@ int sem_ax_batched(const semax_group *groups, int ngroups, void *workspace,
  *   flags |= SEMAX_PLAN_F64TC: groups of order N = 7 and N = 15 leave the
  *             persistent launch and run sem_ax_f64tc (FP64-accurate on tensor
  *             cores), bit for bit that call's result.  With SEMAX_PLAN_F64X
- *             as well, every order with even n = N + 1 is FP64-accurate.
+ *             as well, every group with even n = N + 1 leaves it (the others
+ *             run sem_ax_f64x, bit for bit), each in a launch of its own, so
+ *             that groups too small to fill the GPU alone run side by side.
  * The group arrays are bound into the plan: they must stay valid while the
  * plan is used (tuning runs the kernel on them, overwriting their w). */
 typedef struct semax_plan semax_plan;
 enum {
     SEMAX_PLAN_F64X = 1,    /* even n: the double-float FP64-accurate tile of sem_ax_f64x */
-    SEMAX_PLAN_F64TC = 2    /* N = 7, 15: sem_ax_f64tc, launched beside the persistent kernel */
+    SEMAX_PLAN_F64TC = 2    /* N = 7, 15: sem_ax_f64tc beside the persistent kernel (with F64X: every even n apart) */
 };
 int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, int ngroups,
                        int tune, const char *cache_path, int flags);
@@ -287,7 +289,8 @@ int sem_ax_plan_status(semax_plan *plan, void *stream);
  * 2 = one thread per line with the even/odd split of D, even n only,
  * 3 = the double-float tile of sem_ax_f64x, chosen by SEMAX_PLAN_F64X,
  * 4 = sem_ax_f64tc in its own launch, chosen by SEMAX_PLAN_F64TC; elements
- * per tile is then 1).  Returns SEMAX_EINVAL if N is not in the plan. */
+ * per tile is then 1; the other orders launched apart report 3 and the
+ * double-float tile's elements per tile).  Returns SEMAX_EINVAL if N is not in the plan. */
 int sem_ax_plan_config(const semax_plan *plan, int N, int *elems_per_tile, int *mapping);
 
 /* ---------------------------------------------------------------- solver around Ax */

@@ -440,7 +440,7 @@ __device__ __forceinline__ void f64x_tile(int cnt, int epb, const double *__rest
 
 
 template <int n>
-__global__ void __launch_bounds__(kThreads, (n <= 8 ? 3 : 1))
+__global__ void __launch_bounds__(kThreads, (n <= 8 ? 3 : (n == 12 ? 4 : 1)))
 ax_f64x_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
                const double *__restrict__ D, double *__restrict__ w) {
     constexpr int n3 = n * n * n, epb = elems_per_tile<n>();

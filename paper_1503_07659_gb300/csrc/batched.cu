@@ -264,7 +264,7 @@ extern "C" int sem_ax_batched(const semax_group *groups, int ngroups, void *work
 
 struct semax_plan {
     BatchParams P;                    // the groups of the persistent launch
-    std::vector<semax_group> tc;      // SEMAX_PLAN_F64TC: the groups of order 7 and 15 (own launches)
+    std::vector<semax_group> tc;      // SEMAX_PLAN_F64TC: the groups launched apart (own graph branches)
     std::vector<TileChoice> choice;   // by n
     unsigned long long *counter = nullptr;   // 256 bytes: the work counter, and at byte 128 the status word
     cudaGraph_t graph = nullptr;
@@ -388,14 +388,28 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
     if (st != SEMAX_OK) return st;
     semax_plan *p = new semax_plan();
     // SEMAX_PLAN_F64TC: orders 7 and 15 leave the persistent launch for the
-    // tensor-core FP64-accurate kernels, captured on a forked stream beside it
+    // tensor-core FP64-accurate kernels; with SEMAX_PLAN_F64X as well, every
+    // group of even n does (orders other than 7 and 15 then run sem_ax_f64x's
+    // kernel).  Each such launch is captured on a branch of its own beside the
+    // persistent launch, so that groups too small to fill the GPU alone share it.
+    const bool all_even_apart = (flags & SEMAX_PLAN_F64TC) && (flags & SEMAX_PLAN_F64X);
     std::vector<semax_group> rest;
     for (int q = 0; q < ngroups; ++q) {
-        if ((flags & SEMAX_PLAN_F64TC) && (groups[q].N == 7 || groups[q].N == 15))
+        const int N = groups[q].N;
+        if ((flags & SEMAX_PLAN_F64TC) && (N == 7 || N == 15 || (all_even_apart && (N + 1) % 2 == 0)))
             p->tc.push_back(groups[q]);
         else
             rest.push_back(groups[q]);
     }
+    // longest first: nodes, the double-float kernel counted at twice the
+    // tensor-core one's cost per node
+    std::stable_sort(p->tc.begin(), p->tc.end(), [](const semax_group &a, const semax_group &b) {
+        auto cost = [](const semax_group &g) {
+            const double n3 = (double)(g.N + 1) * (g.N + 1) * (g.N + 1);
+            return (double)g.E * n3 * ((g.N == 7 || g.N == 15) ? 1.0 : 2.0);
+        };
+        return cost(a) > cost(b);
+    });
     p->choice.assign(17, TileChoice{1, MAP_COLUMN});
     for (int n = 2; n <= 16; ++n) p->choice[n] = default_choice(n);
     std::vector<bool> have(17, false);
@@ -432,12 +446,17 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
 
     if (st == SEMAX_OK && (flags & SEMAX_PLAN_F64X))
         for (int n = 2; n <= 16; n += 2) p->choice[n] = TileChoice{f64x_epb(n), MAP_F64X};
-    cudaStream_t cs2 = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-    if (st == SEMAX_OK && !p->tc.empty()) {
-        st = cuda_status(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
-        if (st == SEMAX_OK) st = cuda_status(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        if (st == SEMAX_OK) st = cuda_status(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    // up to kBranches forked streams, the groups launched apart dealt to them in turn
+    constexpr int kBranches = 8;
+    const int nb = std::min<int>((int)p->tc.size(), kBranches);
+    cudaStream_t cs2[kBranches] = {};
+    cudaEvent_t fork = nullptr, join[kBranches] = {};
+    if (st == SEMAX_OK && nb > 0) {
+        st = cuda_status(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        for (int b = 0; b < nb && st == SEMAX_OK; ++b) {
+            st = cuda_status(cudaStreamCreateWithFlags(&cs2[b], cudaStreamNonBlocking));
+            if (st == SEMAX_OK) st = cuda_status(cudaEventCreateWithFlags(&join[b], cudaEventDisableTiming));
+        }
     }
     if (st == SEMAX_OK) {
         build_params(p->P, rest.data(), (int)rest.size(), p->choice);
@@ -446,18 +465,19 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
         if (st == SEMAX_OK) st = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         if (st == SEMAX_OK) {
             int lst = SEMAX_OK;
-            if (!p->tc.empty()) {   // fork: the tensor-core groups on cs2, joined back before the end
+            if (nb > 0) {   // fork: the groups launched apart on their branches, joined back before the end
                 lst = cuda_status(cudaEventRecord(fork, cs));
-                if (lst == SEMAX_OK) lst = cuda_status(cudaStreamWaitEvent(cs2, fork, 0));
+                for (int b = 0; b < nb && lst == SEMAX_OK; ++b) lst = cuda_status(cudaStreamWaitEvent(cs2[b], fork, 0));
                 for (size_t q = 0; q < p->tc.size() && lst == SEMAX_OK; ++q) {
-                    const semax_group &g = p->tc[q];
-                    if (g.E > 0) lst = sem_ax_f64tc_status(g.E, g.N, g.u, g.G, g.D, g.w, plan_status(p), cs2);
+                    const semax_group &g = p->tc[q];   // sem_ax_f64tc_status runs sem_ax_f64x's kernel for other orders
+                    if (g.E > 0)
+                        lst = sem_ax_f64tc_status(g.E, g.N, g.u, g.G, g.D, g.w, plan_status(p), cs2[q % nb]);
                 }
-                if (lst == SEMAX_OK) lst = cuda_status(cudaEventRecord(join, cs2));
+                for (int b = 0; b < nb && lst == SEMAX_OK; ++b) lst = cuda_status(cudaEventRecord(join[b], cs2[b]));
             }
             if (lst == SEMAX_OK && !rest.empty()) lst = enqueue_batched(p->P, ls, p->counter, cs);
-            if (!p->tc.empty()) {
-                const int jst = cuda_status(cudaStreamWaitEvent(cs, join, 0));
+            for (int b = 0; b < nb; ++b) {
+                const int jst = cuda_status(cudaStreamWaitEvent(cs, join[b], 0));
                 if (lst == SEMAX_OK) lst = jst;
             }
             int est = cuda_status(cudaStreamEndCapture(cs, &p->graph));
@@ -466,8 +486,10 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
         if (st == SEMAX_OK) st = cuda_status(cudaGraphInstantiate(&p->exec, p->graph, 0));
     }
     if (fork) cudaEventDestroy(fork);
-    if (join) cudaEventDestroy(join);
-    if (cs2) cudaStreamDestroy(cs2);
+    for (int b = 0; b < nb; ++b) {
+        if (join[b]) cudaEventDestroy(join[b]);
+        if (cs2[b]) cudaStreamDestroy(cs2[b]);
+    }
     if (cs) cudaStreamDestroy(cs);
     if (st != SEMAX_OK) {
         destroy_plan(p);
@@ -502,9 +524,10 @@ extern "C" int sem_ax_plan_destroy(semax_plan *plan) {
 extern "C" int sem_ax_plan_config(const semax_plan *plan, int N, int *elems_per_tile, int *mapping) {
     if (!plan || plan->magic != 0x5e3a9u) return SEMAX_ENOPLAN;
     for (const semax_group &g : plan->tc) {
-        if (g.N == N) {   // launched apart, one element per CTA pass
-            if (elems_per_tile) *elems_per_tile = 1;
-            if (mapping) *mapping = MAP_F64TC;
+        if (g.N == N) {   // launched apart: the tensor-core kernel (one element per CTA pass) or sem_ax_f64x's
+            const bool tcn = N == 7 || N == 15;
+            if (elems_per_tile) *elems_per_tile = tcn ? 1 : f64x_epb(N + 1);
+            if (mapping) *mapping = tcn ? MAP_F64TC : MAP_F64X;
             return SEMAX_OK;
         }
     }

@@ -120,9 +120,11 @@ def test_plan_f64x_with_odd_orders_and_tuning(semax, oracle_mod):
 @pytest.mark.parametrize("f64x", [False, True])
 def test_plan_with_tensor_core_orders(semax, mix, f64x):
     """SEMAX_PLAN_F64TC: the groups of order 7 and 15 run sem_ax_f64tc beside
-    the persistent launch (a forked stream in the captured graph) and equal
-    that call bit for bit; the other groups equal the plan without the flag,
-    bit for bit, so the fork and join change nothing else.  Replays agree."""
+    the persistent launch (forked streams in the captured graph) and equal
+    that call bit for bit; with SEMAX_PLAN_F64X as well, the other groups of
+    even n are launched apart too and equal sem_ax_f64x bit for bit; every
+    other group equals the plan without the flag, bit for bit, so the forks
+    and joins change nothing else.  Replays agree."""
     ws = [torch.full_like(m.u, float("nan")) for m in mix]
     plan = semax.Plan(_groups(mix, ws), f64x=f64x, f64tc=True)
     plan()
@@ -138,6 +140,8 @@ def test_plan_with_tensor_core_orders(semax, mix, f64x):
         else:
             assert plan.config(m.N) == base.config(m.N)
             assert torch.equal(w, w0), m.N
+            if f64x and (m.N + 1) % 2 == 0:   # launched apart: sem_ax_f64x's kernel
+                assert torch.equal(w, semax.sem_ax_f64x(m.u, m.G, m.D)), m.N
     first = [w.clone() for w in ws]
     plan()
     torch.cuda.synchronize()
