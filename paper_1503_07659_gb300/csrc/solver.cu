@@ -233,6 +233,35 @@ gs_dot_kernel(int64_t nglobal, const int64_t *__restrict__ offsets, const int64_
     finish_in_last_block(part, scal, FIN_PAP, counter);
 }
 
+// The same on the handle's split index: index t < nwork walks the global
+// nodes that need work (Dirichlet nodes first, their copies set to zero,
+// then the shared nodes, summed and written back, in the CSR's order);
+// t >= nwork takes a local node that is its global node's only copy and not
+// Dirichlet, which gather-scatter leaves as it is, so it only adds p_l w_l.
+__global__ void __launch_bounds__(kSolverThreads)
+gs_dot_split_kernel(int64_t nwork, int64_t ndir, int64_t nalone, const int *__restrict__ offsets,
+                    const int *__restrict__ locals, const int *__restrict__ alone, double *__restrict__ w,
+                    const double *__restrict__ p, double *__restrict__ part, double *__restrict__ scal,
+                    unsigned *__restrict__ counter) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, total = nwork + nalone;
+    double acc = 0.0, unused = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        if (t < nwork) {
+            const int q0 = offsets[t], q1 = offsets[t + 1];
+            double sum = 0.0;
+            if (t >= ndir)
+                for (int q = q0; q < q1; ++q) sum += w[locals[q]];
+            for (int q = q0; q < q1; ++q) w[locals[q]] = sum;
+            acc = __fma_rn(p[locals[q0]], sum, acc);
+        } else {
+            const int l = alone[t - nwork];
+            acc = __fma_rn(p[l], w[l], acc);
+        }
+    }
+    block_sum2(acc, unused, part + 2 * blockIdx.x);
+    finish_in_last_block(part, scal, FIN_PAP, counter);
+}
+
 // p = z + beta p (beta from the previous iteration, 0 after a restart) and
 // its FP32 copy, for the mixed-precision operator
 __global__ void __launch_bounds__(kSolverThreads)
@@ -306,6 +335,11 @@ struct semax_gs {
     int64_t *locals = nullptr;         // [nlocal], grouped by global node
     unsigned char *dirichlet = nullptr;
     double *inv_mult = nullptr;        // [nlocal]
+    // split index (32-bit, when nlocal < 2^31): the global nodes that need
+    // work, Dirichlet first (ndir of them), then shared (nwork in all), as a
+    // CSR; and the local nodes that are alone on a non-Dirichlet global node
+    int64_t nwork = 0, ndir = 0, nalone = 0;
+    int *work_off = nullptr, *work_loc = nullptr, *alone = nullptr;
     unsigned magic = 0x95u;
 };
 
@@ -315,6 +349,9 @@ static void gs_free(semax_gs *g) {
     cudaFree(g->locals);
     cudaFree(g->dirichlet);
     cudaFree(g->inv_mult);
+    cudaFree(g->work_off);
+    cudaFree(g->work_loc);
+    cudaFree(g->alone);
     g->magic = 0;
     delete g;
 }
@@ -346,6 +383,32 @@ extern "C" int semax_gs_create(semax_gs **gs, int64_t nlocal, const int64_t *l2g
     if (st == SEMAX_OK && dirichlet) {
         st = cuda_status(cudaMalloc(&g->dirichlet, nglobal));
         if (st == SEMAX_OK) st = cuda_status(cudaMemcpy(g->dirichlet, dirichlet, nglobal, cudaMemcpyHostToDevice));
+    }
+    if (st == SEMAX_OK && nlocal < (int64_t)INT32_MAX) {
+        std::vector<int> woff(1, 0), wloc, al;
+        auto add = [&](int64_t gn) {
+            for (int64_t q = off[gn]; q < off[gn + 1]; ++q) wloc.push_back((int)loc[q]);
+            woff.push_back((int)wloc.size());
+        };
+        for (int64_t gn = 0; gn < nglobal; ++gn)
+            if (dirichlet && dirichlet[gn] && off[gn + 1] > off[gn]) add(gn);
+        g->ndir = (int64_t)woff.size() - 1;
+        for (int64_t gn = 0; gn < nglobal; ++gn) {
+            const int64_t m = off[gn + 1] - off[gn];
+            if (dirichlet && dirichlet[gn]) continue;
+            if (m > 1) add(gn);
+            else if (m == 1) al.push_back((int)loc[off[gn]]);
+        }
+        g->nwork = (int64_t)woff.size() - 1;
+        g->nalone = (int64_t)al.size();
+        st = cuda_status(cudaMalloc(&g->work_off, sizeof(int) * woff.size()));
+        if (st == SEMAX_OK && !wloc.empty()) st = cuda_status(cudaMalloc(&g->work_loc, sizeof(int) * wloc.size()));
+        if (st == SEMAX_OK && !al.empty()) st = cuda_status(cudaMalloc(&g->alone, sizeof(int) * al.size()));
+        if (st == SEMAX_OK) st = cuda_status(cudaMemcpy(g->work_off, woff.data(), sizeof(int) * woff.size(), cudaMemcpyHostToDevice));
+        if (st == SEMAX_OK && !wloc.empty())
+            st = cuda_status(cudaMemcpy(g->work_loc, wloc.data(), sizeof(int) * wloc.size(), cudaMemcpyHostToDevice));
+        if (st == SEMAX_OK && !al.empty())
+            st = cuda_status(cudaMemcpy(g->alone, al.data(), sizeof(int) * al.size(), cudaMemcpyHostToDevice));
     }
     if (st != SEMAX_OK) {
         gs_free(g);
@@ -462,9 +525,14 @@ static int pcg_iteration(semax_pcg *s, double *x, cudaStream_t cs) {
     }
     if (st != SEMAX_OK) return st;
     const semax_gs *gs = s->gs;
-    gs_dot_kernel<<<solver_blocks(gs->nglobal), kSolverThreads, 0, cs>>>(gs->nglobal, gs->offsets, gs->locals,
-                                                                          gs->dirichlet, s->w, s->p, s->part,
-                                                                          s->scal, s->counters);
+    if (gs->work_off)   // the split index: only the nodes that need work walk the CSR
+        gs_dot_split_kernel<<<solver_blocks(gs->nwork + gs->nalone), kSolverThreads, 0, cs>>>(
+            gs->nwork, gs->ndir, gs->nalone, gs->work_off, gs->work_loc, gs->alone, s->w, s->p, s->part, s->scal,
+            s->counters);
+    else
+        gs_dot_kernel<<<solver_blocks(gs->nglobal), kSolverThreads, 0, cs>>>(gs->nglobal, gs->offsets, gs->locals,
+                                                                              gs->dirichlet, s->w, s->p, s->part,
+                                                                              s->scal, s->counters);
     update_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, x, s->r, s->z, s->p, s->w, s->invdiag,
                                                      s->gs->inv_mult, s->scal, s->part, s->counters + 1);
     if (!mixed) pupdate_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->z, s->scal, 1);
