@@ -167,7 +167,11 @@ __device__ __forceinline__ void finish_in_last_block(const double *part, double 
     }
 }
 
-// x += alpha p; r -= alpha w; z = invdiag r; partials of r.z and r.r (weighted)
+// x += alpha p; r -= alpha w; z = invdiag r; partials of r.z and (RR) r.r
+// (weighted).  r.r only serves the host's convergence test, read after the
+// last iteration of each launched block of iterations; the others skip it
+// (and leave 0 in its scalar).
+template <bool RR>
 __global__ void __launch_bounds__(kSolverThreads)
 update_kernel(int64_t count, double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
               const double *__restrict__ p, const double *__restrict__ w, const double *__restrict__ invdiag,
@@ -184,7 +188,7 @@ update_kernel(int64_t count, double *__restrict__ x, double *__restrict__ r, dou
         z[q] = zq;
         const double tq = rq * wt[q];   // shared by both weighted partials
         s0 = __fma_rn(tq, zq, s0);
-        s1 = __fma_rn(tq, rq, s1);
+        if (RR) s1 = __fma_rn(tq, rq, s1);
     }
     block_sum2(s0, s1, part + 2 * blockIdx.x);
     finish_in_last_block(part, scal, FIN_RZ_RR, counter);
@@ -506,7 +510,7 @@ static void pcg_free(semax_pcg *s) {
 // One PCG iteration on stream cs (x is the caller's solution vector).
 // With SEMAX_PCG_MIXED the direction update p = z + beta p is deferred to
 // the start of the next iteration, fused with its FP32 conversion.
-static int pcg_iteration(semax_pcg *s, double *x, cudaStream_t cs) {
+static int pcg_iteration(semax_pcg *s, double *x, cudaStream_t cs, bool rr) {
     const int blocks = solver_blocks(s->count);
     const bool mixed = (s->flags & SEMAX_PCG_MIXED) != 0;
     int st = SEMAX_OK;
@@ -533,8 +537,12 @@ static int pcg_iteration(semax_pcg *s, double *x, cudaStream_t cs) {
         gs_dot_kernel<<<solver_blocks(gs->nglobal), kSolverThreads, 0, cs>>>(gs->nglobal, gs->offsets, gs->locals,
                                                                               gs->dirichlet, s->w, s->p, s->part,
                                                                               s->scal, s->counters);
-    update_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, x, s->r, s->z, s->p, s->w, s->invdiag,
-                                                     s->gs->inv_mult, s->scal, s->part, s->counters + 1);
+    if (rr)
+        update_kernel<true><<<blocks, kSolverThreads, 0, cs>>>(s->count, x, s->r, s->z, s->p, s->w, s->invdiag,
+                                                               s->gs->inv_mult, s->scal, s->part, s->counters + 1);
+    else
+        update_kernel<false><<<blocks, kSolverThreads, 0, cs>>>(s->count, x, s->r, s->z, s->p, s->w, s->invdiag,
+                                                                s->gs->inv_mult, s->scal, s->part, s->counters + 1);
     if (!mixed) pupdate_kernel<<<blocks, kSolverThreads, 0, cs>>>(s->count, s->p, s->z, s->scal, 1);
     return launch_status();
 }
@@ -641,7 +649,8 @@ extern "C" int sem_pcg_solve(semax_pcg *s, const double *b, double *x, int max_i
         if (st == SEMAX_OK) st = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
         if (st == SEMAX_OK) {
             int lst = SEMAX_OK;
-            for (int it = 0; it < kItersPerGraph && lst == SEMAX_OK; ++it) lst = pcg_iteration(s, xi, cap);
+            for (int it = 0; it < kItersPerGraph && lst == SEMAX_OK; ++it)
+                lst = pcg_iteration(s, xi, cap, it == kItersPerGraph - 1);
             int est = cuda_status(cudaStreamEndCapture(cap, &s->graph));
             st = lst != SEMAX_OK ? lst : est;
         }
@@ -672,7 +681,7 @@ extern "C" int sem_pcg_solve(semax_pcg *s, const double *b, double *x, int max_i
                 rs = cuda_status(cudaGraphLaunch(s->exec, cs));
                 done += kItersPerGraph;
             } else {
-                for (int it = 0; it < left && rs == SEMAX_OK; ++it) rs = pcg_iteration(s, xi, cs);
+                for (int it = 0; it < left && rs == SEMAX_OK; ++it) rs = pcg_iteration(s, xi, cs, it == left - 1);
                 done += left;
             }
             if (rs == SEMAX_OK) rs = read_scalars();
