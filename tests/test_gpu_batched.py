@@ -224,3 +224,30 @@ def test_every_mapping_through_cached_plan(semax, oracle_mod, tmp_path, mapping)
         ref = oracle_mod.sem_ax(m.u.cpu(), m.G.cpu(), m.D.cpu())
         assert np.max(np.abs(w.cpu().numpy() - ref)) / np.max(np.abs(ref)) <= 1e-12, (m.N, mapping)
     plan.close()
+
+
+def test_plan_more_groups_apart_than_branches(semax):
+    """With SEMAX_PLAN_F64X and SEMAX_PLAN_F64TC every even-n group runs in a
+    launch of its own, dealt to at most eight graph branches: twelve such
+    groups (orders 1 to 15, some twice, uneven sizes) plus groups of even N
+    that stay in the persistent launch; each equals its own call bit for
+    bit, and a replay gives the same bits."""
+    rng = np.random.default_rng(47)
+    spec = [(1, 30), (3, 17), (5, 9), (7, 40), (9, 5), (11, 3), (13, 2), (15, 2), (7, 3), (3, 1), (11, 6), (5, 21),
+            (2, 11), (4, 7)]
+    meshes = [si.make_mesh(rng, E, N, device="cuda") for N, E in spec]
+    ws = [torch.full_like(m.u, float("nan")) for m in meshes]
+    plan = semax.Plan(_groups(meshes, ws), f64x=True, f64tc=True)
+    plan()
+    torch.cuda.synchronize()
+    first = [w.clone() for w in ws]
+    for m, w in zip(meshes, ws):
+        if (m.N + 1) % 2 == 0:
+            assert torch.equal(w, semax.sem_ax_f64tc(m.u, m.G, m.D)), m.N   # sem_ax_f64x's kernel off 7, 15
+            assert plan.config(m.N)[1] == (4 if m.N in (7, 15) else 3)
+        else:
+            assert torch.isfinite(w).all(), m.N
+    plan()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(first, ws))
+    plan.close()
