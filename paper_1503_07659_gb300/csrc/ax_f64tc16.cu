@@ -74,6 +74,44 @@ __device__ __forceinline__ void pairs15(float (&acc)[kS10][4], const uint32_t (&
             mma::f16_16816(acc[L], A[a][0], A[a][1], A[a][2], A[a][3], B[L - a][0], B[L - a][1]);
 }
 
+// (hi + lo) 2^SH as a double with integer operations only, for SH in
+// [-896, 896] with csh = (896 + SH) << 20 as in f2d_shift: the pair is
+// renormalised by a two-sum (|lo| <= ulp(hi) / 2), so the double of hi has
+// its low 29 significand bits clear and lo, counted in units of that
+// double's ulp and rounded to the nearest integer (ties to even), is an
+// integer k with |k| <= 2^28; adding k to the bit pattern adds k ulps to the
+// magnitude.  Where hi is a power of two and lo pulls its magnitude down, the
+// result lies in the binade below, whose ulp is half as large, and k is
+// counted in those units.  The result is the correctly rounded (hi + lo)
+// 2^SH, bit for bit the FP64 add of the two f2d_shift values.  The prepared
+// instance's output phase converts one node of each pair this way and the
+// other with that add, so that the ALU and the FP64 pipe share the work.
+__device__ __forceinline__ double df_to_double_int(float hi, float lo, unsigned csh) {
+    const df n = dfx::two_sum(hi, lo);
+    const unsigned bs = __float_as_uint(n.hi), bl = __float_as_uint(n.lo);
+    const int es = (int)((bs >> 23) & 0xffu), el = (int)((bl >> 23) & 0xffu);
+    if (es == 0) return dfx::f2d_shift(n.lo, csh);
+    const unsigned hw = (((bs >> 3) & 0x0fffffffu) + csh) | (bs & 0x80000000u);
+    int k = 0;
+    if (el != 0) {
+        const unsigned m = (bl & 0x7fffffu) | 0x800000u;
+        const bool opp = ((bs ^ bl) & 0x80000000u) != 0;
+        const int sh = el - es + 29 + ((opp && !(bs & 0x7fffffu)) ? 1 : 0);   // <= 6
+        unsigned mag = 0u;
+        if (sh >= 0) {
+            mag = m << sh;
+        } else if (sh > -25) {
+            const int r = -sh;
+            const unsigned q = m >> r, rem = m & ((1u << r) - 1u), half = 1u << (r - 1);
+            mag = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+        }
+        k = opp ? -(int)mag : (int)mag;
+    }
+    const unsigned long long bits = ((unsigned long long)hw << 32 | (unsigned long long)(bs << 29)) +
+                                    (unsigned long long)(long long)k;
+    return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ int max16(const int *p) {
     const int4 a = reinterpret_cast<const int4 *>(p)[0], b = reinterpret_cast<const int4 *>(p)[1];
     const int4 c = reinterpret_cast<const int4 *>(p)[2], d = reinterpret_cast<const int4 *>(p)[3];
@@ -563,11 +601,13 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const float vh = c ? s2.hi.y : s2.hi.x, vl = c ? lo.y : lo.x;
-                    // bit-level conversions and scaling: one FP64 add per node (the whole
-                    // CTA runs this phase at once, so FP64-pipe work here is not hidden)
+                    // bit-level conversions and scaling, one FP64 add per node; the whole CTA
+                    // runs this phase at once, so the prepared instance gives the second node
+                    // of each pair to the integer form (the same bits) and the ALU
                     double dh, dl;
                     if (fastSH)
-                        o[c] = dfx::f2d_shift(vh, cSH) + dfx::f2d_shift(vl, cSH);
+                        o[c] = (PRE && c) ? df_to_double_int(vh, vl, cSH)
+                                          : dfx::f2d_shift(vh, cSH) + dfx::f2d_shift(vl, cSH);
                     else if (dfx::f2d_scaled(vh, SHm, dh) && dfx::f2d_scaled(vl, SHm, dl))
                         o[c] = dh + dl;
                     else
