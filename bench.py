@@ -364,7 +364,18 @@ def variants(semax, reps: int, fp64_peak_tflops: float) -> dict:
     r["arith"] = ("G split into float pairs once (sem_ax_f64tc_prepare), 64 B per node + 16 B per element; "
                   "GB/s counted at the operator's 64 B per node")
     out["f64tc_prepared_N15_E8192"] = r
-    del w64, wp, gp
+    del wp, gp
+    # Helmholtz form w = h1 A u + h2 B u at N=15: FP64, and A u on tensor cores
+    # (the mass term read with u again in the output phase: 80 B/node moved)
+    Bm = si.mass_diagonal(m.X, m.N, device="cuda")
+    wh = torch.empty_like(w64)
+    r = rate(lambda: semax.sem_ax_helmholtz(m.u, m.G, Bm, m.D, 1.0, 0.1, w64), dofs, dofs * 72)
+    out["helmholtz_f64_N15_E8192"] = r
+    r = rate(lambda: semax.sem_ax_helmholtz_f64tc(m.u, m.G, Bm, m.D, 1.0, 0.1, wh), dofs, dofs * 72)
+    r["rel_err_vs_f64"] = rel_err_gpu(semax, wh, w64)
+    r["arith"] = "A u FP64-accurate on tensor cores (order-15 kernel), mass term in FP64; GB/s at 72 B/node"
+    out["helmholtz_f64tc_N15_E8192"] = r
+    del w64, wh, Bm
     u, G, D = m.u.float(), m.G.float(), m.D.float()
     u64 = m.u
     X = torch.from_numpy(m.X).float().cuda().contiguous()

@@ -130,8 +130,10 @@ int sem_ax_f64tc(int64_t E, int N, const double *u, const double *G, const doubl
 /* The Helmholtz form w = h1 A u + h2 B u (as sem_ax_helmholtz) with A u
  * computed FP64-accurately on tensor cores as in sem_ax_f64tc and the mass
  * term added in FP64: 72 bytes per node moved, like the FP64 form, without
- * its FP64-pipe limit.  N = 7 on tensor cores; other orders are computed by
- * sem_ax_helmholtz.  B follows the alignment and aliasing rules of G. */
+ * its FP64-pipe limit (N = 15 reads u a second time for the mass term, 80
+ * bytes per node).  N = 7 and N = 15 on tensor cores; other orders are
+ * computed by sem_ax_helmholtz.  B follows the alignment and aliasing rules
+ * of G. */
 int sem_ax_helmholtz_f64tc(int64_t E, int N, const double *u, const double *G, const double *B,
                            const double *D, double h1, double h2, double *w, void *stream);
 

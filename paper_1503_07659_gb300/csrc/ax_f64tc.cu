@@ -439,7 +439,7 @@ ax_f64tc_kernel(int64_t E, const double *__restrict__ u, const double *__restric
                     o[c] = scale2(dfx::f2d(b.hi) + dfx::f2d(lo), SH);
                 if (HELM) {   // u of this node is still in uv from phase A
                     const double uu = c ? uv[h].y : uv[h].x, bb = c ? bv.y : bv.x;
-                    o[c] = __fma_rn(hm.h2 * bb, uu, hm.h1 * o[c]);
+                    o[c] = hm.h1 == 1.0 ? __fma_rn(hm.h2 * bb, uu, o[c]) : __fma_rn(hm.h2 * bb, uu, hm.h1 * o[c]);
                 }
                 if (bad) o[c] = __longlong_as_double(0x7ff8000000000000ll);
             }
@@ -528,6 +528,8 @@ int launch_f64tc16(int64_t E, const double *u, const double *G, const double *D,
 int launch_f64tc16_prepared(int64_t E, const double *u, const void *Gp, const double *D, double *w, int *status,
                             cudaStream_t s);
 int prepare_f64tc16(int64_t E, const double *G, void *Gp, cudaStream_t s);
+int launch_f64tc16_helmholtz(int64_t E, const double *u, const double *G, const double *B, const double *D,
+                             double h1, double h2, double *w, cudaStream_t s);
 size_t f64tc16_prepared_bytes_per_element();
 }
 
@@ -545,12 +547,14 @@ extern "C" int sem_ax_f64tc_status(int64_t E, int N, const double *u, const doub
 
 extern "C" int sem_ax_helmholtz_f64tc(int64_t E, int N, const double *u, const double *G, const double *B,
                                       const double *D, double h1, double h2, double *w, void *stream) {
-    if (N != 7) return sem_ax_helmholtz(E, N, u, G, B, D, h1, h2, w, stream);
+    if (N != 7 && N != 15) return sem_ax_helmholtz(E, N, u, G, B, D, h1, h2, w, stream);
     int st = check_args(E, N, u, G, D, w);
     if (st != SEMAX_OK || E == 0) return st;
     if (!B) return SEMAX_EINVAL;
     if (!aligned16(B)) return SEMAX_EALIGN;
-    if (overlaps(w, (size_t)E * 512 * sizeof(double), B, (size_t)E * 512 * sizeof(double))) return SEMAX_EALIAS;
+    const size_t bytes = (size_t)E * (N + 1) * (N + 1) * (N + 1) * sizeof(double);
+    if (overlaps(w, bytes, B, bytes)) return SEMAX_EALIAS;
+    if (N == 15) return launch_f64tc16_helmholtz(E, u, G, B, D, h1, h2, w, (cudaStream_t)stream);
     return oz::launch<false, true>(E, u, G, D, w, nullptr, (cudaStream_t)stream, oz::HelmArgs{B, h1, h2});
 }
 

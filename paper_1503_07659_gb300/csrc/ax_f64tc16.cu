@@ -124,10 +124,20 @@ __device__ __forceinline__ int max16(const int *p) {
 // biased exponent of G, then the halves (rr, rs, rt) and (ss, st, tt), each
 // 3 x 4096 (hi, lo) float pairs split against that one scale (so the halves
 // need no alignment; FP64 G is split per node and half, below).
-template <bool PRE>
+// The Helmholtz form's mass term: w = h1 (A u) + h2 B u, B [E][4096].
+struct HelmArgs16 {
+    const double *B;
+    double h1, h2;
+};
+
+// HELM: w = h1 (A u) + h2 B u, the mass term added in FP64 to the FP64
+// output of A u; u and B of the element are read again in the output phase
+// (u's digits are gone by then), 16 B per node more than A u alone.
+template <bool PRE, bool HELM = false>
 __global__ void __launch_bounds__(kThreads, 1)
 ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restrict__ G,
-                  const double *__restrict__ D, double *__restrict__ w, int *__restrict__ status, int polls) {
+                  const double *__restrict__ D, double *__restrict__ w, int *__restrict__ status, int polls,
+                  HelmArgs16 hm) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *ud = smem;
     unsigned char *dd = ud + kUD;
@@ -598,20 +608,33 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
                 const df2 s2 = two_sum2(s1.hi, cc.hi);
                 const float2 lo = __fadd2_rn(__fadd2_rn(__fadd2_rn(a.lo, b.lo), cc.lo), __fadd2_rn(s1.lo, s2.lo));
                 double o[2];
+                const int64_t nd = e * 4096 + k * 256 + j * 16 + 8 * nt + 2 * t;   // this node pair
+                double2 uv2 = make_double2(0.0, 0.0), bv2 = make_double2(0.0, 0.0);
+                if (HELM) {
+                    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];"
+                                 : "=d"(uv2.x), "=d"(uv2.y) : "l"(u + nd));
+                    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];"
+                                 : "=d"(bv2.x), "=d"(bv2.y) : "l"(hm.B + nd));
+                }
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const float vh = c ? s2.hi.y : s2.hi.x, vl = c ? lo.y : lo.x;
                     // bit-level conversions and scaling, one FP64 add per node; the whole CTA
                     // runs this phase at once, so the prepared instance gives the second node
-                    // of each pair to the integer form (the same bits) and the ALU
+                    // of each pair to the integer form (the same bits) and the ALU, and the
+                    // Helmholtz instance, whose mass term needs the FP64 pipe, both nodes
                     double dh, dl;
                     if (fastSH)
-                        o[c] = (PRE && c) ? df_to_double_int(vh, vl, cSH)
-                                          : dfx::f2d_shift(vh, cSH) + dfx::f2d_shift(vl, cSH);
+                        o[c] = ((PRE && c) || HELM) ? df_to_double_int(vh, vl, cSH)
+                                                    : dfx::f2d_shift(vh, cSH) + dfx::f2d_shift(vl, cSH);
                     else if (dfx::f2d_scaled(vh, SHm, dh) && dfx::f2d_scaled(vl, SHm, dl))
                         o[c] = dh + dl;
                     else
                         o[c] = scale2(dfx::f2d(vh) + dfx::f2d(vl), SHm);
+                    if (HELM) {   // the Helmholtz instance leaves the FP64 pipe to the mass term
+                        const double mb = hm.h2 * (c ? bv2.y : bv2.x), mu = c ? uv2.y : uv2.x;
+                        o[c] = hm.h1 == 1.0 ? __fma_rn(mb, mu, o[c]) : __fma_rn(mb, mu, hm.h1 * o[c]);
+                    }
                     if (bad) o[c] = __longlong_as_double(0x7ff8000000000000ll);
                 }
                 *reinterpret_cast<double2 *>(we + k * 256 + j * 16 + 8 * nt + 2 * t) = make_double2(o[0], o[1]);
@@ -626,15 +649,15 @@ ax_f64tc16_kernel(int64_t E, const double *__restrict__ u, const double *__restr
 
 }  // namespace oz16
 
-template <bool PRE>
+template <bool PRE, bool HELM = false>
 static int launch16(int64_t E, const double *u, const double *G, const double *D, double *w, int *status,
-                    cudaStream_t s) {
-    auto kern = oz16::ax_f64tc16_kernel<PRE>;
+                    cudaStream_t s, oz16::HelmArgs16 hm = oz16::HelmArgs16{nullptr, 1.0, 0.0}) {
+    auto kern = oz16::ax_f64tc16_kernel<PRE, HELM>;
     constexpr size_t kSmem = oz16::smem_bytes<PRE>();
     int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
     if (st != SEMAX_OK) return st;
     const int64_t grid = std::min<int64_t>(E, (int64_t)device_sm_count());
-    kern<<<(unsigned)grid, oz16::kThreads, kSmem, s>>>(E, u, G, D, w, status, first_wait_polls());
+    kern<<<(unsigned)grid, oz16::kThreads, kSmem, s>>>(E, u, G, D, w, status, first_wait_polls(), hm);
     return launch_status();
 }
 
@@ -646,6 +669,11 @@ int launch_f64tc16(int64_t E, const double *u, const double *G, const double *D,
 int launch_f64tc16_prepared(int64_t E, const double *u, const void *Gp, const double *D, double *w, int *status,
                             cudaStream_t s) {
     return launch16<true>(E, u, reinterpret_cast<const double *>(Gp), D, w, status, s);
+}
+
+int launch_f64tc16_helmholtz(int64_t E, const double *u, const double *G, const double *B, const double *D,
+                             double h1, double h2, double *w, cudaStream_t s) {
+    return launch16<false, true>(E, u, G, D, w, nullptr, s, oz16::HelmArgs16{B, h1, h2});
 }
 
 size_t f64tc16_prepared_bytes_per_element() { return (size_t)oz16::kPreElem; }

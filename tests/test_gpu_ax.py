@@ -169,9 +169,9 @@ def test_helmholtz_full_size_sampled(semax, oracle_mod):
     assert rel_err(w[it], ref) <= TOL_F64
 
 
-@pytest.mark.parametrize("N,E", [(7, 1), (7, 37), (7, 3000), (5, 20)])
+@pytest.mark.parametrize("N,E", [(7, 1), (7, 37), (7, 3000), (15, 1), (15, 40), (5, 20)])
 def test_helmholtz_f64tc_against_oracle(semax, oracle_mod, N, E):
-    """A u on tensor cores (N = 7; the FP64 form otherwise), the mass term in FP64."""
+    """A u on tensor cores (N = 7 and 15; the FP64 form otherwise), the mass term in FP64."""
     m = si.make_mesh(np.random.default_rng(620 + N + E), E, N)
     B = si.mass_diagonal(m.X, N)
     h1, h2 = 0.625, 7.25
@@ -182,9 +182,10 @@ def test_helmholtz_f64tc_against_oracle(semax, oracle_mod, N, E):
     assert rel_err(w, ref) <= TOL_F64
 
 
-def test_helmholtz_f64tc_reduces_to_f64tc_and_mass(semax):
-    m = si.make_mesh(np.random.default_rng(630), 40, 7, device="cuda")
-    B = si.mass_diagonal(m.X, 7, device="cuda")
+@pytest.mark.parametrize("N", [7, 15])
+def test_helmholtz_f64tc_reduces_to_f64tc_and_mass(semax, N):
+    m = si.make_mesh(np.random.default_rng(630 + N), 40, N, device="cuda")
+    B = si.mass_diagonal(m.X, N, device="cuda")
     w_ax = semax.sem_ax_f64tc(m.u, m.G, m.D)
     w_h = semax.sem_ax_helmholtz_f64tc(m.u, m.G, B, m.D, 1.0, 0.0)
     one = torch.ones_like(m.u)
