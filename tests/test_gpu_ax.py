@@ -202,8 +202,9 @@ def test_helmholtz_f64tc_reduces_to_f64tc_and_mass(semax, N):
     assert w_1.abs().max().item() <= 1e-12 * semax.sem_ax_f64tc(m.u, m.G, m.D).abs().max().item()
 
 
-def test_helmholtz_f64tc_full_size_sampled(semax, oracle_mod):
-    m = si.make_workload(1, device="cuda")[0]
+@pytest.mark.parametrize("wl", [1, 2])   # N = 7, E = 32768 and N = 15, E = 8192
+def test_helmholtz_f64tc_full_size_sampled(semax, oracle_mod, wl):
+    m = si.make_workload(wl, device="cuda")[0]
     B = si.mass_diagonal(m.X, m.N, device="cuda")
     w = semax.sem_ax_helmholtz_f64tc(m.u, m.G, B, m.D, 1.0, 0.1)
     torch.cuda.synchronize()
