@@ -459,6 +459,12 @@ def variants(semax, reps: int, fp64_peak_tflops: float) -> dict:
                   "(forked stream in the same graph), the other even orders on the double-float tile")
     out["batched_plan_f64tc_mix"] = r
     plantc.close()
+    planp = semax.Plan([(x.N, x.u, x.G, x.D, w) for x, w in zip(mix, ws)], f64x=True, f64tc=True, f64tc_prepared=True)
+    r = rate(planp, dofs, dofs * bytes_per_node(8))
+    r["rel_err_vs_f64"] = max(rel_err_gpu(semax, w, rw) for w, rw in zip(ws, ref_ws))
+    r["arith"] = "as batched_plan_f64tc_mix, with the G of orders 7 and 15 prepared once at plan creation"
+    out["batched_plan_f64tc_prepared_mix"] = r
+    planp.close()
     del ref_ws
     out["mix_orders"] = {x.N: x.E for x in mix}
     plan.close()

@@ -270,12 +270,18 @@ int sem_ax_batched(const semax_group *groups, int ngroups, void *workspace,
  *             as well, every group with even n = N + 1 leaves it (the others
  *             run sem_ax_f64x, bit for bit), each in a launch of its own, so
  *             that groups too small to fill the GPU alone run side by side.
+ *   flags |= SEMAX_PLAN_F64TC_PREPARED (with SEMAX_PLAN_F64TC): the groups of
+ *             order 7 and 15 run sem_ax_f64tc_prepared on their G split once
+ *             at plan creation (sem_ax_f64tc_prepare, into device buffers the
+ *             plan owns), bit for bit sem_ax_f64tc: G's values are read then,
+ *             so a later change to them does not reach the plan.
  * The group arrays are bound into the plan: they must stay valid while the
  * plan is used (tuning runs the kernel on them, overwriting their w). */
 typedef struct semax_plan semax_plan;
 enum {
     SEMAX_PLAN_F64X = 1,    /* even n: the double-float FP64-accurate tile of sem_ax_f64x */
-    SEMAX_PLAN_F64TC = 2    /* N = 7, 15: sem_ax_f64tc beside the persistent kernel (with F64X: every even n apart) */
+    SEMAX_PLAN_F64TC = 2,   /* N = 7, 15: sem_ax_f64tc beside the persistent kernel (with F64X: every even n apart) */
+    SEMAX_PLAN_F64TC_PREPARED = 4   /* with F64TC: N = 7, 15 on G prepared at plan creation */
 };
 int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, int ngroups,
                        int tune, const char *cache_path, int flags);

@@ -13,7 +13,7 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (SemaxError, semax_group, check, SEMAX_OK, SEMAX_ETIMEOUT, SEMAX_F32, SEMAX_F64, SEMAX_PLAN_F64X, SEMAX_PLAN_F64TC,
+from ._lib import (SemaxError, semax_group, check, SEMAX_OK, SEMAX_ETIMEOUT, SEMAX_F32, SEMAX_F64, SEMAX_PLAN_F64X, SEMAX_PLAN_F64TC, SEMAX_PLAN_F64TC_PREPARED,
                    SEMAX_PCG_F64X, SEMAX_PCG_F64TC, SEMAX_PCG_MIXED)
 
 __all__ = ["GatherScatter", "PCG", "sem_ax_diag", "sem_ax", "sem_ax_helmholtz", "sem_ax_helmholtz_f64tc", "sem_ax_f64x", "sem_ax_f64tc", "sem_ax_f64tc_prepared", "f64tc_prepare", "set_wait_polls", "fma_probe", "sem_ax_f32", "sem_ax_bf16x3", "sem_ax_f16x3", "sem_ax_bf16x3_geo", "sem_ax_batched", "Plan", "reduce",
@@ -206,10 +206,11 @@ class Plan:
     """Graph-captured persistent batched launch (see sem_ax_plan_create)."""
 
     def __init__(self, groups, tune: bool = False, cache_path: str | None = None, f64x: bool = False,
-                 f64tc: bool = False):
+                 f64tc: bool = False, f64tc_prepared: bool = False):
         self._arr, ng = _groups(groups)
         self._handle = ctypes.c_void_p()
-        flags = (SEMAX_PLAN_F64X if f64x else 0) | (SEMAX_PLAN_F64TC if f64tc else 0)
+        flags = ((SEMAX_PLAN_F64X if f64x else 0) | (SEMAX_PLAN_F64TC if f64tc else 0) |
+                 (SEMAX_PLAN_F64TC_PREPARED if f64tc_prepared else 0))
         check(_lib.lib().sem_ax_plan_create(ctypes.byref(self._handle), self._arr, ng, int(bool(tune)),
                                             cache_path.encode() if cache_path else None, flags),
               "sem_ax_plan_create")

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsemax.so")
 SEMAX_OK = 0
 SEMAX_ETIMEOUT = -6
 SEMAX_F64, SEMAX_F32 = 0, 1
-SEMAX_PLAN_F64X, SEMAX_PLAN_F64TC = 1, 2
+SEMAX_PLAN_F64X, SEMAX_PLAN_F64TC, SEMAX_PLAN_F64TC_PREPARED = 1, 2, 4
 SEMAX_PCG_F64X, SEMAX_PCG_F64TC, SEMAX_PCG_MIXED = 1, 2, 4
 
 STATUS_NAMES = {

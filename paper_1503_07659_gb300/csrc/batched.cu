@@ -265,6 +265,7 @@ extern "C" int sem_ax_batched(const semax_group *groups, int ngroups, void *work
 struct semax_plan {
     BatchParams P;                    // the groups of the persistent launch
     std::vector<semax_group> tc;      // SEMAX_PLAN_F64TC: the groups launched apart (own graph branches)
+    std::vector<void *> prep;         // SEMAX_PLAN_F64TC_PREPARED: each tc group's prepared G, or NULL
     std::vector<TileChoice> choice;   // by n
     unsigned long long *counter = nullptr;   // 256 bytes: the work counter, and at byte 128 the status word
     cudaGraph_t graph = nullptr;
@@ -375,6 +376,8 @@ static void destroy_plan(semax_plan *p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->counter) cudaFree(p->counter);
+    for (void *b : p->prep)
+        if (b) cudaFree(b);
     p->magic = 0;
     delete p;
 }
@@ -383,7 +386,8 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
                                   const char *cache_path, int flags) {
     if (!plan) return SEMAX_EINVAL;
     *plan = nullptr;
-    if (flags & ~(SEMAX_PLAN_F64X | SEMAX_PLAN_F64TC)) return SEMAX_EINVAL;
+    if (flags & ~(SEMAX_PLAN_F64X | SEMAX_PLAN_F64TC | SEMAX_PLAN_F64TC_PREPARED)) return SEMAX_EINVAL;
+    if ((flags & SEMAX_PLAN_F64TC_PREPARED) && !(flags & SEMAX_PLAN_F64TC)) return SEMAX_EINVAL;
     int st = check_groups(groups, ngroups);
     if (st != SEMAX_OK) return st;
     semax_plan *p = new semax_plan();
@@ -446,6 +450,20 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
 
     if (st == SEMAX_OK && (flags & SEMAX_PLAN_F64X))
         for (int n = 2; n <= 16; n += 2) p->choice[n] = TileChoice{f64x_epb(n), MAP_F64X};
+    // SEMAX_PLAN_F64TC_PREPARED: the geometric factor of the groups of order
+    // 7 and 15 split once, now, into buffers the plan owns
+    p->prep.assign(p->tc.size(), nullptr);
+    if (st == SEMAX_OK && (flags & SEMAX_PLAN_F64TC_PREPARED)) {
+        for (size_t q = 0; q < p->tc.size() && st == SEMAX_OK; ++q) {
+            const semax_group &g = p->tc[q];
+            if (g.E <= 0 || (g.N != 7 && g.N != 15)) continue;
+            size_t bytes = 0;
+            st = sem_ax_f64tc_prepare_size(g.E, g.N, &bytes);
+            if (st == SEMAX_OK) st = cuda_status(cudaMalloc(&p->prep[q], bytes));
+            if (st == SEMAX_OK) st = sem_ax_f64tc_prepare(g.E, g.N, g.G, p->prep[q], cs);
+        }
+        if (st == SEMAX_OK) st = cuda_status(cudaStreamSynchronize(cs));
+    }
     // up to kBranches forked streams, the groups launched apart dealt to them in turn
     constexpr int kBranches = 8;
     const int nb = std::min<int>((int)p->tc.size(), kBranches);
@@ -470,7 +488,10 @@ extern "C" int sem_ax_plan_create(semax_plan **plan, const semax_group *groups, 
                 for (int b = 0; b < nb && lst == SEMAX_OK; ++b) lst = cuda_status(cudaStreamWaitEvent(cs2[b], fork, 0));
                 for (size_t q = 0; q < p->tc.size() && lst == SEMAX_OK; ++q) {
                     const semax_group &g = p->tc[q];   // sem_ax_f64tc_status runs sem_ax_f64x's kernel for other orders
-                    if (g.E > 0)
+                    if (g.E > 0 && p->prep[q])
+                        lst = sem_ax_f64tc_prepared_status(g.E, g.N, g.u, p->prep[q], g.D, g.w, plan_status(p),
+                                                           cs2[q % nb]);
+                    else if (g.E > 0)
                         lst = sem_ax_f64tc_status(g.E, g.N, g.u, g.G, g.D, g.w, plan_status(p), cs2[q % nb]);
                 }
                 for (int b = 0; b < nb && lst == SEMAX_OK; ++b) lst = cuda_status(cudaEventRecord(join[b], cs2[b]));

@@ -147,7 +147,7 @@ def test_binding_constants_match_the_header():
     import paper_1503_07659_gb300._lib as L
     text = open(os.path.join(ROOT, "include", "semax.h")).read()
     vals = dict((k, int(v)) for k, v in re.findall(r"\b(SEMAX_[A-Z0-9_]+)\s*=\s*(-?\d+)", text))
-    for name in ("SEMAX_F64", "SEMAX_F32", "SEMAX_PLAN_F64X", "SEMAX_PLAN_F64TC", "SEMAX_PCG_F64X",
+    for name in ("SEMAX_F64", "SEMAX_F32", "SEMAX_PLAN_F64X", "SEMAX_PLAN_F64TC", "SEMAX_PLAN_F64TC_PREPARED", "SEMAX_PCG_F64X",
                  "SEMAX_PCG_F64TC", "SEMAX_PCG_MIXED"):
         assert getattr(L, name) == vals[name], name
     for code, name in L.STATUS_NAMES.items():
@@ -157,7 +157,7 @@ def test_binding_constants_match_the_header():
 def test_plan_rejects_unknown_flags(lib):
     h = ctypes.c_void_p()
     assert lib.sem_ax_plan_create(ctypes.byref(h), None, 0, 0, None, 8) == -1   # SEMAX_EINVAL
-    assert lib.sem_ax_plan_create(ctypes.byref(h), None, 0, 0, None, 4) == -1
+    assert lib.sem_ax_plan_create(ctypes.byref(h), None, 0, 0, None, 4) == -1   # F64TC_PREPARED needs F64TC
 
 
 def test_status_variants_validation(lib):

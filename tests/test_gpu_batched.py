@@ -251,3 +251,36 @@ def test_plan_more_groups_apart_than_branches(semax):
     torch.cuda.synchronize()
     assert all(torch.equal(a, b) for a, b in zip(first, ws))
     plan.close()
+
+
+def test_plan_with_prepared_tensor_core_orders(semax, mix):
+    """SEMAX_PLAN_F64TC_PREPARED: the groups of order 7 and 15 run on their G
+    split once at plan creation, bit for bit sem_ax_f64tc; the other groups
+    equal the plan without the flag; G's values are read at creation, so a
+    later change to G does not reach the plan."""
+    ws = [torch.full_like(m.u, float("nan")) for m in mix]
+    Gs = [m.G.clone() for m in mix]
+    plan = semax.Plan([(m.N, m.u, G, m.D, w) for m, G, w in zip(mix, Gs, ws)], f64x=True, f64tc=True,
+                      f64tc_prepared=True)
+    plan()
+    torch.cuda.synchronize()
+    ws0 = [torch.full_like(m.u, float("nan")) for m in mix]
+    base = semax.Plan(_groups(mix, ws0), f64x=True, f64tc=True)
+    base()
+    torch.cuda.synchronize()
+    for m, w, w0 in zip(mix, ws, ws0):
+        assert torch.equal(w, w0), m.N
+        if m.N in (7, 15):
+            assert torch.equal(w, semax.sem_ax_f64tc(m.u, m.G, m.D)), m.N
+    first = [w.clone() for w in ws]
+    for G in Gs:
+        G.mul_(2.0)
+    plan()
+    torch.cuda.synchronize()
+    for m, w, w1 in zip(mix, ws, first):
+        if m.N in (7, 15):
+            assert torch.equal(w, w1), m.N              # prepared at creation: unchanged
+        else:
+            assert torch.equal(w, 2.0 * w1), m.N        # read at execution: doubled (exact)
+    plan.close()
+    base.close()
