@@ -213,6 +213,9 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
     float *sgeo = W + kWBytes / 4;                            // GEO: map coefficients [3][8], xi [16], wq [16]
     unsigned *smax = reinterpret_cast<unsigned *>(W + kWBytes / 4);   // F16: per-warp maxima of |u| and |wt|
     const uint32_t upc_s = smem_addr(upc), wpc_s = smem_addr(wpc);
+    // launched as a programmatic dependent of the previous kernel in the
+    // stream: no global memory is read before that kernel has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (GEO && threadIdx.x < 32) sgeo[24 + threadIdx.x] = xq[threadIdx.x];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -238,6 +241,8 @@ ax_bf16_kernel(int64_t E, const float *__restrict__ u, const float *__restrict__
 
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         const float *Ge = G + e * (GEO ? 24 : 6 * 4096);
+        // the CTA's last element: a dependent launch may start taking SMs
+        if (e + gridDim.x >= E) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         // the element's stored G into L2 ahead of pass P (three 128-byte lines
         // per thread); two-piece forms only, the three-piece form measured slower
         if (!GEO && NP == 2) {
@@ -586,7 +591,18 @@ static int launch(int64_t E, const float *u, const float *G, const float *D, flo
     if (per_sm < 1) return SEMAX_EINVAL;
     int64_t grid = (int64_t)per_sm * device_sm_count();
     if (grid > E) grid = E;
-    kern<<<(unsigned)grid, kThreads, smem, s>>>(E, u, G, D, w, scale, xq);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];   // a programmatic dependent of the previous kernel in the stream
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    st = cuda_status(cudaLaunchKernelEx(&cfg, kern, E, u, G, D, w, scale, xq));
+    if (st != SEMAX_OK) return st;
     return launch_status();
 }
 

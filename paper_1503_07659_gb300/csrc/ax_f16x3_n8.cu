@@ -100,6 +100,9 @@ ax_f16x3_n8_kernel(int64_t E, const float *__restrict__ u, const float *__restri
     float *bt = bs + 8 * kSPlane;                                   // ut, later w_t [k][j][i]
     unsigned *sred = reinterpret_cast<unsigned *>(bt + 8 * kTPlane);   // [0, 4) |u|, [4, 8) |wt| maxima
     const uint32_t pc_s = mma::smem_u32(pc), stage_s = mma::smem_u32(smem);
+    // launched as a programmatic dependent of the previous kernel in the
+    // stream: no global memory is read before that kernel has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
 
     // u and G of element ep into the staging buffer: 896 16-byte chunks
@@ -124,6 +127,8 @@ ax_f16x3_n8_kernel(int64_t E, const float *__restrict__ u, const float *__restri
     pieces(D[(2 * t) * 8 + g] * sD, D[(2 * t + 1) * 8 + g] * sD, ft[0], ft[1]);
 
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        // the CTA's last element: a dependent launch may start taking SMs
+        if (e + gridDim.x >= E) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();   // every thread's chunks of this element have landed
 
@@ -276,7 +281,18 @@ int launch_f16x3_n8(int64_t E, const float *u, const float *G, const float *D, f
     st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, f16n8::kThreads, f16n8::kSmem));
     if (st != SEMAX_OK) return st;
     const int64_t grid = std::min<int64_t>(E, (int64_t)device_sm_count() * std::max(per_sm, 1));
-    kern<<<(unsigned)grid, f16n8::kThreads, f16n8::kSmem, s>>>(E, u, G, D, w, scale);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(f16n8::kThreads);
+    cfg.dynamicSmemBytes = f16n8::kSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];   // a programmatic dependent of the previous kernel in the stream
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    st = cuda_status(cudaLaunchKernelEx(&cfg, kern, E, u, G, D, w, scale));
+    if (st != SEMAX_OK) return st;
     return launch_status();
 }
 
